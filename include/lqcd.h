@@ -1,0 +1,208 @@
+/*
+ * lqcd.h - C ABI of the GB300 even-odd staggered multi-shift CG library (liblqcd.so).
+ *
+ * The library implements the hot path of 2-flavour staggered RHMC described in
+ * Gupta & Majumdar, arXiv:1710.09178: the half-lattice hopping operator
+ * (Section 3.2), the shifted conjugate gradient that applies the rational
+ * approximations of Eq. ratapprx (Section 4), and the host-side generation of
+ * the rational coefficients (Appendix).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status (LQCD_OK = 0 on success).  No C++
+ *    exception crosses the ABI and no error traps the GPU; lqcd_last_error()
+ *    returns a message for the last failure on a context.
+ *  - Pointers named *_dev are CUDA device pointers (e.g. torch tensor
+ *    data_ptr()); the caller owns them and keeps them alive for the duration of
+ *    the call.  The library never frees caller memory.  The context owns its
+ *    workspace and its internal copies of the gauge field.
+ *  - All GPU work is enqueued on the context's stream (lqcd_set_stream).  Calls
+ *    that return host scalars or statistics synchronise that stream only.
+ *  - Lattice: extents Nx, Ny, Nz, Nt, all positive and even; site address
+ *    l = x + Nx*(y + Ny*(z + Nz*t)) (Section 2, 0-based); a site is even when
+ *    x+y+z+t is even; within one parity a site's half-lattice index is l >> 1.
+ *    V = Nx*Ny*Nz*Nt, Vh = V/2.
+ *  - Operator (Section 3.2, normalised with a factor 1/2 and explicit phases):
+ *      (D psi)(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) psi(x+mu) - U_mu(x-mu)^+ psi(x-mu)],
+ *    eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z),
+ *    periodic in x, y, z and antiperiodic in t.  D_oe maps even to odd sites,
+ *    D_eo odd to even, and A = 4 m^2 - D_eo D_oe acts on even sites.
+ *  - Canonical layouts (what callers hand in and get back):
+ *      gauge : complex128 [V][4][3][3]  (site l, direction mu, row, column)
+ *      vector: complex128 [Vh][3]       (one parity, half-lattice index, colour)
+ *    Internal layouts (what dslash_eo works on) are produced by
+ *    lqcd_pack_vector and described there.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LQCD_OK 0
+#define LQCD_ERR_ARG 1           /* bad argument (null pointer, bad size, unknown enum) */
+#define LQCD_ERR_DIMS 2          /* lattice extents not all positive and even */
+#define LQCD_ERR_CUDA 3          /* a CUDA runtime call failed */
+#define LQCD_ERR_NOT_CONVERGED 4 /* solver reached maxiter; outputs hold the last iterate */
+#define LQCD_ERR_NONFINITE 5     /* NaN or Inf met in a reduction */
+#define LQCD_ERR_STATE 6         /* e.g. no gauge field loaded yet */
+
+/* precision modes (storage / arithmetic of links and Krylov vectors) */
+#define LQCD_FP64 0     /* FP64 links and vectors, FP64 arithmetic */
+#define LQCD_FP32 1     /* FP32 18-real links and vectors, FP32 arithmetic */
+#define LQCD_FP32_R12 2 /* FP32 12-real links (third row rebuilt), FP32 vectors */
+#define LQCD_FP16FIX 3  /* FP32 links; shifted Krylov vectors in 16-bit fixed point + per-site scale */
+
+#define LQCD_MAX_SHIFTS 32
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+/* Per-solve statistics filled by mshift_cg. */
+typedef struct {
+  int iterations;         /* shifted-CG iterations of the base system */
+  int reliable_updates;   /* FP64 residual recomputations */
+  int refine_iterations;  /* CG iterations spent in per-shift refinement */
+  int refined_shifts;     /* shifts that needed refinement */
+  int kernel_launches;    /* kernels this call launched (graph nodes counted) */
+  int n_shifts;
+  double true_residual[LQCD_MAX_SHIFTS]; /* |b - (A + d_k) x_k| / |b| in FP64, per shift */
+  double ms;              /* wall time of the call on its stream (CUDA events) */
+} lqcd_solve_stats;
+
+/*
+ * lqcd_create - allocate a context for one lattice.
+ *   dims   : Nx, Ny, Nz, Nt (each positive and even; LQCD_ERR_DIMS otherwise)
+ *   mass   : quark mass m of M = 2m + D (A = 4 m^2 - D_eo D_oe)
+ *   stream : cudaStream_t to enqueue work on (NULL = legacy default stream)
+ * On success *out holds the context; on failure *out is NULL.
+ */
+int lqcd_create(lqcd_ctx** out, const int dims[4], double mass, void* stream);
+
+/* Release a context and all device memory it owns.  NULL is accepted. */
+int lqcd_destroy(lqcd_ctx* ctx);
+
+/* Message for the last failure on ctx (static storage owned by the context). */
+const char* lqcd_last_error(const lqcd_ctx* ctx);
+
+/* Change the stream that later calls enqueue on. */
+int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
+
+/*
+ * lqcd_set_gauge - load a gauge field (Section 2: 3x3 complex SU(3) matrices on links).
+ *   U_dev : device complex128 [V][4][3][3], canonical layout.  Read only.
+ * Builds the internal copies (FP64 and FP32 with 1/2 eta_mu and the boundary sign
+ * folded in; FP32 12-real rows 0-1 without signs).  The 12-real form assumes
+ * the links are in SU(3).  Returns LQCD_ERR_ARG on a NULL pointer.
+ */
+int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev);
+
+/*
+ * lqcd_vector_bytes - bytes of one internal half-lattice vector of precision prec:
+ *   LQCD_FP64                : 48*Vh, [3 colours][Vh] double2 (re, im)
+ *   LQCD_FP32, LQCD_FP32_R12 : 24*Vh, [3 colours][Vh] float2
+ *   LQCD_FP16FIX             : 16*Vh, [Vh] x 16 bytes: six int16 codes q_i then a
+ *                              float32 scale s; component i = q_i * s (order re0,
+ *                              im0, re1, im1, re2, im2)
+ * Returns 0 for an unknown precision.
+ */
+size_t lqcd_vector_bytes(const lqcd_ctx* ctx, int prec);
+
+/*
+ * lqcd_pack_vector / lqcd_unpack_vector - convert one half-lattice vector between
+ * the canonical complex128 layout and the internal layout of `prec`
+ * (device to device, enqueued on the context stream).  Packing to FP32 rounds to
+ * nearest; packing to FP16FIX uses n = max_i |v_i| of the float32-rounded site,
+ * q_i = rint(v_i * (32767/n)), s = n/32767 (zero site -> zero codes, s = 0).
+ */
+int lqcd_pack_vector(lqcd_ctx* ctx, void* dst_dev, int prec, const double* src_dev);
+int lqcd_unpack_vector(lqcd_ctx* ctx, double* dst_dev, const void* src_dev, int prec);
+
+/*
+ * dslash_eo - half-lattice hopping operator (Section 3.2; Fig. evenodd).
+ *   out_parity = 1: out = D_oe in  (in on even sites, out on odd sites)
+ *   out_parity = 0: out = D_eo in  (in on odd sites, out on even sites)
+ *   prec       : LQCD_FP64, LQCD_FP32 or LQCD_FP32_R12 (which link copy is used);
+ *                in_dev and out_dev are internal vectors of that precision
+ *                (lqcd_vector_bytes(ctx, prec) bytes each, must not overlap).
+ * Requires a gauge field (LQCD_ERR_STATE otherwise).  Asynchronous.
+ */
+int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, int prec);
+
+/*
+ * lqcd_apply_A - q = (A + sigma) p on even sites, A = 4 m^2 - D_eo D_oe (Section 3.2),
+ * internal vectors of precision prec (FP64, FP32 or FP32_R12).  If pq_host is not
+ * NULL the call synchronises and stores Re<p, q> (FP64 accumulation) there.
+ */
+int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
+
+/*
+ * lqcd_neighbour_table - the geometry the kernels compute on the fly, written out.
+ *   fwd_dev, bwd_dev : int32 [2 parities][4 mu][Vh] half index of x +- mu
+ *   sign_dev         : int32 [2][4][Vh] eta_mu(x) times the boundary sign of the
+ *                      forward hop x -> x + mu (the sign folded into link U_mu(x))
+ * Any of the pointers may be NULL.  Asynchronous.
+ */
+int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_dev);
+
+/* Solver options (lqcd_set_option keys).  Reliable updates (mixed modes) run at the end of a
+ * 10-iteration window once one is due: after LQCD_OPT_RELIABLE_INTERVAL iterations, or earlier when
+ * the iterated residual fell by LQCD_OPT_RELIABLE_DELTA (so that the FP32 drift stays small
+ * against the residual it replaces). */
+#define LQCD_OPT_RELIABLE_INTERVAL 1 /* most iterations between FP64 reliable updates (mixed modes; default 100) */
+#define LQCD_OPT_REFINE 2            /* 1 = refine every shift to the true residual (default), 0 = off */
+#define LQCD_OPT_BATCH 3             /* iterations per captured CUDA graph launch (default 32) */
+#define LQCD_OPT_USE_GRAPH 4         /* 1 = capture iteration batches in CUDA graphs (default), 0 = plain launches */
+#define LQCD_OPT_DSLASH_TPS 5        /* threads per output site in the FP32 Dslash (1, 2, 4 or 8; 0 = tuned) */
+#define LQCD_OPT_RELIABLE_DELTA 6    /* a reliable update is also due once |r| drops below delta times its
+                                        largest value since the last one (default 0.1) */
+int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
+
+/*
+ * mshift_cg - shifted conjugate gradient for (A + d_k) x_k = b, k = 1..n, and the
+ * rational application y = c0 b + sum_k c_k x_k (Eq. ratapprx, Section 4; shifted
+ * CG of ref. [mcg] with base system at the smallest shift).
+ *   shifts     : host double[n], d_k >= 0 (not necessarily sorted)
+ *   residues   : host double[n], c_k (may be NULL when y_dev is NULL)
+ *   n          : 1 <= n <= LQCD_MAX_SHIFTS
+ *   c0         : constant term of the rational function
+ *   b_dev      : device complex128 [Vh][3] on even sites (canonical)
+ *   x_dev      : host array of n device pointers to complex128 [Vh][3] outputs,
+ *                or NULL (then only y is produced); entries may not be NULL
+ *   y_dev      : device complex128 [Vh][3] output or NULL
+ *   tol        : requested relative residual; the call returns LQCD_OK only when
+ *                the FP64 true residual |b - (A+d_k)x_k|/|b| <= tol for every k
+ *   maxiter    : cap on base iterations (and on each refinement solve)
+ *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12 or LQCD_FP16FIX
+ *                (FP32 arithmetic, FP64 dot products, solution accumulation,
+ *                reliable updates and final residuals)
+ *   stats      : host lqcd_solve_stats or NULL
+ * Synchronises the context stream before returning.  b = 0 gives x_k = 0, y = 0.
+ */
+int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0,
+              const double* b_dev, double* const* x_dev, double* y_dev, double tol, int maxiter, int prec,
+              lqcd_solve_stats* stats);
+
+/*
+ * lqcd_rational_coeffs - host-side coefficients of Eq. ratapprx (Appendix):
+ * best relative-error rational approximation of type (n, n) to x^power on [lo, hi],
+ *   r(x) = c0 + sum_{k<n} residues[k] / (x + poles[k]).
+ * power = -0.5 uses Zolotarev's closed form; other powers in (-1, 1) use a Remez
+ * exchange.  err (may be NULL) receives max |r(x)/x^power - 1| on [lo, hi].
+ * Host memory only; no context needed.  LQCD_ERR_ARG for lo <= 0, hi <= lo,
+ * n < 1 or n > LQCD_MAX_SHIFTS; LQCD_ERR_NOT_CONVERGED if the exchange fails.
+ */
+int lqcd_rational_coeffs(double power, double lo, double hi, int n, double* c0, double* residues, double* poles,
+                         double* err);
+
+/* Number of kernels the library has launched on this context (graph nodes counted). */
+long long lqcd_launch_count(const lqcd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,1 +1,244 @@
-"""GB300-native even-odd staggered multi-shift CG (placeholder, filled in below)."""
+"""GB300-native even-odd staggered multi-shift CG (Gupta & Majumdar, arXiv:1710.09178, Sections 3-4).
+
+Thin ctypes binding over liblqcd.so (include/lqcd.h).  Every step of the path
+runs in the library's CUDA kernels; this module only marshals arguments
+(torch tensors -> device pointers, stream handles, the stats struct).  There is
+no CPU fallback: if the library is missing, every call raises.
+
+    from paper_1710_09178_gb300 import Context, mshift_cg, dslash_eo
+    ctx = Context((32, 32, 32, 8), mass=0.02)
+    ctx.set_gauge(U)                      # complex128 cuda tensor (V, 4, 3, 3)
+    st = mshift_cg(ctx, shifts, residues, c0, b, xs, y, tol=1e-10, prec=FP32)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblqcd.so")
+
+LQCD_OK = 0
+LQCD_ERR_ARG = 1
+LQCD_ERR_DIMS = 2
+LQCD_ERR_CUDA = 3
+LQCD_ERR_NOT_CONVERGED = 4
+LQCD_ERR_NONFINITE = 5
+LQCD_ERR_STATE = 6
+
+FP64 = 0
+FP32 = 1
+FP32_R12 = 2
+FP16FIX = 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_r12": FP32_R12, "fp16fix": FP16FIX}
+
+OPT_RELIABLE_INTERVAL = 1
+OPT_REFINE = 2
+OPT_BATCH = 3
+OPT_USE_GRAPH = 4
+OPT_DSLASH_TPS = 5
+OPT_RELIABLE_DELTA = 6
+
+MAX_SHIFTS = 32
+
+EXPORTED = [
+    "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
+    "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
+    "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count",
+]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("reliable_updates", ctypes.c_int),
+        ("refine_iterations", ctypes.c_int),
+        ("refined_shifts", ctypes.c_int),
+        ("kernel_launches", ctypes.c_int),
+        ("n_shifts", ctypes.c_int),
+        ("true_residual", ctypes.c_double * MAX_SHIFTS),
+        ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        n = self.n_shifts
+        return dict(iterations=self.iterations, reliable_updates=self.reliable_updates,
+                    refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
+                    kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms)
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lqcd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblqcd.so (built by build.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "lqcd_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), d, vp]),
+        "lqcd_destroy": (i, [vp]),
+        "lqcd_last_error": (ctypes.c_char_p, [vp]),
+        "lqcd_set_stream": (i, [vp, vp]),
+        "lqcd_set_gauge": (i, [vp, vp]),
+        "lqcd_vector_bytes": (ctypes.c_size_t, [vp, i]),
+        "lqcd_pack_vector": (i, [vp, vp, i, vp]),
+        "lqcd_unpack_vector": (i, [vp, vp, vp, i]),
+        "dslash_eo": (i, [vp, vp, vp, i, i]),
+        "lqcd_apply_A": (i, [vp, vp, vp, d, i, ctypes.POINTER(d)]),
+        "lqcd_neighbour_table": (i, [vp, vp, vp, vp]),
+        "lqcd_set_option": (i, [vp, i, d]),
+        "mshift_cg": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), i, d, vp, ctypes.POINTER(vp), vp, d, i, i,
+                          ctypes.POINTER(SolveStats)]),
+        "lqcd_rational_coeffs": (i, [d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                                     ctypes.POINTER(d)]),
+        "lqcd_launch_count": (ctypes.c_longlong, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _current_stream():
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Context:
+    """Owns one lqcd_ctx (device workspace and internal gauge copies) for a lattice."""
+
+    def __init__(self, dims, mass, stream=None):
+        lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        self.mass = float(mass)
+        self.V = int(np.prod(self.dims))
+        self.Vh = self.V // 2
+        arr = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        rc = lib.lqcd_create(ctypes.byref(h), arr, self.mass, stream if stream is not None else _current_stream())
+        if rc != LQCD_OK:
+            raise LqcdError(rc, f"lqcd_create failed for dims {self.dims}")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().lqcd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != LQCD_OK:
+            msg = load_library().lqcd_last_error(self.handle)
+            raise LqcdError(rc, msg.decode() if msg else "")
+        return rc
+
+    def set_stream(self, stream=None):
+        return self.check(load_library().lqcd_set_stream(self.handle, stream if stream is not None
+                                                         else _current_stream()))
+
+    def set_gauge(self, U):
+        """U: complex128 cuda tensor of shape (V, 4, 3, 3), canonical layout."""
+        assert tuple(U.shape) == (self.V, 4, 3, 3) and U.is_contiguous()
+        return self.check(load_library().lqcd_set_gauge(self.handle, _ptr(U)))
+
+    def vector_bytes(self, prec):
+        return int(load_library().lqcd_vector_bytes(self.handle, prec))
+
+    def new_vector(self, prec):
+        """Uninitialised internal vector of precision prec (uint8 cuda tensor)."""
+        import torch
+
+        return torch.empty(self.vector_bytes(prec), dtype=torch.uint8, device="cuda")
+
+    def pack(self, dst, prec, src):
+        return self.check(load_library().lqcd_pack_vector(self.handle, _ptr(dst), prec, _ptr(src)))
+
+    def unpack(self, dst, src, prec):
+        return self.check(load_library().lqcd_unpack_vector(self.handle, _ptr(dst), _ptr(src), prec))
+
+    def apply_A(self, q, p, sigma, prec, want_dot=False):
+        pq = ctypes.c_double(0.0)
+        self.check(load_library().lqcd_apply_A(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
+                                               ctypes.byref(pq) if want_dot else None))
+        return pq.value if want_dot else None
+
+    def neighbour_table(self, fwd, bwd, sign):
+        return self.check(load_library().lqcd_neighbour_table(self.handle, _ptr(fwd), _ptr(bwd), _ptr(sign)))
+
+    def set_option(self, key, value):
+        return self.check(load_library().lqcd_set_option(self.handle, int(key), float(value)))
+
+    def launch_count(self):
+        return int(load_library().lqcd_launch_count(self.handle))
+
+
+def dslash_eo(ctx: Context, out, in_, out_parity: int, prec: int):
+    """out = D_oe in (out_parity=1) or D_eo in (out_parity=0); internal vectors of precision prec."""
+    return ctx.check(load_library().dslash_eo(ctx.handle, _ptr(out), _ptr(in_), int(out_parity), int(prec)))
+
+
+def mshift_cg(ctx: Context, shifts, residues, c0, b, xs=None, y=None, tol=1e-10, maxiter=20000, prec=FP32,
+              raise_on_error=True):
+    """Shifted CG (A + d_k) x_k = b for every shift and y = c0 b + sum_k c_k x_k.
+
+    b, xs[k], y: complex128 cuda tensors of shape (Vh, 3) (canonical layout).
+    Returns (status, stats dict).
+    """
+    lib = load_library()
+    n = len(shifts)
+    sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
+    rs = (ctypes.c_double * n)(*[float(c) for c in residues]) if residues is not None else None
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs]) if xs is not None else None
+    st = SolveStats()
+    rc = lib.mshift_cg(ctx.handle, sh, rs, n, float(c0), _ptr(b), xp, _ptr(y), float(tol), int(maxiter),
+                       int(prec), ctypes.byref(st))
+    if raise_on_error and rc not in (LQCD_OK,):
+        ctx.check(rc)
+    return rc, st.as_dict()
+
+
+def lqcd_rational_coeffs(power, lo, hi, n):
+    """(c0, residues, poles, err) of the best relative (n, n) rational approximation of x^power on [lo, hi]."""
+    lib = load_library()
+    c0 = ctypes.c_double()
+    err = ctypes.c_double()
+    res = (ctypes.c_double * n)()
+    pol = (ctypes.c_double * n)()
+    rc = lib.lqcd_rational_coeffs(float(power), float(lo), float(hi), int(n), ctypes.byref(c0), res, pol,
+                                  ctypes.byref(err))
+    if rc != LQCD_OK:
+        raise LqcdError(rc, f"lqcd_rational_coeffs({power}, {lo}, {hi}, {n}) failed")
+    return c0.value, np.array(res[:]), np.array(pol[:]), err.value
+
+
+def rational_coeffs(power, lo, hi, n):
+    return lqcd_rational_coeffs(power, lo, hi, n)

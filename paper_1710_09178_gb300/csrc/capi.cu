@@ -1,0 +1,254 @@
+// capi.cu - the extern "C" entry points of liblqcd.so (declared in include/lqcd.h):
+// argument checking, context and gauge-field management, and dispatch to the
+// kernels.  Errors come back as status codes with a message in the context.
+#include <string.h>
+
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lqcd {
+
+Geom make_geom(const lqcd_ctx* ctx) {
+  Geom g;
+  g.nx = ctx->dims[0];
+  g.ny = ctx->dims[1];
+  g.nz = ctx->dims[2];
+  g.nt = ctx->dims[3];
+  g.vh = (int)ctx->Vh;
+  g.nxy = g.nx * g.ny;
+  g.nxyz = g.nxy * g.nz;
+  return g;
+}
+
+int fail(lqcd_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+int cuda_check(lqcd_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LQCD_OK;
+  return fail(ctx, LQCD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool prec_valid(int prec) {
+  return prec == LQCD_FP64 || prec == LQCD_FP32 || prec == LQCD_FP32_R12 || prec == LQCD_FP16FIX;
+}
+
+static int ensure_scratch(lqcd_ctx* ctx) {
+  if (ctx->scalars) return LQCD_OK;
+  cudaError_t e;
+  size_t nparts = (size_t)dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8) + 64;
+  if ((e = cudaMalloc(&ctx->partials, sizeof(double) * nparts)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->tickets, sizeof(unsigned) * 8)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
+  if ((e = cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 8, ctx->stream)) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMemset");
+  if ((e = cudaMalloc(&ctx->scalars, sizeof(double) * 8)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
+  if ((e = cudaMalloc(&ctx->tmp_odd, 48 * (size_t)ctx->Vh)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
+  return LQCD_OK;
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_create(lqcd_ctx** out, const int dims[4], double mass, void* stream) {
+  if (!out) return LQCD_ERR_ARG;
+  *out = nullptr;
+  if (!dims) return LQCD_ERR_ARG;
+  long long V = 1;
+  for (int d = 0; d < 4; ++d) {
+    if (dims[d] <= 0 || dims[d] % 2) return LQCD_ERR_DIMS;
+    V *= dims[d];
+  }
+  if (V / 2 > (1LL << 30) / 8) return LQCD_ERR_DIMS;  // 32-bit site indices with room for 8 threads per site
+  if (!(mass >= 0.0)) return LQCD_ERR_ARG;
+  lqcd_ctx* c = new lqcd_ctx();
+  for (int d = 0; d < 4; ++d) c->dims[d] = dims[d];
+  c->V = V;
+  c->Vh = V / 2;
+  c->mass = mass;
+  c->stream = static_cast<cudaStream_t>(stream);
+  *out = c;
+  return LQCD_OK;
+}
+
+int lqcd_destroy(lqcd_ctx* ctx) {
+  if (!ctx) return LQCD_OK;
+  free_workspace(ctx);
+  void* bufs[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->partials, ctx->tickets, ctx->scalars,
+                  ctx->tmp_odd};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete ctx;
+  return LQCD_OK;
+}
+
+const char* lqcd_last_error(const lqcd_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int lqcd_set_stream(lqcd_ctx* ctx, void* stream) {
+  if (!ctx) return LQCD_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return LQCD_OK;
+}
+
+int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!U_dev) return fail(ctx, LQCD_ERR_ARG, "lqcd_set_gauge: null gauge pointer");
+  Geom g = make_geom(ctx);
+  GaugeCopies& gc = ctx->gauge;
+  cudaError_t e;
+  size_t vh = (size_t)ctx->Vh;
+  if (!gc.u64 && (e = cudaMalloc(&gc.u64, 2 * 4 * 9 * vh * sizeof(double2))) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge fp64)");
+  if (!gc.u32 && (e = cudaMalloc(&gc.u32, 2 * 4 * 18 * vh * sizeof(float))) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge fp32)");
+  if (!gc.u12 && (e = cudaMalloc(&gc.u12, 2 * 4 * 3 * vh * sizeof(float4))) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge r12)");
+  e = launch_pack_gauge(g, reinterpret_cast<const double2*>(U_dev), gc, ctx->stream);
+  ctx->launches += 1;
+  if (e != cudaSuccess) return cuda_check(ctx, e, "pack_gauge");
+  gc.loaded = true;
+  return LQCD_OK;
+}
+
+size_t lqcd_vector_bytes(const lqcd_ctx* ctx, int prec) {
+  if (!ctx) return 0;
+  switch (prec) {
+    case LQCD_FP64: return 48 * (size_t)ctx->Vh;
+    case LQCD_FP32:
+    case LQCD_FP32_R12: return 24 * (size_t)ctx->Vh;
+    case LQCD_FP16FIX: return 16 * (size_t)ctx->Vh;
+  }
+  return 0;
+}
+
+int lqcd_pack_vector(lqcd_ctx* ctx, void* dst_dev, int prec, const double* src_dev) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!dst_dev || !src_dev || !prec_valid(prec)) return fail(ctx, LQCD_ERR_ARG, "lqcd_pack_vector: bad argument");
+  cudaError_t e = launch_pack_vector(make_geom(ctx), dst_dev, prec, reinterpret_cast<const double2*>(src_dev),
+                                     ctx->stream);
+  ctx->launches += 1;
+  return cuda_check(ctx, e, "pack_vector");
+}
+
+int lqcd_unpack_vector(lqcd_ctx* ctx, double* dst_dev, const void* src_dev, int prec) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!dst_dev || !src_dev || !prec_valid(prec)) return fail(ctx, LQCD_ERR_ARG, "lqcd_unpack_vector: bad argument");
+  cudaError_t e = launch_unpack_vector(make_geom(ctx), reinterpret_cast<double2*>(dst_dev), src_dev, prec,
+                                       ctx->stream);
+  ctx->launches += 1;
+  return cuda_check(ctx, e, "unpack_vector");
+}
+
+int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, int prec) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!out_dev || !in_dev || (out_parity != 0 && out_parity != 1) || !prec_valid(prec) || prec == LQCD_FP16FIX)
+    return fail(ctx, LQCD_ERR_ARG, "dslash_eo: bad argument");
+  if (out_dev == in_dev) return fail(ctx, LQCD_ERR_ARG, "dslash_eo: output must not alias the input");
+  if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "dslash_eo: no gauge field loaded");
+  DslashArgs a;
+  a.out = out_dev;
+  a.in = in_dev;
+  a.out_parity = out_parity;
+  a.prec = prec;
+  a.tps = ctx->dslash_tps;
+  int nl = 0;
+  cudaError_t e = launch_dslash(make_geom(ctx), ctx->gauge, a, ctx->stream, &nl);
+  ctx->launches += nl;
+  return cuda_check(ctx, e, "dslash_eo");
+}
+
+int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!q_dev || !p_dev || !prec_valid(prec) || prec == LQCD_FP16FIX || q_dev == p_dev)
+    return fail(ctx, LQCD_ERR_ARG, "lqcd_apply_A: bad argument");
+  if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_apply_A: no gauge field loaded");
+  int rc = ensure_scratch(ctx);
+  if (rc != LQCD_OK) return rc;
+  Geom g = make_geom(ctx);
+  DslashArgs a;
+  a.out = ctx->tmp_odd;
+  a.in = p_dev;
+  a.out_parity = 1;
+  a.prec = prec;
+  a.tps = ctx->dslash_tps;
+  int nl = 0;
+  cudaError_t e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A");
+  DslashArgs b = a;
+  b.out = q_dev;
+  b.in = ctx->tmp_odd;
+  b.out_parity = 0;
+  b.epi = Epi::AApply;
+  b.a = 4.0 * ctx->mass * ctx->mass + sigma;
+  b.aux = p_dev;
+  b.dot_out = ctx->scalars;
+  b.partials = ctx->partials;
+  b.ticket = ctx->tickets;
+  e = launch_dslash(g, ctx->gauge, b, ctx->stream, &nl);
+  ctx->launches += nl;
+  if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A");
+  if (pq_host) {
+    e = cudaMemcpyAsync(pq_host, ctx->scalars, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A readback");
+  }
+  return LQCD_OK;
+}
+
+int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_dev) {
+  if (!ctx) return LQCD_ERR_ARG;
+  cudaError_t e = launch_neighbour_table(make_geom(ctx), fwd_dev, bwd_dev, sign_dev, ctx->stream);
+  ctx->launches += 1;
+  return cuda_check(ctx, e, "neighbour_table");
+}
+
+int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
+  if (!ctx) return LQCD_ERR_ARG;
+  int v = (int)value;
+  switch (key) {
+    case LQCD_OPT_RELIABLE_INTERVAL:
+      if (v < 1) return fail(ctx, LQCD_ERR_ARG, "reliable interval must be >= 1");
+      ctx->reliable_interval = v;
+      break;
+    case LQCD_OPT_REFINE: ctx->refine = v ? 1 : 0; break;
+    case LQCD_OPT_RELIABLE_DELTA:
+      if (!(value > 0.0 && value < 1.0)) return fail(ctx, LQCD_ERR_ARG, "reliable delta must be in (0, 1)");
+      ctx->reliable_delta = value;
+      break;
+    case LQCD_OPT_BATCH:
+      if (v < 1) return fail(ctx, LQCD_ERR_ARG, "batch must be >= 1");
+      ctx->batch = v;
+      break;
+    case LQCD_OPT_USE_GRAPH: ctx->use_graph = v ? 1 : 0; break;
+    case LQCD_OPT_DSLASH_TPS:
+      if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return fail(ctx, LQCD_ERR_ARG, "tps must be 0,1,2,4,8");
+      ctx->dslash_tps = v;
+      break;
+    default: return fail(ctx, LQCD_ERR_ARG, "unknown option");
+  }
+  free_workspace(ctx);  // captured graphs depend on the options
+  return LQCD_OK;
+}
+
+int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
+              double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (!shifts || n < 1 || n > LQCD_MAX_SHIFTS || !b_dev || !prec_valid(prec) || maxiter < 1 || !(tol > 0.0))
+    return fail(ctx, LQCD_ERR_ARG, "mshift_cg: bad argument");
+  if (y_dev && !residues) return fail(ctx, LQCD_ERR_ARG, "mshift_cg: y requested without residues");
+  for (int k = 0; k < n; ++k) {
+    if (!(shifts[k] >= 0.0) || !isfinite(shifts[k])) return fail(ctx, LQCD_ERR_ARG, "mshift_cg: shifts must be >= 0");
+    if (x_dev && !x_dev[k]) return fail(ctx, LQCD_ERR_ARG, "mshift_cg: null x_k pointer");
+  }
+  if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "mshift_cg: no gauge field loaded");
+  return run_mshift(ctx, shifts, residues, n, c0, b_dev, x_dev, y_dev, tol, maxiter, prec, stats);
+}
+
+long long lqcd_launch_count(const lqcd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

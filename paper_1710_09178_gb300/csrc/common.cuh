@@ -1,0 +1,360 @@
+// common.cuh - device-side building blocks shared by the kernels of liblqcd.so:
+// lattice geometry computed from the half-lattice index, complex 3x3 algebra,
+// loads and stores of the internal link and vector layouts, and deterministic
+// block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lqcd.h"
+
+namespace lqcd {
+
+// ---------------------------------------------------------------------------
+// Geometry (Section 2 site address; Section 3.2 even/odd split).
+// A site of parity p (= (x+y+z+t) & 1) with half-lattice index i has address
+// l = 2i or 2i+1: with all extents even, the pair (2i, 2i+1) shares y, z, t and
+// holds one site of each parity.
+// ---------------------------------------------------------------------------
+struct Geom {
+  int nx, ny, nz, nt;
+  int vh;   // V/2
+  int nxy;  // nx*ny
+  int nxyz; // nx*ny*nz
+};
+
+struct Site {
+  int x, y, z, t, l;
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int parity, int i) {
+  int l0 = 2 * i;
+  int x0 = l0 % g.nx;
+  int r = l0 / g.nx;
+  int y = r % g.ny;
+  r /= g.ny;
+  int z = r % g.nz;
+  int t = r / g.nz;
+  int dx = (y + z + t + parity) & 1;  // x0 is even, so x = x0 + dx has the requested parity
+  Site s;
+  s.x = x0 + dx;
+  s.y = y;
+  s.z = z;
+  s.t = t;
+  s.l = l0 + dx;
+  return s;
+}
+
+// address of x + mu (fwd) or x - mu (bwd), periodic wrap in every direction
+__device__ __forceinline__ int neighbour_fwd(const Geom& g, const Site& s, int mu) {
+  switch (mu) {
+    case 0: return (s.x == g.nx - 1) ? s.l - (g.nx - 1) : s.l + 1;
+    case 1: return (s.y == g.ny - 1) ? s.l - (g.ny - 1) * g.nx : s.l + g.nx;
+    case 2: return (s.z == g.nz - 1) ? s.l - (g.nz - 1) * g.nxy : s.l + g.nxy;
+    default: return (s.t == g.nt - 1) ? s.l - (g.nt - 1) * g.nxyz : s.l + g.nxyz;
+  }
+}
+
+__device__ __forceinline__ int neighbour_bwd(const Geom& g, const Site& s, int mu) {
+  switch (mu) {
+    case 0: return (s.x == 0) ? s.l + (g.nx - 1) : s.l - 1;
+    case 1: return (s.y == 0) ? s.l + (g.ny - 1) * g.nx : s.l - g.nx;
+    case 2: return (s.z == 0) ? s.l + (g.nz - 1) * g.nxy : s.l - g.nxy;
+    default: return (s.t == 0) ? s.l + (g.nt - 1) * g.nxyz : s.l - g.nxyz;
+  }
+}
+
+// eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z)
+__device__ __forceinline__ int eta_odd(const Site& s, int mu) {
+  switch (mu) {
+    case 0: return 0;
+    case 1: return s.x & 1;
+    case 2: return (s.x + s.y) & 1;
+    default: return (s.x + s.y + s.z) & 1;
+  }
+}
+
+// sign carried by link U_mu(x): eta_mu(x) times -1 when the link crosses the t boundary
+__device__ __forceinline__ int link_sign_fwd(const Geom& g, const Site& s, int mu) {
+  int neg = eta_odd(s, mu) ^ ((mu == 3 && s.t == g.nt - 1) ? 1 : 0);
+  return neg ? -1 : 1;
+}
+
+// sign carried by link U_mu(x - mu): eta_mu(x - mu) = eta_mu(x); boundary when t(x) == 0
+__device__ __forceinline__ int link_sign_bwd(const Geom& g, const Site& s, int mu) {
+  int neg = eta_odd(s, mu) ^ ((mu == 3 && s.t == 0) ? 1 : 0);
+  return neg ? -1 : 1;
+}
+
+// ---------------------------------------------------------------------------
+// Complex helpers (T = float or double)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cplx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmake(T r, T i) {
+  Cplx<T> c;
+  c.re = r;
+  c.im = i;
+  return c;
+}
+
+// acc += a * b
+template <typename T>
+__device__ __forceinline__ void cmac(Cplx<T>& acc, const Cplx<T>& a, const Cplx<T>& b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+
+// acc += conj(a) * b
+template <typename T>
+__device__ __forceinline__ void cmac_conj(Cplx<T>& acc, const Cplx<T>& a, const Cplx<T>& b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+
+template <typename T>
+struct Mat3 {
+  Cplx<T> e[3][3];
+};
+
+template <typename T>
+struct Vec3 {
+  Cplx<T> c[3];
+};
+
+// out += M v
+template <typename T>
+__device__ __forceinline__ void mv_acc(Vec3<T>& out, const Mat3<T>& M, const Vec3<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) cmac(out.c[a], M.e[a][b], v.c[b]);
+  }
+}
+
+// out += M^dagger v  ((M^dagger)_{ab} = conj(M_{ba}))
+template <typename T>
+__device__ __forceinline__ void mdv_acc(Vec3<T>& out, const Mat3<T>& M, const Vec3<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) cmac_conj(out.c[a], M.e[b][a], v.c[b]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Vec3<T> vzero() {
+  Vec3<T> v;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v.c[a] = cmake<T>(0, 0);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Internal vector layouts (one parity, Vh sites)
+//   FP64 : [3][Vh] double2      FP32 : [3][Vh] float2
+//   H16  : [Vh] 16-byte records: int16 q[6] then float scale (component = q * scale)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Vec3<double> load_vec(const double2* __restrict__ v, int i, int vh) {
+  Vec3<double> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double2 d = v[c * vh + i];
+    o.c[c] = cmake(d.x, d.y);
+  }
+  return o;
+}
+
+__device__ __forceinline__ Vec3<float> load_vec(const float2* __restrict__ v, int i, int vh) {
+  Vec3<float> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 d = v[c * vh + i];
+    o.c[c] = cmake(d.x, d.y);
+  }
+  return o;
+}
+
+__device__ __forceinline__ void store_vec(double2* __restrict__ v, int i, int vh, const Vec3<double>& o) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c * vh + i] = make_double2(o.c[c].re, o.c[c].im);
+}
+
+__device__ __forceinline__ void store_vec(float2* __restrict__ v, int i, int vh, const Vec3<float>& o) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[c * vh + i] = make_float2(o.c[c].re, o.c[c].im);
+}
+
+// 16-bit fixed point with per-site scale (record = 16 bytes)
+struct H16Rec {
+  int4 w;  // w.x = q0 | q1 << 16, w.y = q2 | q3 << 16, w.z = q4 | q5 << 16, w.w = float bits of scale
+};
+
+__device__ __forceinline__ float h16_lo(int w) { return (float)(short)(w & 0xffff); }
+__device__ __forceinline__ float h16_hi(int w) { return (float)(short)((unsigned)w >> 16); }
+
+__device__ __forceinline__ Vec3<float> load_vec_h16(const int4* __restrict__ v, int i) {
+  int4 w = v[i];
+  float s = __int_as_float(w.w);
+  Vec3<float> o;
+  o.c[0] = cmake(h16_lo(w.x) * s, h16_hi(w.x) * s);
+  o.c[1] = cmake(h16_lo(w.y) * s, h16_hi(w.y) * s);
+  o.c[2] = cmake(h16_lo(w.z) * s, h16_hi(w.z) * s);
+  return o;
+}
+
+__device__ __forceinline__ int h16_code(float v, float inv) {
+  float q = rintf(__fmul_rn(v, inv));
+  q = fminf(fmaxf(q, -32767.0f), 32767.0f);
+  return (int)q;
+}
+
+__device__ __forceinline__ int h16_pack2(int a, int b) { return (a & 0xffff) | ((b & 0xffff) << 16); }
+
+// n = max |v_i|; q_i = rint(v_i * (32767/n)); s = n/32767 (IEEE float32 division)
+__device__ __forceinline__ void store_vec_h16(int4* __restrict__ v, int i, const Vec3<float>& o) {
+  float n = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) n = fmaxf(n, fmaxf(fabsf(o.c[c].re), fabsf(o.c[c].im)));
+  int4 w;
+  if (n > 0.0f) {
+    float inv = __fdiv_rn(32767.0f, n);
+    float s = __fdiv_rn(n, 32767.0f);
+    w.x = h16_pack2(h16_code(o.c[0].re, inv), h16_code(o.c[0].im, inv));
+    w.y = h16_pack2(h16_code(o.c[1].re, inv), h16_code(o.c[1].im, inv));
+    w.z = h16_pack2(h16_code(o.c[2].re, inv), h16_code(o.c[2].im, inv));
+    w.w = __float_as_int(s);
+  } else {
+    w = make_int4(0, 0, 0, 0);
+  }
+  v[i] = w;
+}
+
+// ---------------------------------------------------------------------------
+// Internal link layouts, per (parity p, direction mu) block of Vh links stored
+// at the site x they start from (U_mu(x), x of parity p):
+//   L64 : [p][mu][9][Vh] double2, row-major complex entries, times 1/2 eta*bc
+//   L32 : [p][mu] { float4 [4][Vh] ; float2 [Vh] }, same entry order, times 1/2 eta*bc
+//   L12 : [p][mu][3][Vh] float4  rows 0 and 1 only, no sign (third row rebuilt)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Mat3<double> load_link64(const double2* __restrict__ U, int p, int mu, int i, int vh) {
+  const double2* b = U + (size_t)(p * 4 + mu) * 9 * vh + i;
+  Mat3<double> M;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    double2 d = b[(size_t)j * vh];
+    M.e[j / 3][j % 3] = cmake(d.x, d.y);
+  }
+  return M;
+}
+
+__device__ __forceinline__ Mat3<float> load_link32(const float* __restrict__ U, int p, int mu, int i, int vh) {
+  const float* blk = U + (size_t)(p * 4 + mu) * 18 * vh;
+  const float4* f4 = reinterpret_cast<const float4*>(blk);
+  const float2* f2 = reinterpret_cast<const float2*>(blk + 16 * (size_t)vh);
+  float4 a = f4[i], b = f4[vh + i], c = f4[2 * vh + i], d = f4[3 * vh + i];
+  float2 e = f2[i];
+  Mat3<float> M;
+  M.e[0][0] = cmake(a.x, a.y);
+  M.e[0][1] = cmake(a.z, a.w);
+  M.e[0][2] = cmake(b.x, b.y);
+  M.e[1][0] = cmake(b.z, b.w);
+  M.e[1][1] = cmake(c.x, c.y);
+  M.e[1][2] = cmake(c.z, c.w);
+  M.e[2][0] = cmake(d.x, d.y);
+  M.e[2][1] = cmake(d.z, d.w);
+  M.e[2][2] = cmake(e.x, e.y);
+  return M;
+}
+
+// rows 0,1 from memory; row 2 = conj(row0 x row1) (exact for SU(3)); then scale by 1/2 * sign
+__device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U, int p, int mu, int i, int vh,
+                                                   float scale) {
+  const float4* blk = U + (size_t)(p * 4 + mu) * 3 * vh;
+  float4 a = blk[i], b = blk[vh + i], c = blk[2 * vh + i];
+  Mat3<float> M;
+  M.e[0][0] = cmake(a.x, a.y);
+  M.e[0][1] = cmake(a.z, a.w);
+  M.e[0][2] = cmake(b.x, b.y);
+  M.e[1][0] = cmake(b.z, b.w);
+  M.e[1][1] = cmake(c.x, c.y);
+  M.e[1][2] = cmake(c.z, c.w);
+  // (r0 x r1)_k = r0_{k+1} r1_{k+2} - r0_{k+2} r1_{k+1}; row 2 is its complex conjugate
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const Cplx<float>& a1 = M.e[0][(k + 1) % 3];
+    const Cplx<float>& a2 = M.e[0][(k + 2) % 3];
+    const Cplx<float>& b1 = M.e[1][(k + 1) % 3];
+    const Cplx<float>& b2 = M.e[1][(k + 2) % 3];
+    float re = a1.re * b2.re - a1.im * b2.im - (a2.re * b1.re - a2.im * b1.im);
+    float im = a1.re * b2.im + a1.im * b2.re - (a2.re * b1.im + a2.im * b1.re);
+    M.e[2][k] = cmake(re, -im);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      M.e[r][c].re *= scale;
+      M.e[r][c].im *= scale;
+    }
+  return M;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions.  Each block reduces in a fixed tree and writes one
+// partial; the last block to finish (atomic ticket) adds the partials in index
+// order, so the result does not depend on block scheduling.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// result valid in every thread; blockDim.x a multiple of 32, at most 1024
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red_smem[32];
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red_smem[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  double t = (l < nw) ? red_smem[l] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+
+// Publish this block's partial; returns true in the one block that finishes last.
+__device__ __forceinline__ bool publish_partial(double* partials, unsigned* ticket, double v) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v;
+    __threadfence();
+    unsigned prev = atomicAdd(ticket, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// In the last block: the sum of all partials in index order (identical in every thread).
+__device__ __forceinline__ double gather_partials(const double* partials, unsigned* ticket) {
+  __threadfence();
+  double v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + b);
+  v = block_sum(v);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return v;
+}
+
+}  // namespace lqcd

@@ -1,0 +1,217 @@
+// dslash.cu - the half-lattice staggered hopping operator (Section 3.2):
+//   out(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) in(x+mu) - U_mu(x-mu)^dagger in(x-mu)]
+// for every x of the output parity, with optional fused epilogues:
+//   AApply : out = a * aux - D in, and the FP64 sum Re<aux, out>   (one half of A = 4m^2 - D_eo D_oe)
+//   Resid  : out = bvec - (a * aux - D in), and the FP64 sum |out|^2 (true residual)
+//
+// Bandwidth-bound gather kernel: each output site reads 8 links (all links once
+// per call) and 8 neighbour vectors (the input vector is small and stays in L2).
+// TPS threads cooperate on one site, each taking 8/TPS of the hops, and combine
+// their partial sums with warp shuffles; more threads per site means more
+// independent loads in flight per SM.
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+#include "solver_dev.cuh"
+
+namespace lqcd {
+
+enum LinkFmt { kL64 = 0, kL32 = 1, kL12 = 2 };
+
+struct KArgs {
+  void* out;
+  const void* in;
+  const void* aux;
+  const void* bvec;
+  double a;
+  const double* a_dev;
+  int out_parity;
+  double* dot_out;
+  SolverDev* solver;
+  const int* done;
+  double* partials;
+  unsigned* ticket;
+  const void* links;
+};
+
+template <int LF>
+struct LinkTraits {
+  typedef float T;
+};
+template <>
+struct LinkTraits<kL64> {
+  typedef double T;
+};
+
+template <int LF>
+__device__ __forceinline__ Mat3<typename LinkTraits<LF>::T> load_link(const void* links, int p, int mu, int i, int vh,
+                                                                      int sign) {
+  if constexpr (LF == kL64) {
+    return load_link64(static_cast<const double2*>(links), p, mu, i, vh);
+  } else if constexpr (LF == kL32) {
+    return load_link32(static_cast<const float*>(links), p, mu, i, vh);
+  } else {
+    return load_link12(static_cast<const float4*>(links), p, mu, i, vh, 0.5f * (float)sign);
+  }
+}
+
+// Which colours lane `sub` of a TPS group stores: TPS = 1 all; TPS = 2 lane 0 -> {0, 2},
+// lane 1 -> {1}; TPS >= 4 lane c -> colour c (lanes 3.. store nothing).
+template <int TPS>
+__device__ __forceinline__ bool lane_writes(int sub, int c) {
+  if (TPS == 1) return true;
+  if (TPS == 2) return sub == 0 ? (c != 1) : (c == 1);
+  return c == sub;
+}
+
+template <int LF, int TPS, int EPI>
+__global__ void __launch_bounds__(256) dslash_kernel(Geom g, KArgs k) {
+  typedef typename LinkTraits<LF>::T T;
+  typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
+  if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
+
+  const int vh = g.vh;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / TPS;
+  const int sub = gt % TPS;
+  const bool valid = i < vh;
+  const int p = k.out_parity;
+  const V2* in = static_cast<const V2*>(k.in);
+
+  Vec3<T> accf = vzero<T>(), accb = vzero<T>();
+  if (valid) {
+    Site s = site_of(g, p, i);
+#pragma unroll
+    for (int h = sub; h < 8; h += TPS) {
+      const int mu = h >> 1;
+      if ((h & 1) == 0) {
+        int j = neighbour_fwd(g, s, mu) >> 1;
+        int sg = (LF == kL12) ? link_sign_fwd(g, s, mu) : 1;
+        Mat3<T> W = load_link<LF>(k.links, p, mu, i, vh, sg);
+        Vec3<T> v = load_vec(in, j, vh);
+        mv_acc(accf, W, v);
+      } else {
+        int j = neighbour_bwd(g, s, mu) >> 1;
+        int sg = (LF == kL12) ? link_sign_bwd(g, s, mu) : 1;
+        Mat3<T> W = load_link<LF>(k.links, 1 - p, mu, j, vh, sg);
+        Vec3<T> v = load_vec(in, j, vh);
+        mdv_acc(accb, W, v);
+      }
+    }
+  }
+  // D in = fwd - bwd, summed over the TPS lanes of the site
+  Vec3<T> d;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T re = accf.c[c].re - accb.c[c].re;
+    T im = accf.c[c].im - accb.c[c].im;
+#pragma unroll
+    for (int o = 1; o < TPS; o <<= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    d.c[c] = cmake(re, im);
+  }
+
+  V2* out = static_cast<V2*>(k.out);
+  const T aval = (EPI != (int)Epi::Plain && k.a_dev) ? (T)*k.a_dev : (T)k.a;
+  T dsite = 0;  // this lane's share of the site's dot product, summed in T, then added in FP64
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!lane_writes<TPS>(sub, c)) continue;
+      size_t o = (size_t)c * vh + i;
+      if constexpr (EPI == (int)Epi::Plain) {
+        V2 w;
+        w.x = d.c[c].re;
+        w.y = d.c[c].im;
+        out[o] = w;
+      } else {
+        V2 ps = static_cast<const V2*>(k.aux)[o];
+        T qre = aval * ps.x - d.c[c].re;
+        T qim = aval * ps.y - d.c[c].im;
+        if constexpr (EPI == (int)Epi::AApply) {
+          dsite += ps.x * qre + ps.y * qim;
+        } else {
+          V2 bv = static_cast<const V2*>(k.bvec)[o];
+          qre = bv.x - qre;
+          qim = bv.y - qim;
+          dsite += qre * qre + qim * qim;
+        }
+        V2 w;
+        w.x = qre;
+        w.y = qim;
+        out[o] = w;
+      }
+    }
+  }
+  if constexpr (EPI != (int)Epi::Plain) {
+    double bs = block_sum((double)dsite);
+    if (publish_partial(k.partials, k.ticket, bs)) {
+      double tot = gather_partials(k.partials, k.ticket);
+      if (k.solver && EPI == (int)Epi::AApply) {
+        solver_alpha_step(k.solver, tot);
+      } else if (threadIdx.x == 0 && k.dot_out) {
+        *k.dot_out = tot;
+      }
+    }
+  }
+}
+
+template <int LF, int TPS>
+static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream_t st, int bs) {
+  long long threads = (long long)g.vh * TPS;
+  unsigned nb = (unsigned)((threads + bs - 1) / bs);
+  switch (epi) {
+    case Epi::Plain: dslash_kernel<LF, TPS, 0><<<nb, bs, 0, st>>>(g, k); break;
+    case Epi::AApply: dslash_kernel<LF, TPS, 1><<<nb, bs, 0, st>>>(g, k); break;
+    case Epi::Resid: dslash_kernel<LF, TPS, 2><<<nb, bs, 0, st>>>(g, k); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int LF>
+static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cudaStream_t st) {
+  const int bs = 128;
+  switch (tps) {
+    case 1: return launch_tps<LF, 1>(g, k, epi, st, bs);
+    case 2: return launch_tps<LF, 2>(g, k, epi, st, bs);
+    case 4: return launch_tps<LF, 4>(g, k, epi, st, bs);
+    default: return launch_tps<LF, 8>(g, k, epi, st, bs);
+  }
+}
+
+static int default_tps(int prec) { return prec == LQCD_FP64 ? 1 : 2; }
+
+int dslash_grid_blocks(const Geom& g, int prec, int tps) {
+  if (tps <= 0) tps = default_tps(prec);
+  long long threads = (long long)g.vh * tps;
+  return (int)((threads + 127) / 128);
+}
+
+cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch) {
+  KArgs k;
+  k.out = a.out;
+  k.in = a.in;
+  k.aux = a.aux;
+  k.bvec = a.bvec;
+  k.a = a.a;
+  k.a_dev = a.a_dev;
+  k.out_parity = a.out_parity;
+  k.dot_out = a.dot_out;
+  k.solver = a.solver;
+  k.done = a.done;
+  k.partials = a.partials;
+  k.ticket = a.ticket;
+  int tps = a.tps > 0 ? a.tps : default_tps(a.prec);
+  if (tps != 1 && tps != 2 && tps != 4 && tps != 8) return cudaErrorInvalidValue;
+  if (nlaunch) *nlaunch += 1;
+  switch (a.prec) {
+    case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, st);
+    case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, st);
+    default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st);
+  }
+}
+
+}  // namespace lqcd

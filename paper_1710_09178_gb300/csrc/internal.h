@@ -1,0 +1,126 @@
+// internal.h - host-side declarations shared by the translation units of liblqcd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "lqcd.h"
+
+namespace lqcd {
+
+struct Geom;
+
+// Device-resident state of one shifted-CG solve (scalars, per-shift recurrences
+// and the coefficients of the pending window of shift-vector updates).
+constexpr int kMaxShifts = LQCD_MAX_SHIFTS;
+constexpr int kWindow = 10;  // iterations folded into one update of x_k, p_k
+
+struct SolverDev {
+  double rr;       // |r|^2 of the current base residual
+  double bb;       // |b|^2
+  double stop2;    // tol^2 |b|^2: shift k stops when zeta_k^2 |r|^2 <= stop2
+  double alpha, alpha_prev, beta, beta_prev;
+  double pq;
+  double a_diag;   // 4 m^2 + sigma_0
+  int iter;
+  int done;        // 1: every shift stopped (or error); iteration kernels return at entry
+  int status;      // LQCD_OK or LQCD_ERR_NONFINITE
+  int n;
+  int m;           // iterations accumulated in the pending window
+  int n_active;
+  int first;       // pending window is the first of the solve (p_k0 = b, x_k0 = 0)
+  int maxiter;     // the beta step sets done once iter reaches it
+  // reliable updates: due when ru_interval iterations have passed since the last one, or when
+  // |r|^2 fell below ru_delta2 times its largest value since then; ru_skip = !due || done
+  int ru_interval;
+  int iter_ru;
+  int ru_skip;
+  double ru_delta2;
+  double rr_ru_max;
+  unsigned ticket[4];
+  double s[kMaxShifts];  // sigma_k - sigma_0
+  double zeta[kMaxShifts], zeta_prev[kMaxShifts], zeta_new[kMaxShifts];
+  int active[kMaxShifts];   // shift still iterating
+  int wactive[kMaxShifts];  // shift takes part in the pending window
+  // pending window: p_k = P p_k0 + sum_i pi_i R_i,  x_k = x_k0 + X p_k0 + sum_i chi_i R_i
+  double P[kMaxShifts], X[kMaxShifts];
+  double pi[kMaxShifts][kWindow], chi[kMaxShifts][kWindow];
+  double scal[kMaxShifts + 4];  // reduction results of auxiliary kernels
+};
+
+struct GaugeCopies {
+  double2* u64 = nullptr;  // [2][4][9][Vh] double2, 1/2 eta*bc folded in
+  float* u32 = nullptr;    // [2][4][18][Vh] floats (float4 x4 + float2), 1/2 eta*bc folded in
+  float4* u12 = nullptr;   // [2][4][3][Vh] float4, rows 0-1, no sign
+  bool loaded = false;
+};
+
+struct Workspace;
+
+}  // namespace lqcd
+
+struct lqcd_ctx {
+  int dims[4];
+  long long V = 0, Vh = 0;
+  double mass = 0;
+  cudaStream_t stream = nullptr;
+  lqcd::GaugeCopies gauge;
+  std::string last_error;
+  long long launches = 0;
+  // solver options
+  int reliable_interval = 100;
+  double reliable_delta = 0.1;
+  int refine = 1;
+  int batch = 20;
+  int use_graph = 1;
+  int dslash_tps = 0;
+  lqcd::Workspace* ws = nullptr;
+  double* partials = nullptr;  // reduction scratch, one double per block
+  void* tmp_odd = nullptr;     // odd-parity temporary of lqcd_apply_A (sized for FP64)
+  unsigned* tickets = nullptr;  // reduction tickets for stand-alone reductions
+  double* scalars = nullptr;    // device scalars for stand-alone reductions
+};
+
+namespace lqcd {
+
+Geom make_geom(const lqcd_ctx* ctx);
+int fail(lqcd_ctx* ctx, int code, const std::string& msg);
+int cuda_check(lqcd_ctx* ctx, cudaError_t e, const char* what);
+
+// pack.cu
+cudaError_t launch_pack_gauge(const Geom& g, const double2* U, GaugeCopies& gc, cudaStream_t st);
+cudaError_t launch_pack_vector(const Geom& g, void* dst, int prec, const double2* src, cudaStream_t st);
+cudaError_t launch_unpack_vector(const Geom& g, double2* dst, const void* src, int prec, cudaStream_t st);
+cudaError_t launch_neighbour_table(const Geom& g, int* fwd, int* bwd, int* sign, cudaStream_t st);
+
+// dslash.cu
+enum class Epi { Plain = 0, AApply = 1, Resid = 2 };
+struct DslashArgs {
+  void* out = nullptr;        // output vector (parity out_parity)
+  const void* in = nullptr;   // input vector (other parity)
+  int out_parity = 0;
+  int prec = LQCD_FP32;       // link copy / vector precision
+  int tps = 0;                // threads per site (FP32 paths), 0 = default
+  // AApply: out = a * aux - D in, dot = Re<aux, out>;  Resid: out = bvec - (a * aux - D in), dot = |out|^2
+  Epi epi = Epi::Plain;
+  double a = 0;
+  const double* a_dev = nullptr; // if set, a is read from device memory (solver state) at run time
+  const void* aux = nullptr;
+  const void* bvec = nullptr;
+  double* dot_out = nullptr;     // where the reduced scalar goes (AApply without solver, Resid)
+  SolverDev* solver = nullptr;   // AApply inside a solve: last block runs the alpha step
+  const int* done = nullptr;     // if non-null and *done, the kernel returns at entry
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+};
+cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
+int dslash_grid_blocks(const Geom& g, int prec, int tps);
+
+// solver.cu
+int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
+               double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats);
+void free_workspace(lqcd_ctx* ctx);
+
+}  // namespace lqcd

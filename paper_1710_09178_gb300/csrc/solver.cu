@@ -1,0 +1,838 @@
+// solver.cu - shifted conjugate gradient on the GPU (Section 4, ref. [mcg]) with
+// mixed-precision storage, FP64 reliable updates and per-shift refinement.
+//
+// One base iteration is four kernels, all enqueued without host round trips:
+//   1. tmp = D_oe p                                          (dslash.cu)
+//   2. q = (4m^2 + sigma_0) p - D_eo tmp, (p, q) -> alpha step (dslash.cu epilogue + solver_dev.cuh)
+//   3. r -= alpha q, R[m] = r, (r, r) -> beta step           (r_update_kernel)
+//   4. p = r + beta p                                        (p_update_kernel)
+// Every kWindow iterations the window kernel applies the pending x_k / p_k
+// updates of all shifts at once (flush_kernel): each shift vector is read and
+// written once per window instead of once per iteration, which is what makes
+// the multi-shift update (the heaviest loop of the shifted CG in Section 7)
+// cheap.  Iteration batches are captured in CUDA graphs; kernels return at entry
+// once the device-side `done` flag is set, so the host only polls a flag per batch.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "solver_dev.cuh"
+
+namespace lqcd {
+
+// storage formats of the shifted Krylov vectors p_k and the residual window R
+enum SFmt { kS64 = 0, kS32 = 1, kS16 = 2 };
+
+template <typename T>
+__device__ __forceinline__ Vec3<T> to_t(const Vec3<double>& v) {
+  Vec3<T> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o.c[c] = cmake((T)v.c[c].re, (T)v.c[c].im);
+  return o;
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> to_t(const Vec3<float>& v) {
+  Vec3<T> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o.c[c] = cmake((T)v.c[c].re, (T)v.c[c].im);
+  return o;
+}
+
+template <int SF, typename T>
+__device__ __forceinline__ Vec3<T> load_s(const void* base, int i, int vh) {
+  if constexpr (SF == kS64) return to_t<T>(load_vec(static_cast<const double2*>(base), i, vh));
+  else if constexpr (SF == kS32) return to_t<T>(load_vec(static_cast<const float2*>(base), i, vh));
+  else return to_t<T>(load_vec_h16(static_cast<const int4*>(base), i));
+}
+
+template <int SF, typename T>
+__device__ __forceinline__ void store_s(void* base, int i, int vh, const Vec3<T>& v) {
+  if constexpr (SF == kS64) store_vec(static_cast<double2*>(base), i, vh, to_t<double>(v));
+  else if constexpr (SF == kS32) store_vec(static_cast<float2*>(base), i, vh, to_t<float>(v));
+  else store_vec_h16(static_cast<int4*>(base), i, to_t<float>(v));
+}
+
+template <typename T>
+struct KTraits;
+template <>
+struct KTraits<float> {
+  typedef float2 V2;
+};
+template <>
+struct KTraits<double> {
+  typedef double2 V2;
+};
+
+template <typename T>
+__device__ __forceinline__ T site_norm2(const Vec3<T>& v) {
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) s += v.c[c].re * v.c[c].re + v.c[c].im * v.c[c].im;
+  return s;
+}
+
+struct InitParams {
+  int n;
+  int maxiter;
+  int ru_interval;
+  double ru_delta;
+  double s[kMaxShifts];
+  double a_diag;
+  double tol;
+};
+
+// r = p = b (Krylov precision), |b|^2 in FP64, then the scalar state of a fresh solve.
+template <typename T>
+__global__ void __launch_bounds__(256) init_kernel(Geom g, const double2* __restrict__ b64, void* r, void* p,
+                                                   SolverDev* sd, InitParams ip, double* partials,
+                                                   unsigned* ticket) {
+  typedef typename KTraits<T>::V2 V2;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double loc = 0.0;
+  if (i < g.vh) {
+    Vec3<double> b = load_vec(b64, i, g.vh);
+    Vec3<T> bt = to_t<T>(b);
+    store_vec(static_cast<V2*>(r), i, g.vh, bt);
+    store_vec(static_cast<V2*>(p), i, g.vh, bt);
+    loc = site_norm2(b);
+  }
+  double bs = block_sum(loc);
+  if (publish_partial(partials, ticket, bs)) {
+    double bb = gather_partials(partials, ticket);
+    int k = threadIdx.x;
+    const int trivial = !(bb > 0.0);  // b = 0 (every x_k = 0) or a non-finite source
+    if (k < ip.n) {
+      sd->s[k] = ip.s[k];
+      sd->zeta[k] = sd->zeta_prev[k] = sd->zeta_new[k] = 1.0;
+      sd->active[k] = sd->wactive[k] = trivial ? 0 : 1;
+      sd->P[k] = 1.0;
+      sd->X[k] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+      sd->n = ip.n;
+      sd->a_diag = ip.a_diag;
+      sd->bb = bb;
+      sd->rr = bb;
+      sd->stop2 = ip.tol * ip.tol * bb;
+      sd->alpha = sd->beta = 0.0;
+      sd->alpha_prev = 1.0;
+      sd->beta_prev = 0.0;
+      sd->pq = 0.0;
+      sd->iter = 0;
+      sd->m = 0;
+      sd->first = 1;
+      sd->maxiter = ip.maxiter;
+      sd->ru_interval = ip.ru_interval;
+      sd->iter_ru = 0;
+      sd->ru_skip = 1;
+      sd->ru_delta2 = ip.ru_delta * ip.ru_delta;
+      sd->rr_ru_max = bb;
+      sd->n_active = trivial ? 0 : ip.n;
+      sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
+      sd->done = trivial ? 1 : 0;
+    }
+  }
+}
+
+struct RUpdArgs {
+  void* r;
+  const void* q;
+  void* ring;  // kWindow slots, slot stride in bytes
+  size_t slot_bytes;
+  SolverDev* sd;
+  double* partials;
+  unsigned* ticket;
+};
+
+// r -= alpha q; R[m] = r; |r|^2 -> beta step
+template <typename T, int SF>
+__global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
+  typedef typename KTraits<T>::V2 V2;
+  SolverDev* sd = a.sd;
+  if (sd->done) return;
+  const int m = sd->m;
+  const T alpha = (T)sd->alpha;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double loc = 0.0;
+  if (i < g.vh && m < kWindow) {
+    Vec3<T> r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
+    Vec3<T> q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r.c[c].re = fma(-alpha, q.c[c].re, r.c[c].re);
+      r.c[c].im = fma(-alpha, q.c[c].im, r.c[c].im);
+    }
+    store_vec(static_cast<V2*>(a.r), i, g.vh, r);
+    store_s<SF, T>(static_cast<char*>(a.ring) + m * a.slot_bytes, i, g.vh, r);
+    loc = (double)site_norm2(r);
+  }
+  double bs = block_sum(loc);
+  if (publish_partial(a.partials, a.ticket, bs)) {
+    double rr = gather_partials(a.partials, a.ticket);
+    solver_beta_step(sd, rr);
+  }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) p_update_kernel(Geom g, const void* r, void* p, const SolverDev* sd) {
+  typedef typename KTraits<T>::V2 V2;
+  if (sd->done) return;
+  const T beta = (T)sd->beta;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * g.vh) return;
+  V2 rv = static_cast<const V2*>(r)[i];
+  V2 pv = static_cast<V2*>(p)[i];
+  pv.x = fma(beta, pv.x, rv.x);
+  pv.y = fma(beta, pv.y, rv.y);
+  static_cast<V2*>(p)[i] = pv;
+}
+
+struct FlushArgs {
+  const void* ring;
+  size_t slot_bytes;
+  void* pk[kMaxShifts];
+  double2* xk[kMaxShifts];
+  const double2* b64;
+  SolverDev* sd;
+  double* partials;
+  unsigned* ticket;
+};
+
+// Apply the pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i.
+// At the first window of a solve p_k0 = b and x_k0 = 0 (nothing is read).
+template <typename T, int SF>
+__global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
+  SolverDev* sd = a.sd;
+  const int m = sd->m;
+  if (m == 0) return;  // nothing pending
+  __shared__ T cP[kMaxShifts], cX[kMaxShifts], cpi[kMaxShifts][kWindow], cchi[kMaxShifts][kWindow];
+  __shared__ int act[kMaxShifts];
+  const int n = sd->n;
+  const int first = sd->first;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    cP[t] = (T)sd->P[t];
+    cX[t] = (T)sd->X[t];
+    act[t] = sd->wactive[t];
+    for (int s = 0; s < kWindow; ++s) {
+      cpi[t][s] = (s < m) ? (T)sd->pi[t][s] : (T)0;
+      cchi[t][s] = (s < m) ? (T)sd->chi[t][s] : (T)0;
+    }
+  }
+  __syncthreads();
+  const int vh = g.vh;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < vh) {
+    Vec3<T> R[kWindow];
+#pragma unroll
+    for (int s = 0; s < kWindow; ++s)
+      R[s] = (s < m) ? load_s<SF, T>(static_cast<const char*>(a.ring) + s * a.slot_bytes, i, vh) : vzero<T>();
+    Vec3<T> b0 = vzero<T>();
+    if (first) b0 = to_t<T>(load_vec(a.b64, i, vh));
+    for (int k = 0; k < n; ++k) {
+      if (!act[k]) continue;
+      Vec3<T> p0 = first ? b0 : load_s<SF, T>(a.pk[k], i, vh);
+      Vec3<T> np, dx;
+      const T P = cP[k], X = cX[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        np.c[c] = cmake(P * p0.c[c].re, P * p0.c[c].im);
+        dx.c[c] = cmake(X * p0.c[c].re, X * p0.c[c].im);
+      }
+#pragma unroll
+      for (int s = 0; s < kWindow; ++s) {
+        const T pis = cpi[k][s], chs = cchi[k][s];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          np.c[c].re = fma(pis, R[s].c[c].re, np.c[c].re);
+          np.c[c].im = fma(pis, R[s].c[c].im, np.c[c].im);
+          dx.c[c].re = fma(chs, R[s].c[c].re, dx.c[c].re);
+          dx.c[c].im = fma(chs, R[s].c[c].im, dx.c[c].im);
+        }
+      }
+      store_s<SF, T>(a.pk[k], i, vh, np);
+      Vec3<double> x;
+      if (first) {
+        x = to_t<double>(dx);
+      } else {
+        x = load_vec(a.xk[k], i, vh);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          x.c[c].re += (double)dx.c[c].re;
+          x.c[c].im += (double)dx.c[c].im;
+        }
+      }
+      store_vec(a.xk[k], i, vh, x);
+    }
+  }
+  if (publish_partial(a.partials, a.ticket, 0.0)) {
+    __threadfence();
+    int t = threadIdx.x;
+    if (t == 0) *a.ticket = 0u;
+    if (t < n) {
+      sd->P[t] = 1.0;
+      sd->X[t] = 0.0;
+      sd->wactive[t] = sd->active[t];
+    }
+    if (t == 0) {
+      sd->m = 0;
+      sd->first = 0;
+    }
+  }
+}
+
+// r (Krylov precision) = r64 after a reliable update; |r|^2 = scal[0]
+template <typename T>
+__global__ void ru_finish_kernel(Geom g, const double2* __restrict__ r64, void* r, const SolverDev* sd) {
+  typedef typename KTraits<T>::V2 V2;
+  if (sd->ru_skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * g.vh) {
+    double2 v = r64[i];
+    V2 w;
+    w.x = (T)v.x;
+    w.y = (T)v.y;
+    static_cast<V2*>(r)[i] = w;
+  }
+  // ru_skip is cleared only by ru_close_kernel, which runs after this kernel: every block sees one value
+}
+
+// bookkeeping of a reliable update, one thread, after ru_finish_kernel
+__global__ void ru_close_kernel(SolverDev* sd, int* ru_count) {
+  if (sd->ru_skip) return;
+  double rr = sd->scal[0];
+  if (!isfinite(rr)) {
+    sd->status = LQCD_ERR_NONFINITE;
+    sd->done = 1;
+  }
+  sd->rr = rr;
+  sd->rr_ru_max = rr;
+  sd->iter_ru = sd->iter;
+  sd->ru_skip = 1;
+  *ru_count += 1;
+}
+
+// x += e (FP64 internal vectors)
+__global__ void axpy64_kernel(int n3, double2* __restrict__ x, const double2* __restrict__ e) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double2 a = x[i], b = e[i];
+  x[i] = make_double2(a.x + b.x, a.y + b.y);
+}
+
+// canonical outputs: x_k unpacked, y = c0 b + sum_k c_k x_k (FP64)
+struct OutArgs {
+  const double2* xk[kMaxShifts];
+  double2* xout[kMaxShifts];
+  double c[kMaxShifts];
+  double c0;
+  const double2* b64;
+  double2* y;
+  int n;
+};
+
+__global__ void outputs_kernel(Geom g, OutArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.vh) return;
+  int vh = g.vh;
+  for (int c = 0; c < 3; ++c) {
+    double2 b = a.b64[c * vh + i];
+    double yr = a.c0 * b.x, yi = a.c0 * b.y;
+    for (int k = 0; k < a.n; ++k) {
+      double2 x = a.xk[k][c * vh + i];
+      if (a.xout[k]) a.xout[k][3 * (size_t)i + c] = x;
+      yr += a.c[k] * x.x;
+      yi += a.c[k] * x.y;
+    }
+    if (a.y) a.y[3 * (size_t)i + c] = make_double2(yr, yi);
+  }
+}
+
+__global__ void zero_kernel(int n3, double2* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n3) x[i] = make_double2(0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct StatusWords {
+  int iter, done, status, n, m, n_active;
+};
+
+struct Workspace {
+  int prec = -1;
+  int n_cap = 0;
+  int kprec = LQCD_FP32;  // Krylov vector precision (FP64 or FP32)
+  int sfmt = kS32;        // shift-vector storage format
+  size_t kbytes = 0, sbytes = 0, dbytes = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+  cudaEvent_t ev_batch[2] = {nullptr, nullptr};
+  void *r = nullptr, *p = nullptr, *q = nullptr, *tmp = nullptr;
+  void* ring = nullptr;
+  void* pk[kMaxShifts] = {};
+  double2* xk[kMaxShifts] = {};
+  double2 *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr, *e64 = nullptr, *rb64 = nullptr;
+  SolverDev* sd = nullptr;
+  int* ru_count = nullptr;
+  StatusWords* host_status = nullptr;  // pinned, 2 slots
+  double* host_scal = nullptr;         // pinned
+  double* partials = nullptr;
+  unsigned* tickets = nullptr;
+  std::map<std::tuple<const void*, const void*, int, int>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<const void*, const void*, int, int>, int> graph_nodes;
+};
+
+static size_t vec_bytes(long long vh, int prec) {
+  switch (prec) {
+    case LQCD_FP64: return 48 * (size_t)vh;
+    case LQCD_FP32:
+    case LQCD_FP32_R12: return 24 * (size_t)vh;
+    case LQCD_FP16FIX: return 16 * (size_t)vh;
+  }
+  return 0;
+}
+
+void free_workspace(lqcd_ctx* ctx) {
+  Workspace* w = ctx->ws;
+  if (!w) return;
+  for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+  void* bufs[] = {w->r, w->p, w->q, w->tmp, w->ring, w->b64, w->r64, w->tmp64, w->e64, w->rb64, w->sd,
+                  w->ru_count, w->partials, w->tickets};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int k = 0; k < kMaxShifts; ++k) {
+    if (w->pk[k]) cudaFree(w->pk[k]);
+    if (w->xk[k]) cudaFree(w->xk[k]);
+  }
+  if (w->host_status) cudaFreeHost(w->host_status);
+  if (w->host_scal) cudaFreeHost(w->host_scal);
+  cudaEvent_t evs[] = {w->ev_in, w->ev_out, w->ev_t0, w->ev_t1, w->ev_batch[0], w->ev_batch[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (w->st) cudaStreamDestroy(w->st);
+  delete w;
+  ctx->ws = nullptr;
+}
+
+#define LQ_CUDA(call)                                            \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return cuda_check(ctx, _e, #call);    \
+  } while (0)
+
+static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
+  Workspace* w = ctx->ws;
+  if (w && w->prec == prec && w->n_cap >= n) return LQCD_OK;
+  free_workspace(ctx);
+  w = new Workspace();
+  ctx->ws = w;
+  w->prec = prec;
+  w->n_cap = n;
+  w->kprec = (prec == LQCD_FP64) ? LQCD_FP64 : LQCD_FP32;
+  w->sfmt = (prec == LQCD_FP64) ? kS64 : (prec == LQCD_FP16FIX ? kS16 : kS32);
+  long long vh = ctx->Vh;
+  w->kbytes = vec_bytes(vh, w->kprec);
+  w->sbytes = vec_bytes(vh, prec == LQCD_FP64 ? LQCD_FP64 : (prec == LQCD_FP16FIX ? LQCD_FP16FIX : LQCD_FP32));
+  w->dbytes = vec_bytes(vh, LQCD_FP64);
+  LQ_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+  LQ_CUDA(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
+  LQ_CUDA(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
+  LQ_CUDA(cudaEventCreate(&w->ev_t0));
+  LQ_CUDA(cudaEventCreate(&w->ev_t1));
+  LQ_CUDA(cudaEventCreateWithFlags(&w->ev_batch[0], cudaEventDisableTiming));
+  LQ_CUDA(cudaEventCreateWithFlags(&w->ev_batch[1], cudaEventDisableTiming));
+  LQ_CUDA(cudaMalloc(&w->r, w->kbytes));
+  LQ_CUDA(cudaMalloc(&w->p, w->kbytes));
+  LQ_CUDA(cudaMalloc(&w->q, w->kbytes));
+  LQ_CUDA(cudaMalloc(&w->tmp, w->kbytes));
+  LQ_CUDA(cudaMalloc(&w->ring, w->sbytes * kWindow));
+  for (int k = 0; k < n; ++k) {
+    LQ_CUDA(cudaMalloc(&w->pk[k], w->sbytes));
+    LQ_CUDA(cudaMalloc(&w->xk[k], w->dbytes));
+  }
+  LQ_CUDA(cudaMalloc(&w->b64, w->dbytes));
+  LQ_CUDA(cudaMalloc(&w->r64, w->dbytes));
+  LQ_CUDA(cudaMalloc(&w->tmp64, w->dbytes));
+  LQ_CUDA(cudaMalloc(&w->e64, w->dbytes));
+  LQ_CUDA(cudaMalloc(&w->rb64, w->dbytes));
+  LQ_CUDA(cudaMalloc(&w->sd, sizeof(SolverDev)));
+  LQ_CUDA(cudaMemsetAsync(w->sd, 0, sizeof(SolverDev), w->st));
+  LQ_CUDA(cudaMalloc(&w->ru_count, sizeof(int)));
+  // one partial per block of the widest reduction kernel
+  int nparts = std::max(dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8), (int)((vh + 127) / 128)) + 64;
+  LQ_CUDA(cudaMalloc(&w->partials, sizeof(double) * nparts));
+  LQ_CUDA(cudaMalloc(&w->tickets, sizeof(unsigned) * 16));
+  LQ_CUDA(cudaMemsetAsync(w->tickets, 0, sizeof(unsigned) * 16, w->st));
+  LQ_CUDA(cudaMallocHost(&w->host_status, sizeof(StatusWords) * 2));
+  LQ_CUDA(cudaMallocHost(&w->host_scal, sizeof(double) * (kMaxShifts + 4)));
+  return LQCD_OK;
+}
+
+struct Launcher {
+  lqcd_ctx* ctx;
+  Workspace* w;
+  Geom g;
+  int nlaunch = 0;
+};
+
+// the four kernels of one base iteration
+static cudaError_t enqueue_iteration(Launcher& L) {
+  Workspace* w = L.w;
+  lqcd_ctx* ctx = L.ctx;
+  cudaStream_t st = w->st;
+  const int* done = &w->sd->done;
+  DslashArgs d1;
+  d1.out = w->tmp;
+  d1.in = w->p;
+  d1.out_parity = 1;
+  d1.prec = w->prec == LQCD_FP16FIX ? LQCD_FP32 : w->prec;
+  d1.tps = ctx->dslash_tps;
+  d1.done = done;
+  cudaError_t e = launch_dslash(L.g, ctx->gauge, d1, st, &L.nlaunch);
+  if (e != cudaSuccess) return e;
+  DslashArgs d2 = d1;
+  d2.out = w->q;
+  d2.in = w->tmp;
+  d2.out_parity = 0;
+  d2.epi = Epi::AApply;
+  d2.aux = w->p;
+  d2.a_dev = &w->sd->a_diag;  // 4 m^2 + sigma_0 of the running solve
+  d2.solver = w->sd;
+  d2.partials = w->partials;
+  d2.ticket = w->tickets + 0;
+  e = launch_dslash(L.g, ctx->gauge, d2, st, &L.nlaunch);
+  if (e != cudaSuccess) return e;
+  RUpdArgs ra;
+  ra.r = w->r;
+  ra.q = w->q;
+  ra.ring = w->ring;
+  ra.slot_bytes = w->sbytes;
+  ra.sd = w->sd;
+  ra.partials = w->partials;
+  ra.ticket = w->tickets + 1;
+  int nb = (L.g.vh + 255) / 256;
+  int nb3 = (3 * L.g.vh + 255) / 256;
+  if (w->kprec == LQCD_FP64) {
+    r_update_kernel<double, kS64><<<nb, 256, 0, st>>>(L.g, ra);
+    p_update_kernel<double><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+  } else if (w->sfmt == kS16) {
+    r_update_kernel<float, kS16><<<nb, 256, 0, st>>>(L.g, ra);
+    p_update_kernel<float><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+  } else {
+    r_update_kernel<float, kS32><<<nb, 256, 0, st>>>(L.g, ra);
+    p_update_kernel<float><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+  }
+  L.nlaunch += 2;
+  return cudaGetLastError();
+}
+
+static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n) {
+  Workspace* w = L.w;
+  FlushArgs fa;
+  memset(&fa, 0, sizeof(fa));
+  fa.ring = w->ring;
+  fa.slot_bytes = w->sbytes;
+  for (int k = 0; k < n; ++k) {
+    fa.pk[k] = w->pk[k];
+    fa.xk[k] = xs[k];
+  }
+  fa.b64 = b64;
+  fa.sd = w->sd;
+  fa.partials = w->partials;
+  fa.ticket = w->tickets + 2;
+  int nb = (L.g.vh + 127) / 128;
+  if (w->sfmt == kS64) flush_kernel<double, kS64><<<nb, 128, 0, w->st>>>(L.g, fa);
+  else if (w->sfmt == kS16) flush_kernel<float, kS16><<<nb, 128, 0, w->st>>>(L.g, fa);
+  else flush_kernel<float, kS32><<<nb, 128, 0, w->st>>>(L.g, fa);
+  L.nlaunch += 1;
+  return cudaGetLastError();
+}
+
+// FP64 residual r64 = bvec - (A + sigma) x into r64, |r64|^2 into *dot (device)
+static cudaError_t enqueue_resid64(Launcher& L, const double2* x, const double2* bvec, double sigma, double* dot,
+                                   const int* done, const double* a_dev = nullptr) {
+  Workspace* w = L.w;
+  lqcd_ctx* ctx = L.ctx;
+  DslashArgs d1;
+  d1.out = w->tmp64;
+  d1.in = x;
+  d1.out_parity = 1;
+  d1.prec = LQCD_FP64;
+  d1.done = done;
+  cudaError_t e = launch_dslash(L.g, ctx->gauge, d1, w->st, &L.nlaunch);
+  if (e != cudaSuccess) return e;
+  DslashArgs d2 = d1;
+  d2.out = w->r64;
+  d2.in = w->tmp64;
+  d2.out_parity = 0;
+  d2.epi = Epi::Resid;
+  d2.a = 4.0 * ctx->mass * ctx->mass + sigma;
+  d2.a_dev = a_dev;
+  d2.aux = x;
+  d2.bvec = bvec;
+  d2.dot_out = dot;
+  d2.partials = w->partials;
+  d2.ticket = w->tickets + 3;
+  return launch_dslash(L.g, ctx->gauge, d2, w->st, &L.nlaunch);
+}
+
+// iteration batch: windows x (kWindow iterations, flush, reliable update if due).  The reliable-update
+// kernels return at entry unless the beta step marked one as due (ru_skip == 0).
+static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2* b64, int n, int k0, double sigma0,
+                                 int windows, bool use_ru) {
+  cudaError_t e;
+  Workspace* w = L.w;
+  for (int wdx = 0; wdx < windows; ++wdx) {
+    for (int it = 0; it < kWindow; ++it)
+      if ((e = enqueue_iteration(L)) != cudaSuccess) return e;
+    if ((e = enqueue_flush(L, xs, b64, n)) != cudaSuccess) return e;
+    if (use_ru) {
+      // r64 = b - (A + sigma_0) x_0 in FP64 with FP64 links, then r <- r64 and |r|^2 <- |r64|^2
+      if ((e = enqueue_resid64(L, xs[k0], b64, sigma0, &w->sd->scal[0], &w->sd->ru_skip, &w->sd->a_diag)) !=
+          cudaSuccess)
+        return e;
+      int nb3 = (3 * L.g.vh + 255) / 256;
+      if (w->kprec == LQCD_FP64)
+        ru_finish_kernel<double><<<nb3, 256, 0, w->st>>>(L.g, w->r64, w->r, w->sd);
+      else
+        ru_finish_kernel<float><<<nb3, 256, 0, w->st>>>(L.g, w->r64, w->r, w->sd);
+      ru_close_kernel<<<1, 1, 0, w->st>>>(w->sd, w->ru_count);
+      L.nlaunch += 2;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Solve (A + shifts[k]) xs[k] = b64 for all k (FP64 internal vectors).
+static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts, int n, double tol,
+                      int maxiter, bool use_ru, int* iters, int* n_ru, int* status) {
+  Workspace* w = ctx->ws;
+  Launcher L{ctx, w, make_geom(ctx), 0};
+  int k0 = 0;
+  for (int k = 1; k < n; ++k)
+    if (shifts[k] < shifts[k0]) k0 = k;
+  double sigma0 = shifts[k0];
+  InitParams ip;
+  memset(&ip, 0, sizeof(ip));
+  ip.n = n;
+  for (int k = 0; k < n; ++k) ip.s[k] = shifts[k] - sigma0;
+  ip.a_diag = 4.0 * ctx->mass * ctx->mass + sigma0;
+  ip.tol = tol;
+  ip.maxiter = maxiter;
+  ip.ru_interval = ctx->reliable_interval;
+  ip.ru_delta = ctx->reliable_delta;
+  LQ_CUDA(cudaMemsetAsync(w->ru_count, 0, sizeof(int), w->st));
+  int nb = (L.g.vh + 255) / 256;
+  if (w->kprec == LQCD_FP64)
+    init_kernel<double><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
+  else
+    init_kernel<float><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
+  L.nlaunch += 1;
+  LQ_CUDA(cudaGetLastError());
+
+  const int windows = std::max(1, ctx->batch / kWindow);
+  const int per_batch = windows * kWindow;
+  const int max_batches = (maxiter + per_batch - 1) / per_batch;
+
+  auto get_graph = [&](cudaGraphExec_t* out, int* nodes) -> int {
+    auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0), k0);
+    auto it = w->graphs.find(key);
+    if (it != w->graphs.end()) {
+      *out = it->second;
+      *nodes = w->graph_nodes[key];
+      return LQCD_OK;
+    }
+    Launcher C{ctx, w, L.g, 0};
+    cudaGraph_t graph;
+    LQ_CUDA(cudaStreamBeginCapture(w->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_batch(C, xs, b64, n, k0, sigma0, windows, use_ru);
+    cudaError_t e2 = cudaStreamEndCapture(w->st, &graph);
+    LQ_CUDA(e);
+    LQ_CUDA(e2);
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    LQ_CUDA(e);
+    w->graphs[key] = exec;
+    w->graph_nodes[key] = C.nlaunch;
+    *out = exec;
+    *nodes = C.nlaunch;
+    return LQCD_OK;
+  };
+
+  int launched = 0, checked = 0;
+  bool finished = false;
+  StatusWords last;
+  memset(&last, 0, sizeof(last));
+  while (!finished) {
+    if (launched < max_batches) {
+      if (ctx->use_graph) {
+        cudaGraphExec_t exec;
+        int nodes = 0;
+        int rc = get_graph(&exec, &nodes);
+        if (rc != LQCD_OK) return rc;
+        LQ_CUDA(cudaGraphLaunch(exec, w->st));
+        L.nlaunch += nodes;
+      } else {
+        LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
+      }
+      int slot = launched & 1;
+      LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
+                              w->st));
+      LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
+      ++launched;
+    }
+    if (launched - checked >= 2 || launched == max_batches) {
+      int slot = checked & 1;
+      LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
+      last = w->host_status[slot];
+      ++checked;
+      if (last.done || checked == max_batches) finished = true;
+    }
+  }
+  // drain a batch still in flight and read the final state
+  LQ_CUDA(cudaMemcpyAsync(&w->host_status[0], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
+  int ru_host = 0;
+  LQ_CUDA(cudaMemcpyAsync(&ru_host, w->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+  LQ_CUDA(cudaStreamSynchronize(w->st));
+  last = w->host_status[0];
+  ctx->launches += L.nlaunch;
+  *iters = last.iter;
+  *n_ru = ru_host;
+  if (last.status != LQCD_OK) *status = last.status;
+  else if (!last.done || last.n_active > 0) *status = LQCD_ERR_NOT_CONVERGED;
+  else *status = LQCD_OK;
+  return LQCD_OK;
+}
+
+// FP64 true residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts
+static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts,
+                          const std::vector<int>& ks, double bnorm2, double* out) {
+  Workspace* w = ctx->ws;
+  Launcher L{ctx, w, make_geom(ctx), 0};
+  for (size_t j = 0; j < ks.size(); ++j) {
+    int k = ks[j];
+    LQ_CUDA(enqueue_resid64(L, xs[k], b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
+  }
+  LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->scal[4], sizeof(double) * ks.size(), cudaMemcpyDeviceToHost, w->st));
+  LQ_CUDA(cudaStreamSynchronize(w->st));
+  ctx->launches += L.nlaunch;
+  for (size_t j = 0; j < ks.size(); ++j) out[j] = sqrt(w->host_scal[j] / bnorm2);
+  return LQCD_OK;
+}
+
+int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
+               double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats) {
+  int rc = ensure_workspace(ctx, prec, n);
+  if (rc != LQCD_OK) return rc;
+  Workspace* w = ctx->ws;
+  Geom g = make_geom(ctx);
+  long long launches0 = ctx->launches;
+  LQ_CUDA(cudaEventRecord(w->ev_in, ctx->stream));
+  LQ_CUDA(cudaStreamWaitEvent(w->st, w->ev_in, 0));
+  LQ_CUDA(cudaEventRecord(w->ev_t0, w->st));
+  LQ_CUDA(launch_pack_vector(g, w->b64, LQCD_FP64, reinterpret_cast<const double2*>(b_dev), w->st));
+  ctx->launches += 1;
+
+  int iters = 0, n_ru = 0, st_main = LQCD_OK;
+  rc = solve_core(ctx, w->b64, w->xk, shifts, n, tol, maxiter, prec != LQCD_FP64, &iters, &n_ru, &st_main);
+  if (rc != LQCD_OK) return rc;
+  LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
+  LQ_CUDA(cudaStreamSynchronize(w->st));
+  double bb = w->host_scal[0];
+
+  double tres[kMaxShifts];
+  for (int k = 0; k < n; ++k) tres[k] = 0.0;
+  int refine_iters = 0, refined = 0, status = st_main;
+  if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
+    std::vector<int> all(n);
+    for (int k = 0; k < n; ++k) all[k] = k;
+    rc = true_residuals(ctx, w->b64, w->xk, shifts, all, bb, tres);
+    if (rc != LQCD_OK) return rc;
+    if (ctx->refine && st_main == LQCD_OK) {
+      // per-shift refinement: (A + d_k) e = b - (A + d_k) x_k, warm start x_k, until the true residual <= tol
+      for (int k = 0; k < n; ++k) {
+        int rounds = 0;
+        while (tres[k] > tol && rounds < 4) {
+          Launcher L{ctx, w, g, 0};
+          LQ_CUDA(enqueue_resid64(L, w->xk[k], w->b64, shifts[k], &w->sd->scal[1], nullptr));
+          LQ_CUDA(cudaMemcpyAsync(w->rb64, w->r64, w->dbytes, cudaMemcpyDeviceToDevice, w->st));
+          ctx->launches += L.nlaunch;
+          double inner_tol = std::min(0.5, 0.5 * tol / tres[k]);
+          int it2 = 0, ru2 = 0, st2 = LQCD_OK;
+          double2* es[1] = {w->e64};
+          rc = solve_core(ctx, w->rb64, es, &shifts[k], 1, inner_tol, maxiter, prec != LQCD_FP64, &it2, &ru2, &st2);
+          if (rc != LQCD_OK) return rc;
+          refine_iters += it2;
+          n_ru += ru2;
+          axpy64_kernel<<<(3 * g.vh + 255) / 256, 256, 0, w->st>>>(3 * g.vh, w->xk[k], w->e64);
+          ctx->launches += 1;
+          LQ_CUDA(cudaGetLastError());
+          std::vector<int> one(1, k);
+          rc = true_residuals(ctx, w->b64, w->xk, shifts, one, bb, &tres[k]);
+          if (rc != LQCD_OK) return rc;
+          ++rounds;
+          if (st2 == LQCD_ERR_NONFINITE) break;
+        }
+        if (rounds > 0) ++refined;
+      }
+    }
+    if (status == LQCD_OK)
+      for (int k = 0; k < n; ++k)
+        if (!(tres[k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
+  }
+  if (bb == 0.0) {
+    for (int k = 0; k < n; ++k) {
+      zero_kernel<<<(3 * g.vh + 255) / 256, 256, 0, w->st>>>(3 * g.vh, w->xk[k]);
+      ctx->launches += 1;
+    }
+  }
+  // outputs in the canonical layout
+  OutArgs oa;
+  memset(&oa, 0, sizeof(oa));
+  for (int k = 0; k < n; ++k) {
+    oa.xk[k] = w->xk[k];
+    oa.xout[k] = x_dev ? reinterpret_cast<double2*>(x_dev[k]) : nullptr;
+    oa.c[k] = residues ? residues[k] : 0.0;
+  }
+  oa.c0 = c0;
+  oa.b64 = w->b64;
+  oa.y = reinterpret_cast<double2*>(y_dev);
+  oa.n = n;
+  outputs_kernel<<<(g.vh + 255) / 256, 256, 0, w->st>>>(g, oa);
+  ctx->launches += 1;
+  LQ_CUDA(cudaGetLastError());
+  LQ_CUDA(cudaEventRecord(w->ev_t1, w->st));
+  LQ_CUDA(cudaEventRecord(w->ev_out, w->st));
+  LQ_CUDA(cudaStreamWaitEvent(ctx->stream, w->ev_out, 0));
+  LQ_CUDA(cudaEventSynchronize(w->ev_t1));
+  float ms = 0;
+  LQ_CUDA(cudaEventElapsedTime(&ms, w->ev_t0, w->ev_t1));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = iters;
+    stats->reliable_updates = n_ru;
+    stats->refine_iterations = refine_iters;
+    stats->refined_shifts = refined;
+    stats->kernel_launches = (int)(ctx->launches - launches0);
+    stats->n_shifts = n;
+    for (int k = 0; k < n; ++k) stats->true_residual[k] = tres[k];
+    stats->ms = ms;
+  }
+  if (status == LQCD_ERR_NONFINITE) return fail(ctx, status, "non-finite value in the shifted CG");
+  if (status == LQCD_ERR_NOT_CONVERGED) return fail(ctx, status, "shifted CG did not reach the requested residual");
+  if (status != LQCD_OK) return fail(ctx, status, "shifted CG failed");
+  return LQCD_OK;
+}
+
+}  // namespace lqcd

@@ -1,0 +1,75 @@
+"""Helpers for the GPU parity tests: move seeded inputs to the device and run the library."""
+import numpy as np
+
+from paper_1710_09178_gb300 import inputs
+
+
+def torch_mod():
+    import torch
+
+    return torch
+
+
+def to_dev(a):
+    torch = torch_mod()
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make_context(dims, mass, U=None, gauge_seed=1):
+    import paper_1710_09178_gb300 as lq
+
+    ctx = lq.Context(dims, mass)
+    if U is None:
+        U = inputs.gauge_field(dims, seed=gauge_seed)
+    ctx.set_gauge(to_dev(U))
+    return ctx, U
+
+
+def gpu_dslash(ctx, psi, out_parity, prec):
+    """Canonical complex128 numpy vector in -> canonical numpy vector out, via pack / dslash_eo / unpack."""
+    import paper_1710_09178_gb300 as lq
+
+    torch = torch_mod()
+    src = to_dev(psi)
+    vin = ctx.new_vector(prec)
+    vout = ctx.new_vector(prec)
+    ctx.pack(vin, prec, src)
+    lq.dslash_eo(ctx, vout, vin, out_parity, prec)
+    res = torch.empty_like(src)
+    ctx.unpack(res, vout, prec)
+    torch.cuda.synchronize()
+    return res.cpu().numpy()
+
+
+def gpu_apply_A(ctx, psi, sigma, prec):
+    torch = torch_mod()
+    src = to_dev(psi)
+    vin = ctx.new_vector(prec)
+    vout = ctx.new_vector(prec)
+    ctx.pack(vin, prec, src)
+    pq = ctx.apply_A(vout, vin, sigma, prec, want_dot=True)
+    res = torch.empty_like(src)
+    ctx.unpack(res, vout, prec)
+    torch.cuda.synchronize()
+    return res.cpu().numpy(), pq
+
+
+def gpu_mshift(ctx, b, shifts, residues=None, c0=0.0, tol=1e-10, maxiter=20000, prec=0, want_y=False):
+    import paper_1710_09178_gb300 as lq
+
+    torch = torch_mod()
+    bd = to_dev(b)
+    xs = [torch.empty_like(bd) for _ in shifts]
+    y = torch.empty_like(bd) if want_y else None
+    rc, st = lq.mshift_cg(ctx, shifts, residues if residues is not None else [0.0] * len(shifts), c0, bd, xs, y,
+                          tol=tol, maxiter=maxiter, prec=prec, raise_on_error=False)
+    torch.cuda.synchronize()
+    return rc, st, [x.cpu().numpy() for x in xs], (y.cpu().numpy() if want_y else None)
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def rel_norm(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

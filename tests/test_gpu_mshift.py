@@ -1,0 +1,137 @@
+"""GPU parity of the shifted CG (Section 4, ref. [mcg]) and the rational application (Eq. ratapprx).
+
+Bars:
+  - FP64, fixed iteration count (no shift stopped): every x_k within 1e-11 relative of
+    the oracle run for the same number of iterations (the two differ only in
+    the summation order of the dot products);
+  - converged solves, every precision: the FP64 true residual |b - (A+d_k)x_k|/|b|
+    computed by the oracle is <= the requested 1e-10 for every shift, and x_k is within
+    kappa_k * 2e-10 of the oracle's converged solution (kappa_k bounds the condition number);
+  - y = c0 b + sum c_k x_k within the same bound of the oracle's y.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_mshift, make_context, rel_norm
+from oracle import rational, solvers, staggered
+from paper_1710_09178_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32, FP32_R12, FP16FIX = 0, 1, 2, 3
+
+
+def _problem(dims, mass, npoles, gseed, vseed):
+    ctx, U = make_context(dims, mass, gauge_seed=gseed)
+    b = inputs.gaussian_vector(dims, vseed)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(npoles, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    return ctx, U, b, c0, res, poles
+
+
+@pytest.mark.parametrize("dims,iters", [((4, 4, 4, 4), 25), ((10, 6, 4, 6), 37), ((16, 16, 16, 8), 20)])
+def test_fp64_fixed_iterations_match_oracle(dims, iters):
+    import paper_1710_09178_gb300 as lq
+
+    mass = 0.05
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 12, 1, 2)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    rc, st, xs, _ = gpu_mshift(ctx, b, poles, tol=1e-300, maxiter=iters, prec=FP64)
+    assert rc == lq.LQCD_ERR_NOT_CONVERGED and st["iterations"] == iters
+    oxs, info = solvers.multishift_cg(lambda v: staggered.A_apply(U, v, mass, dims, poles.min()), b, poles,
+                                      fixed_iters=iters)
+    for x, ox in zip(xs, oxs):
+        assert rel_norm(x, ox) < 1e-11
+
+
+def _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec, tol=1e-10):
+    import paper_1710_09178_gb300 as lq
+
+    rc, st, xs, y = gpu_mshift(ctx, b, poles, res, c0, tol=tol, prec=prec, want_y=True)
+    assert rc == lq.LQCD_OK, st
+    tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, poles)
+    assert np.all(tr <= tol * 1.001), tr
+    assert np.allclose(tr, st["true_residual"], rtol=1e-3, atol=1e-14)
+    return st, xs, y
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX])
+def test_converged_solve_matches_oracle_4444(prec):
+    dims, mass = (4, 4, 4, 4), 0.1
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 12, 1, 2)
+    st, xs, y = _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec)
+    oxs, _ = solvers.multishift_cg(lambda v: staggered.A_apply(U, v, mass, dims, poles.min()), b, poles, tol=1e-12)
+    lmin = 4 * mass ** 2
+    for x, ox, s in zip(xs, oxs, poles):
+        kappa = (16 + lmin + s) / (lmin + s)
+        assert rel_norm(x, ox) <= kappa * 2e-10
+    oy = solvers.rational_apply(b, oxs, c0, res)
+    assert rel_norm(y, oy) <= (16 / lmin) * 2e-10
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX])
+def test_converged_solve_16c8(prec):
+    dims, mass = (16, 16, 16, 8), 0.05
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 14, 3, 4)
+    st, xs, y = _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec)
+    assert st["iterations"] > 10
+    if prec != FP64:
+        assert st["reliable_updates"] >= st["iterations"] // 100 - 1
+
+
+def test_ragged_lattice_and_unsorted_duplicate_shifts():
+    dims, mass = (10, 6, 4, 6), 0.05
+    ctx, U = make_context(dims, mass, gauge_seed=6)
+    b = inputs.gaussian_vector(dims, 7)
+    shifts = np.array([0.3, 0.0, 0.3, 2.5, 0.001])
+    for prec in (FP64, FP32):
+        rc, st, xs, _ = gpu_mshift(ctx, b, shifts, tol=1e-10, prec=prec)
+        assert rc == 0
+        tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, shifts)
+        assert np.all(tr <= 1.001e-10)
+        assert rel_norm(xs[0], xs[2]) < 1e-9
+
+
+def test_single_shift_and_zero_source():
+    dims, mass = (4, 4, 4, 4), 0.1
+    ctx, U = make_context(dims, mass)
+    b = np.zeros((128, 3), dtype=np.complex128)
+    rc, st, xs, y = gpu_mshift(ctx, b, [0.01, 0.2], [1.0, 2.0], 0.5, prec=FP32, want_y=True)
+    assert rc == 0 and all(np.all(x == 0) for x in xs) and np.all(y == 0)
+    b = inputs.gaussian_vector(dims, 9)
+    rc, st, xs, _ = gpu_mshift(ctx, b, [0.0], prec=FP32)
+    assert rc == 0
+    xc, _ = solvers.cg(lambda v: staggered.A_apply(U, v, mass, dims), b, tol=1e-12)
+    assert rel_norm(xs[0], xc) < (16 / 0.04) * 2e-10
+
+
+def test_maxiter_and_nonfinite_status():
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (4, 4, 4, 4), 0.01
+    ctx, U = make_context(dims, mass)
+    b = inputs.gaussian_vector(dims, 10)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    rc, st, xs, _ = gpu_mshift(ctx, b, [0.0, 0.1], maxiter=3, prec=FP32)
+    assert rc == lq.LQCD_ERR_NOT_CONVERGED and st["iterations"] == 3
+    b2 = b.copy()
+    b2[5, 1] = np.nan
+    rc, st, xs, _ = gpu_mshift(ctx, b2, [0.0, 0.1], prec=FP32)
+    assert rc == lq.LQCD_ERR_NONFINITE
+    # the context stays usable after an error
+    ctx.set_option(lq.OPT_REFINE, 1)
+    rc, st, xs, _ = gpu_mshift(ctx, b, [0.0, 0.1], prec=FP32)
+    assert rc == 0
+
+
+def test_no_graph_path_matches_graph_path():
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (10, 6, 4, 6), 0.05
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 12, 2, 3)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    _, st1, xs1, _ = gpu_mshift(ctx, b, poles, tol=1e-300, maxiter=33, prec=FP32)
+    ctx.set_option(lq.OPT_USE_GRAPH, 0)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    _, st2, xs2, _ = gpu_mshift(ctx, b, poles, tol=1e-300, maxiter=33, prec=FP32)
+    for a, c in zip(xs1, xs2):
+        assert np.array_equal(a, c)  # deterministic reductions: identical bits
