@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the shifted-CG hot path on the 32^3 x 8 workload.
+
+One step = one complete call of mshift_cg: the 16-pole rational approximation of
+x^{-1/2} on [4m^2, 16 + 4m^2] (m = 0.02) applied to a Gaussian source, solved to a
+true FP64 residual of 1e-10 for every shift (Section 4, Eq. ratapprx), in the
+mixed mode (FP32 links and Krylov vectors, FP64 dot products, solution
+accumulation, reliable updates and final residuals) -- every row of the hot path:
+Dslash, A-apply, reductions, shifted updates, reliable updates, refinement and
+the rational application.
+
+Printed JSON line (rank 0): value = ms per solve (mixed), plus the FP64 solve,
+the 12-real and 16-bit variants, the Dslash roofline (algorithmic bytes per
+launch over the CUDA-event launch time, L2 flushed before each launch), the
+end-to-end number through the C ABI with host buffers, and the oracle timed on
+the host cores (cpu_baseline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multishift-CG time/solve to 1e-10, mixed vs FP64 at 32^3x8; Dslash % HBM peak"
+WORKLOAD = "32^3x8"
+DIMS = (32, 32, 32, 8)
+MASS = 0.02
+NPOLES = 16
+TOL = 1e-10
+GAUGE_SEED, VEC_SEED = 5, 6
+# Dslash algorithmic bytes per output site (8 links + 1 input + 1 output vector, each crossing HBM once)
+DSLASH_BYTES_PER_SITE = {"fp32": 8 * 72 + 24 + 24, "fp32_r12": 8 * 48 + 24 + 24, "fp64": 8 * 144 + 48 + 48}
+DSLASH_FLOPS_PER_SITE = 570
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1710_09178_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_key):
+    """DRAM bytes per launch of the FP32 Dslash from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "dslash_fp32_32c8.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+class L2Flusher:
+    """Write a 256 MB buffer, then read another one (both > 129 MB of L2): the read pass evicts the
+    dirty lines of the write pass, so the next kernel starts from a clean, cold L2."""
+
+    def __init__(self, torch):
+        self.w = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
+        self.r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+        self.sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def add_(self, _):
+        self.w.add_(1.0)
+        self.sink.add_(self.r.sum())
+
+
+def setup_problem(lq, torch):
+    from paper_1710_09178_gb300 import inputs
+
+    U = inputs.gauge_field(DIMS, seed=GAUGE_SEED)
+    b = inputs.gaussian_vector(DIMS, VEC_SEED)
+    lo, hi = 4 * MASS * MASS, 16 + 4 * MASS * MASS
+    c0, res, poles, err = lq.rational_coeffs(-0.5, lo, hi, NPOLES)
+    return U, b, (c0, res, poles, err)
+
+
+def time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, steps, warmup, flush_buf):
+    c0, res, poles, _ = coeffs
+    st = None
+    for _ in range(warmup):
+        rc, st = lq.mshift_cg(ctx, poles, res, c0, bd, xs, y, tol=TOL, prec=prec)
+    times, stats = [], []
+    stream = torch.cuda.current_stream()
+    for _ in range(steps):
+        flush_buf.add_(1)  # evict the previous solve's data from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st = lq.mshift_cg(ctx, poles, res, c0, bd, xs, y, tol=TOL, prec=prec)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    return times, stats
+
+
+def time_dslash(lq, torch, ctx, prec_name, prec, reps, flush_buf):
+    """Average duration of one Dslash launch (D_oe then D_eo alternately), L2 flushed before each."""
+    vin = ctx.new_vector(prec)
+    vout = ctx.new_vector(prec)
+    vin.view(torch.float32 if prec != lq.FP64 else torch.float64).normal_()
+    stream = torch.cuda.current_stream()
+    for p in (0, 1, 0, 1):
+        lq.dslash_eo(ctx, vout, vin, p, prec)
+    evs = []
+    for r in range(reps):
+        flush_buf.add_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lq.dslash_eo(ctx, vout, vin, r & 1, prec)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return statistics.mean(ms), statistics.median(ms)
+
+
+def cpu_baseline_oracle(U, b, coeffs, iters_per_solve, sample_iters):
+    """The oracle's shifted CG on the same input, a bounded number of iterations, scaled to one solve."""
+    from oracle import solvers, staggered
+
+    c0, res, poles, _ = coeffs
+    t0 = time.perf_counter()
+    solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles,
+                          fixed_iters=sample_iters)
+    dt = time.perf_counter() - t0
+    per_iter_ms = dt * 1e3 / sample_iters
+    return per_iter_ms * iters_per_solve, per_iter_ms, dt
+
+
+def oracle_iterations():
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations_32c8.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return int(json.load(f)["iterations"])
+    return None
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, same metric and unit, bounded samples."""
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from paper_1710_09178_gb300 import inputs
+    from oracle import rational, solvers, staggered
+
+    U = inputs.gauge_field(DIMS, seed=GAUGE_SEED)
+    b = inputs.gaussian_vector(DIMS, VEC_SEED)
+    lo, hi = 4 * MASS * MASS, 16 + 4 * MASS * MASS
+    c0, res, poles, err = rational.zolotarev_inv_sqrt(NPOLES, lo, hi)
+    iters = oracle_iterations()
+    sample = env_int("LQCD_REF_SAMPLE_ITERS", 4)
+    for _ in range(args.warmup):
+        solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles, fixed_iters=1)
+    per = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles,
+                              fixed_iters=sample)
+        per.append((time.perf_counter() - t0) * 1e3 / sample)
+    per_iter = statistics.mean(per)
+    value = per_iter * iters if iters else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms/solve", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES, "tol": TOL,
+                   "precision": "fp64 oracle (numpy)"},
+        "cpu_baseline": {"value": value, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} shifted-CG iterations per step at 32^3x8, 16 shifts, scaled by the "
+                                   f"{iters} iterations the oracle needs for a full solve (tests/golden)"},
+        "e2e": {"value": value, "unit": "ms/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="mixed mode only (for profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1710_09178_gb300 as lq
+
+    U, b, coeffs = setup_problem(lq, torch)
+    ctx = lq.Context(DIMS, MASS)
+    Ud = torch.from_numpy(U).cuda()
+    ctx.set_gauge(Ud)
+    bd = torch.from_numpy(b).cuda()
+    xs = [torch.empty_like(bd) for _ in range(NPOLES)]
+    y = torch.empty_like(bd)
+    flush_buf = L2Flusher(torch)
+    launches0 = ctx.launch_count()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: mixed-precision solve ------------------------------------------------
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times, stats = time_solves(lq, torch, ctx, bd, xs, y, coeffs, lq.FP32, args.steps, args.warmup, flush_buf)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    launches_timed = sum(s["kernel_launches"] for s in stats)
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_solve = total_ms / args.steps
+    value = total_ms / (args.steps * world)  # whole-job time per solve over all replicas
+
+    extra = {}
+    if not args.quick:
+        # FP64 solve (the plain method) and the other storage modes
+        for name, prec in (("fp64", lq.FP64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX)):
+            tms, sts = time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
+            extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
+                           "reliable_updates": sts[-1]["reliable_updates"],
+                           "refine_iterations": sts[-1]["refine_iterations"],
+                           "max_true_residual": max(sts[-1]["true_residual"])}
+
+    # ---- Dslash roofline (the kernel that dominates the solve) ------------------------------
+    peak, peak_kind = read_peaks()
+    vh = int(np.prod(DIMS)) // 2
+    dsl = {}
+    for name, prec in (("fp32", lq.FP32), ("fp32_r12", lq.FP32_R12), ("fp64", lq.FP64)):
+        if args.quick and name != "fp32":
+            continue
+        mean_ms, med_ms = time_dslash(lq, torch, ctx, name, prec, 40, flush_buf)
+        gbs = DSLASH_BYTES_PER_SITE[name] * vh / (mean_ms * 1e-3) / 1e9
+        dsl[name] = {"ms": mean_ms, "median_ms": med_ms, "algorithmic_GBps": gbs, "frac_of_hbm": gbs / peak,
+                     "gflops": DSLASH_FLOPS_PER_SITE * vh / (mean_ms * 1e-3) / 1e9}
+    traffic = profiled_traffic(WORKLOAD)
+    d32 = dsl["fp32"]
+    roofline = {"bound": "hbm", "achieved": d32["algorithmic_GBps"], "peak": peak, "unit": "GB/s",
+                "frac": d32["algorithmic_GBps"] / peak, "traffic": traffic, "kernel": "dslash_kernel<L32> (FP32)",
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "bytes_per_launch": DSLASH_BYTES_PER_SITE["fp32"] * vh}
+
+    # ---- end to end through the C ABI with host buffers ------------------------------------
+    c0, res, poles, _ = coeffs
+    b_host = torch.from_numpy(b).pin_memory()
+    y_host = torch.empty_like(b_host).pin_memory()
+    e2e_ms = []
+    stream = torch.cuda.current_stream()
+    for i in range(args.steps + 1):
+        flush_buf.add_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd.copy_(b_host, non_blocking=True)
+        lq.mshift_cg(ctx, poles, res, c0, bd, xs, y, tol=TOL, prec=lq.FP32)
+        y_host.copy_(y, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    assert np.array_equal(y_host.numpy(), y.cpu().numpy())
+    nbytes = b.nbytes
+
+    # ---- CPU baseline: the oracle, bounded sample, scaled by the FP64 iteration count -------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        iters_fp64 = extra.get("fp64", {}).get("iterations") or oracle_iterations() or stats[-1]["iterations"]
+        sample = env_int("LQCD_CPU_SAMPLE_ITERS", 12)
+        val, per_iter, dt = cpu_baseline_oracle(U, b, coeffs, iters_fp64, sample)
+        cpu = {"value": val, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+               "sample": f"{sample} iterations of the oracle's shifted CG at 32^3x8 with 16 shifts ({dt:.1f} s, "
+                         f"{per_iter:.0f} ms/iteration, numpy single thread), scaled by {iters_fp64} iterations "
+                         f"per FP64 solve"}
+
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms/solve", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES,
+                   "approximation": "x^-1/2 on [4m^2, 16+4m^2], Zolotarev (n,n)", "tol": TOL,
+                   "precision": "FP32 links+Krylov vectors, FP64 dots/x_k/reliable updates/true residuals",
+                   "gauge": "exp(i 0.5 H) SU(3), seed 5", "source": "complex Gaussian, seed 6",
+                   "l2": "flushed (256 MB written, then another 256 MB read) between timed steps and before every "
+                         "Dslash launch",
+                   "parallelism": f"replicas x{world}"},
+        "mixed": {"iterations": last["iterations"], "reliable_updates": last["reliable_updates"],
+                  "refine_iterations": last["refine_iterations"], "refined_shifts": last["refined_shifts"],
+                  "max_true_residual": max(last["true_residual"]), "ms_per_solve_all": times},
+        "fp64_vs_mixed": (extra["fp64"]["ms_per_solve"] / ms_per_solve) if "fp64" in extra else None,
+        "modes": extra,
+        "dslash": dsl,
+        "roofline": roofline,
+        "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/solve", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches_timed,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -154,11 +154,13 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
  * against the residual it replaces). */
 #define LQCD_OPT_RELIABLE_INTERVAL 1 /* most iterations between FP64 reliable updates (mixed modes; default 100) */
 #define LQCD_OPT_REFINE 2            /* 1 = refine every shift to the true residual (default), 0 = off */
-#define LQCD_OPT_BATCH 3             /* iterations per captured CUDA graph launch (default 32) */
-#define LQCD_OPT_USE_GRAPH 4         /* 1 = capture iteration batches in CUDA graphs (default), 0 = plain launches */
+#define LQCD_OPT_BATCH 3             /* iterations per host-polled batch when graphs are off (default 20) */
+#define LQCD_OPT_USE_GRAPH 4         /* 1 = one CUDA graph per solve whose conditional while-node repeats a
+                                        10-iteration window until the device says done (default);
+                                        0 = plain launches, host polls a device flag per batch */
 #define LQCD_OPT_DSLASH_TPS 5        /* threads per output site in the FP32 Dslash (1, 2, 4 or 8; 0 = tuned) */
 #define LQCD_OPT_RELIABLE_DELTA 6    /* a reliable update is also due once |r| drops below delta times its
-                                        largest value since the last one (default 0.1) */
+                                        largest value since the last one (default 0.01) */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*

@@ -19,6 +19,9 @@ Geom make_geom(const lqcd_ctx* ctx) {
   g.vh = (int)ctx->Vh;
   g.nxy = g.nx * g.ny;
   g.nxyz = g.nxy * g.nz;
+  g.dnx = make_fastdiv((unsigned)g.nx);
+  g.dny = make_fastdiv((unsigned)g.ny);
+  g.dnz = make_fastdiv((unsigned)g.nz);
   return g;
 }
 

@@ -17,11 +17,30 @@ namespace lqcd {
 // l = 2i or 2i+1: with all extents even, the pair (2i, 2i+1) shares y, z, t and
 // holds one site of each parity.
 // ---------------------------------------------------------------------------
+// Division by a run-time constant d without a hardware divide (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, unsigned case with
+// n < 2^31): q = (umulhi(n, m) + n) >> s, s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  unsigned d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while ((1ull << f.s) < d) ++f.s;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << f.s) - d)) / d + 1);
+  return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.s; }
+
 struct Geom {
   int nx, ny, nz, nt;
   int vh;   // V/2
   int nxy;  // nx*ny
   int nxyz; // nx*ny*nz
+  FastDiv dnx, dny, dnz;
 };
 
 struct Site {
@@ -29,13 +48,14 @@ struct Site {
 };
 
 __device__ __forceinline__ Site site_of(const Geom& g, int parity, int i) {
-  int l0 = 2 * i;
-  int x0 = l0 % g.nx;
-  int r = l0 / g.nx;
-  int y = r % g.ny;
-  r /= g.ny;
-  int z = r % g.nz;
-  int t = r / g.nz;
+  unsigned l0 = 2u * (unsigned)i;
+  unsigned r = fdiv(l0, g.dnx);
+  int x0 = (int)(l0 - r * (unsigned)g.nx);
+  unsigned r2 = fdiv(r, g.dny);
+  int y = (int)(r - r2 * (unsigned)g.ny);
+  unsigned r3 = fdiv(r2, g.dnz);
+  int z = (int)(r2 - r3 * (unsigned)g.nz);
+  int t = (int)r3;
   int dx = (y + z + t + parity) & 1;  // x0 is even, so x = x0 + dx has the requested parity
   Site s;
   s.x = x0 + dx;
@@ -184,6 +204,26 @@ __device__ __forceinline__ Vec3<float> load_vec(const float2* __restrict__ v, in
   return o;
 }
 
+__device__ __forceinline__ Vec3<double> ldg_vec(const double2* __restrict__ v, int i, int vh) {
+  Vec3<double> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double2 d = __ldg(v + c * vh + i);
+    o.c[c] = cmake(d.x, d.y);
+  }
+  return o;
+}
+
+__device__ __forceinline__ Vec3<float> ldg_vec(const float2* __restrict__ v, int i, int vh) {
+  Vec3<float> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 d = __ldg(v + c * vh + i);
+    o.c[c] = cmake(d.x, d.y);
+  }
+  return o;
+}
+
 __device__ __forceinline__ void store_vec(double2* __restrict__ v, int i, int vh, const Vec3<double>& o) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) v[c * vh + i] = make_double2(o.c[c].re, o.c[c].im);
@@ -240,29 +280,83 @@ __device__ __forceinline__ void store_vec_h16(int4* __restrict__ v, int i, const
 }
 
 // ---------------------------------------------------------------------------
+// Cache policy.  The FP32 gauge field (75.5 MB at 32^3 x 8) fits in GB300's L2, so link
+// loads bypass L1 (each link is used once per launch) and carry an L2 evict_last hint:
+// across the two half-Dslashes of a CG iteration and across iterations the links stay
+// resident while the streamed shift vectors (evict_first) pass through.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ float4 ld_stream(const float4* p, uint64_t pol) {
+  float4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ float2 ld_stream(const float2* p, uint64_t pol) {
+  float2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ double2 ld_stream(const double2* p, uint64_t pol) {
+  double2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol) {
+  double2 r;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(r.x), "=d"(r.y)
+               : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+               : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Internal link layouts, per (parity p, direction mu) block of Vh links stored
 // at the site x they start from (U_mu(x), x of parity p):
 //   L64 : [p][mu][9][Vh] double2, row-major complex entries, times 1/2 eta*bc
 //   L32 : [p][mu] { float4 [4][Vh] ; float2 [Vh] }, same entry order, times 1/2 eta*bc
 //   L12 : [p][mu][3][Vh] float4  rows 0 and 1 only, no sign (third row rebuilt)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ Mat3<double> load_link64(const double2* __restrict__ U, int p, int mu, int i, int vh) {
+__device__ __forceinline__ Mat3<double> load_link64(const double2* __restrict__ U, int p, int mu, int i, int vh,
+                                                   uint64_t pol) {
   const double2* b = U + (size_t)(p * 4 + mu) * 9 * vh + i;
   Mat3<double> M;
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    double2 d = b[(size_t)j * vh];
+    double2 d = ld_stream(b + (size_t)j * vh, pol);
     M.e[j / 3][j % 3] = cmake(d.x, d.y);
   }
   return M;
 }
 
-__device__ __forceinline__ Mat3<float> load_link32(const float* __restrict__ U, int p, int mu, int i, int vh) {
+__device__ __forceinline__ Mat3<float> load_link32(const float* __restrict__ U, int p, int mu, int i, int vh,
+                                                  uint64_t pol) {
   const float* blk = U + (size_t)(p * 4 + mu) * 18 * vh;
   const float4* f4 = reinterpret_cast<const float4*>(blk);
   const float2* f2 = reinterpret_cast<const float2*>(blk + 16 * (size_t)vh);
-  float4 a = f4[i], b = f4[vh + i], c = f4[2 * vh + i], d = f4[3 * vh + i];
-  float2 e = f2[i];
+  float4 a = ld_stream(f4 + i, pol), b = ld_stream(f4 + vh + i, pol), c = ld_stream(f4 + 2 * vh + i, pol),
+         d = ld_stream(f4 + 3 * vh + i, pol);
+  float2 e = ld_stream(f2 + i, pol);
   Mat3<float> M;
   M.e[0][0] = cmake(a.x, a.y);
   M.e[0][1] = cmake(a.z, a.w);
@@ -278,9 +372,9 @@ __device__ __forceinline__ Mat3<float> load_link32(const float* __restrict__ U, 
 
 // rows 0,1 from memory; row 2 = conj(row0 x row1) (exact for SU(3)); then scale by 1/2 * sign
 __device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U, int p, int mu, int i, int vh,
-                                                   float scale) {
+                                                   float scale, uint64_t pol) {
   const float4* blk = U + (size_t)(p * 4 + mu) * 3 * vh;
-  float4 a = blk[i], b = blk[vh + i], c = blk[2 * vh + i];
+  float4 a = ld_stream(blk + i, pol), b = ld_stream(blk + vh + i, pol), c = ld_stream(blk + 2 * vh + i, pol);
   Mat3<float> M;
   M.e[0][0] = cmake(a.x, a.y);
   M.e[0][1] = cmake(a.z, a.w);
@@ -332,6 +426,23 @@ __device__ __forceinline__ double block_sum(double v) {
   double t = (l < nw) ? red_smem[l] : 0.0;
   t = warp_sum(t);
   return t;
+}
+
+// Sum over the block of per-thread values of type T: within each warp in T (FP32 keeps the
+// FP64 pipe, 1/64 of the FP32 rate on GB300, out of the per-thread path), across warps in FP64.
+// Result valid in every thread.
+template <typename T>
+__device__ __forceinline__ double block_sum_mixed(T v) {
+  __shared__ double red_smem2[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red_smem2[w] = (double)v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  double t = (l < nw) ? red_smem2[l] : 0.0;
+  return warp_sum(t);
 }
 
 // Publish this block's partial; returns true in the one block that finishes last.

@@ -46,13 +46,13 @@ struct LinkTraits<kL64> {
 
 template <int LF>
 __device__ __forceinline__ Mat3<typename LinkTraits<LF>::T> load_link(const void* links, int p, int mu, int i, int vh,
-                                                                      int sign) {
+                                                                      int sign, uint64_t pol) {
   if constexpr (LF == kL64) {
-    return load_link64(static_cast<const double2*>(links), p, mu, i, vh);
+    return load_link64(static_cast<const double2*>(links), p, mu, i, vh, pol);
   } else if constexpr (LF == kL32) {
-    return load_link32(static_cast<const float*>(links), p, mu, i, vh);
+    return load_link32(static_cast<const float*>(links), p, mu, i, vh, pol);
   } else {
-    return load_link12(static_cast<const float4*>(links), p, mu, i, vh, 0.5f * (float)sign);
+    return load_link12(static_cast<const float4*>(links), p, mu, i, vh, 0.5f * (float)sign, pol);
   }
 }
 
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool lane_writes(int sub, int c) {
 }
 
 template <int LF, int TPS, int EPI>
-__global__ void __launch_bounds__(256) dslash_kernel(Geom g, KArgs k) {
+__global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   typedef typename LinkTraits<LF>::T T;
   typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
   if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
@@ -82,22 +82,41 @@ __global__ void __launch_bounds__(256) dslash_kernel(Geom g, KArgs k) {
   Vec3<T> accf = vzero<T>(), accb = vzero<T>();
   if (valid) {
     Site s = site_of(g, p, i);
+    // hops of this lane: h = sub, sub + TPS, ...; h even = forward, odd = backward along mu = h / 2
+    constexpr int NH = 8 / TPS;
+    int nb[NH], sg[NH];
 #pragma unroll
-    for (int h = sub; h < 8; h += TPS) {
+    for (int q = 0; q < NH; ++q) {
+      const int h = sub + q * TPS;  // TPS divides 8, so h < 8 and its parity is sub's
       const int mu = h >> 1;
       if ((h & 1) == 0) {
-        int j = neighbour_fwd(g, s, mu) >> 1;
-        int sg = (LF == kL12) ? link_sign_fwd(g, s, mu) : 1;
-        Mat3<T> W = load_link<LF>(k.links, p, mu, i, vh, sg);
-        Vec3<T> v = load_vec(in, j, vh);
-        mv_acc(accf, W, v);
+        nb[q] = neighbour_fwd(g, s, mu) >> 1;
+        sg[q] = (LF == kL12) ? link_sign_fwd(g, s, mu) : 1;
       } else {
-        int j = neighbour_bwd(g, s, mu) >> 1;
-        int sg = (LF == kL12) ? link_sign_bwd(g, s, mu) : 1;
-        Mat3<T> W = load_link<LF>(k.links, 1 - p, mu, j, vh, sg);
-        Vec3<T> v = load_vec(in, j, vh);
-        mdv_acc(accb, W, v);
+        nb[q] = neighbour_bwd(g, s, mu) >> 1;
+        sg[q] = (LF == kL12) ? link_sign_bwd(g, s, mu) : 1;
       }
+    }
+    // FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
+    const uint64_t pol = (LF == kL64) ? policy_evict_first() : policy_evict_last();
+    // two-stage software pipeline: the loads of hop q+1 are in flight while hop q is computed
+    auto link_of = [&](int q) {
+      const int h = sub + q * TPS;
+      return (h & 1) ? load_link<LF>(k.links, 1 - p, h >> 1, nb[q], vh, sg[q], pol)
+                     : load_link<LF>(k.links, p, h >> 1, i, vh, sg[q], pol);
+    };
+    Mat3<T> Wn = link_of(0);
+    Vec3<T> vn = ldg_vec(in, nb[0], vh);
+#pragma unroll
+    for (int q = 0; q < NH; ++q) {
+      Mat3<T> W = Wn;
+      Vec3<T> v = vn;
+      if (q + 1 < NH) {
+        Wn = link_of(q + 1);
+        vn = ldg_vec(in, nb[q + 1], vh);
+      }
+      if (((sub + q * TPS) & 1) == 0) mv_acc(accf, W, v);
+      else mdv_acc(accb, W, v);
     }
   }
   // D in = fwd - bwd, summed over the TPS lanes of the site
@@ -147,7 +166,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(Geom g, KArgs k) {
     }
   }
   if constexpr (EPI != (int)Epi::Plain) {
-    double bs = block_sum((double)dsite);
+    double bs = block_sum_mixed(dsite);
     if (publish_partial(k.partials, k.ticket, bs)) {
       double tot = gather_partials(k.partials, k.ticket);
       if (k.solver && EPI == (int)Epi::AApply) {
@@ -174,6 +193,7 @@ static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream
 template <int LF>
 static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cudaStream_t st) {
   const int bs = 128;
+  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, bs);  // FP64 is arithmetic-bound: 1 thread/site
   switch (tps) {
     case 1: return launch_tps<LF, 1>(g, k, epi, st, bs);
     case 2: return launch_tps<LF, 2>(g, k, epi, st, bs);
@@ -182,7 +202,7 @@ static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cu
   }
 }
 
-static int default_tps(int prec) { return prec == LQCD_FP64 ? 1 : 2; }
+static int default_tps(int) { return 1; }  // fastest on GB300 at 16^3x8 and 32^3x8 (sweep over 1, 2, 4, 8)
 
 int dslash_grid_blocks(const Geom& g, int prec, int tps) {
   if (tps <= 0) tps = default_tps(prec);

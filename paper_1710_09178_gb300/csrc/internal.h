@@ -39,6 +39,8 @@ struct SolverDev {
   int ru_skip;
   double ru_delta2;
   double rr_ru_max;
+  int windows_run;  // windows executed by the graph loop (bounded by max_windows whatever the flags say)
+  int max_windows;
   unsigned ticket[4];
   double s[kMaxShifts];  // sigma_k - sigma_0
   double zeta[kMaxShifts], zeta_prev[kMaxShifts], zeta_new[kMaxShifts];
@@ -71,9 +73,9 @@ struct lqcd_ctx {
   long long launches = 0;
   // solver options
   int reliable_interval = 100;
-  double reliable_delta = 0.1;
+  double reliable_delta = 0.01;
   int refine = 1;
-  int batch = 20;
+  int batch = 20;  // iterations per host-polled batch when graphs are off
   int use_graph = 1;
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;

@@ -134,6 +134,8 @@ __global__ void __launch_bounds__(256) init_kernel(Geom g, const double2* __rest
       sd->ru_skip = 1;
       sd->ru_delta2 = ip.ru_delta * ip.ru_delta;
       sd->rr_ru_max = bb;
+      sd->windows_run = 0;
+      sd->max_windows = ip.maxiter / kWindow + 2;
       sd->n_active = trivial ? 0 : ip.n;
       sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
       sd->done = trivial ? 1 : 0;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
   const int m = sd->m;
   const T alpha = (T)sd->alpha;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double loc = 0.0;
+  T loc = 0;
   if (i < g.vh && m < kWindow) {
     Vec3<T> r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
     Vec3<T> q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
     }
     store_vec(static_cast<V2*>(a.r), i, g.vh, r);
     store_s<SF, T>(static_cast<char*>(a.ring) + m * a.slot_bytes, i, g.vh, r);
-    loc = (double)site_norm2(r);
+    loc = site_norm2(r);
   }
-  double bs = block_sum(loc);
+  double bs = block_sum_mixed(loc);
   if (publish_partial(a.partials, a.ticket, bs)) {
     double rr = gather_partials(a.partials, a.ticket);
     solver_beta_step(sd, rr);
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
   }
   __syncthreads();
   const int vh = g.vh;
+  const uint64_t pol = policy_evict_first();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < vh) {
     Vec3<T> R[kWindow];
@@ -258,18 +261,15 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
         }
       }
       store_s<SF, T>(a.pk[k], i, vh, np);
-      Vec3<double> x;
-      if (first) {
-        x = to_t<double>(dx);
-      } else {
-        x = load_vec(a.xk[k], i, vh);
+      // x_k is touched once per window: stream it through L2 without displacing the links
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          x.c[c].re += (double)dx.c[c].re;
-          x.c[c].im += (double)dx.c[c].im;
-        }
+      for (int c = 0; c < 3; ++c) {
+        double2* xp = a.xk[k] + (size_t)c * vh + i;
+        double2 x = first ? make_double2(0.0, 0.0) : ld_hint(xp, pol);
+        x.x += (double)dx.c[c].re;
+        x.y += (double)dx.c[c].im;
+        st_hint(xp, x, pol);
       }
-      store_vec(a.xk[k], i, vh, x);
     }
   }
   if (publish_partial(a.partials, a.ticket, 0.0)) {
@@ -317,6 +317,16 @@ __global__ void ru_close_kernel(SolverDev* sd, int* ru_count) {
   sd->iter_ru = sd->iter;
   sd->ru_skip = 1;
   *ru_count += 1;
+}
+
+// End of a window inside the graph's while loop: continue while the solve is running.  The
+// window counter bounds the loop by itself, whatever state the other kernels left.
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle handle, SolverDev* sd) {
+  if (threadIdx.x != 0) return;
+  int wr = sd->windows_run + 1;
+  sd->windows_run = wr;
+  unsigned cont = (!sd->done && wr < sd->max_windows) ? 1u : 0u;
+  cudaGraphSetConditional(handle, cont);
 }
 
 // x += e (FP64 internal vectors)
@@ -640,64 +650,70 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   L.nlaunch += 1;
   LQ_CUDA(cudaGetLastError());
 
-  const int windows = std::max(1, ctx->batch / kWindow);
-  const int per_batch = windows * kWindow;
-  const int max_batches = (maxiter + per_batch - 1) / per_batch;
-
-  auto get_graph = [&](cudaGraphExec_t* out, int* nodes) -> int {
+  if (ctx->use_graph) {
+    // One graph per (source, solution set, shift count, base shift): a while-node repeats
+    // [kWindow iterations, window update, reliable update if due, loop control] until done.
     auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0), k0);
     auto it = w->graphs.find(key);
-    if (it != w->graphs.end()) {
-      *out = it->second;
-      *nodes = w->graph_nodes[key];
-      return LQCD_OK;
-    }
-    Launcher C{ctx, w, L.g, 0};
-    cudaGraph_t graph;
-    LQ_CUDA(cudaStreamBeginCapture(w->st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_batch(C, xs, b64, n, k0, sigma0, windows, use_ru);
-    cudaError_t e2 = cudaStreamEndCapture(w->st, &graph);
-    LQ_CUDA(e);
-    LQ_CUDA(e2);
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    LQ_CUDA(e);
-    w->graphs[key] = exec;
-    w->graph_nodes[key] = C.nlaunch;
-    *out = exec;
-    *nodes = C.nlaunch;
-    return LQCD_OK;
-  };
-
-  int launched = 0, checked = 0;
-  bool finished = false;
-  StatusWords last;
-  memset(&last, 0, sizeof(last));
-  while (!finished) {
-    if (launched < max_batches) {
-      if (ctx->use_graph) {
-        cudaGraphExec_t exec;
-        int nodes = 0;
-        int rc = get_graph(&exec, &nodes);
-        if (rc != LQCD_OK) return rc;
-        LQ_CUDA(cudaGraphLaunch(exec, w->st));
-        L.nlaunch += nodes;
-      } else {
-        LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
+    if (it == w->graphs.end()) {
+      cudaGraph_t graph;
+      LQ_CUDA(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle handle;
+      LQ_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode;
+      LQ_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      Launcher C{ctx, w, L.g, 0};
+      LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
+      if (e == cudaSuccess) {
+        loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, w->sd);
+        C.nlaunch += 1;
+        e = cudaGetLastError();
       }
-      int slot = launched & 1;
-      LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
-                              w->st));
-      LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
-      ++launched;
+      cudaGraph_t captured;
+      cudaError_t e2 = cudaStreamEndCapture(w->st, &captured);
+      LQ_CUDA(e);
+      LQ_CUDA(e2);
+      cudaGraphExec_t exec;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      LQ_CUDA(e);
+      w->graphs[key] = exec;
+      w->graph_nodes[key] = C.nlaunch;
+      it = w->graphs.find(key);
     }
-    if (launched - checked >= 2 || launched == max_batches) {
-      int slot = checked & 1;
-      LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
-      last = w->host_status[slot];
-      ++checked;
-      if (last.done || checked == max_batches) finished = true;
+    LQ_CUDA(cudaGraphLaunch(it->second, w->st));
+    LQ_CUDA(cudaMemcpyAsync(&w->host_status[1], &w->sd->windows_run, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+    LQ_CUDA(cudaStreamSynchronize(w->st));
+    L.nlaunch += w->graph_nodes[key] * w->host_status[1].iter;  // kernel nodes per window x windows run
+  } else {
+    const int windows = std::max(1, ctx->batch / kWindow);
+    const int per_batch = windows * kWindow;
+    const int max_batches = (maxiter + per_batch - 1) / per_batch;
+    int launched = 0, checked = 0;
+    bool finished = false;
+    while (!finished) {
+      if (launched < max_batches) {
+        LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
+        int slot = launched & 1;
+        LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
+                                w->st));
+        LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
+        ++launched;
+      }
+      if (launched - checked >= 2 || launched == max_batches) {
+        int slot = checked & 1;
+        LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
+        StatusWords sw = w->host_status[slot];
+        ++checked;
+        if (sw.done || checked == max_batches) finished = true;
+      }
     }
   }
   // drain a batch still in flight and read the final state
@@ -705,7 +721,7 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   int ru_host = 0;
   LQ_CUDA(cudaMemcpyAsync(&ru_host, w->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
-  last = w->host_status[0];
+  StatusWords last = w->host_status[0];
   ctx->launches += L.nlaunch;
   *iters = last.iter;
   *n_ru = ru_host;
