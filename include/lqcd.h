@@ -140,6 +140,28 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
 int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
 
 /*
+ * lqcd_apply_A_noalloc - the same operation, arguments and results as lqcd_apply_A, for
+ * callers that must not allocate device memory when they call it (device memory owned by
+ * a framework allocator or a fixed budget; loops where a cudaMalloc/cudaFree and the
+ * device synchronisation it brings are not acceptable).  The paper has no counterpart;
+ * this is a property of the library, not of the method.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its scratch
+ *     (reduction ticket, dot result, per-block partial sums, odd-parity temporary) is one
+ *     static device array of 8 MiB compiled into the library, present on every GPU that
+ *     loads it until the process exits.
+ *   - Size limit: V/2 <= 173392 sites for LQCD_FP64 and <= 346784 for LQCD_FP32 /
+ *     LQCD_FP32_R12 (e.g. 32^3 x 8 fits in every precision); larger lattices get
+ *     LQCD_ERR_ARG with a message naming the limit.
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current) and caches it; make that first call before any stream capture.
+ *   - Every call uses the same array: calls that may overlap on the GPU (other streams,
+ *     other host threads) race and must be serialised by the caller.  The ticket is reset
+ *     at each call; everything else is overwritten before it is read.
+ * The context itself (created and given a gauge field beforehand) is an input here.
+ */
+int lqcd_apply_A_noalloc(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
+
+/*
  * lqcd_neighbour_table - the geometry the kernels compute on the fly, written out.
  *   fwd_dev, bwd_dev : int32 [2 parities][4 mu][Vh] half index of x +- mu
  *   sign_dev         : int32 [2][4][Vh] eta_mu(x) times the boundary sign of the

@@ -46,7 +46,7 @@ MAX_SHIFTS = 32
 EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
-    "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count",
+    "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
 ]
 
 
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "lqcd_rational_coeffs": (i, [d, d, d, i, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                      ctypes.POINTER(d)]),
         "lqcd_launch_count": (ctypes.c_longlong, [vp]),
+        "lqcd_apply_A_noalloc": (i, [vp, vp, vp, d, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,13 @@ class Context:
         pq = ctypes.c_double(0.0)
         self.check(load_library().lqcd_apply_A(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
                                                ctypes.byref(pq) if want_dot else None))
+        return pq.value if want_dot else None
+
+    def apply_A_noalloc(self, q, p, sigma, prec, want_dot=False):
+        """apply_A with the library's static scratch instead of allocated scratch (see include/lqcd.h)."""
+        pq = ctypes.c_double(0.0)
+        self.check(load_library().lqcd_apply_A_noalloc(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
+                                                       ctypes.byref(pq) if want_dot else None))
         return pq.value if want_dot else None
 
     def neighbour_table(self, fwd, bwd, sign):
