@@ -105,12 +105,9 @@ def error_extrema(err, lo, hi, ngrid=20000, floor=1e-3):
     xs = np.exp(np.linspace(np.log(lo), np.log(hi), ngrid))
     e = err(xs)
     sg = np.sign(e)
-    runs = []  # (start, stop) index ranges of constant sign
-    start = 0
-    for i in range(1, ngrid + 1):
-        if i == ngrid or sg[i] != sg[start]:
-            runs.append((start, i))
-            start = i
+    cuts = np.nonzero(sg[1:] != sg[:-1])[0] + 1  # maximal runs of constant sign
+    bounds = np.concatenate([[0], cuts, [ngrid]])
+    runs = list(zip(bounds[:-1].tolist(), bounds[1:].tolist()))
     peak = max(np.max(np.abs(e[a:b])) for a, b in runs)
     kept = [(a, b) for a, b in runs if np.max(np.abs(e[a:b])) >= floor * peak]
     merged = []
@@ -143,3 +140,104 @@ def relative_error(c0, residues, poles, power, x):
 def max_relative_error(c0, residues, poles, power, lo, hi):
     ext = error_extrema(lambda x: relative_error(c0, residues, poles, power, x), lo, hi)
     return max(abs(v) for _, v in ext)
+
+
+# ---------------------------------------------------------------------------------------------
+# Exchange (Remez) algorithm for x^power, power in (-1, 0), and its reciprocal for (0, 1).
+#
+# Reading: the Appendix uses Mathematica's MiniMaxApproximation (a Remez-type exchange) at
+# 1000 digits.  Here the same characterisation is reached in double precision by working with
+# the product form R(x) = C prod_l (x + z_l) / (x + p_l) and the logarithmic error
+# E(x) = log R(x) - power log x, whose minimax solution agrees with the relative-error one to
+# second order in the error (|log(1+e) - e| ~ e^2 / 2, i.e. ~1e-22 here).  Steps:
+#   1. start from Zolotarev's solution for power = -1/2 and its alternation points;
+#   2. move power in small steps towards the target; at each step
+#      a. Newton-solve E(x_i) = (-1)^i eta at the 2n+2 reference points for (log C, log z_l,
+#         log p_l, eta),
+#      b. replace the reference points by the 2n+2 alternating extrema of E (exchange),
+#      repeating a-b until the extrema are level;
+#   3. for a positive target power, take the reciprocal of the solution for -power: zeros and
+#      poles swap and C -> 1/C (the logarithmic error just changes sign).
+# ---------------------------------------------------------------------------------------------
+def _log_error(logC, z, p, power, x):
+    x = np.asarray(x, dtype=np.float64)
+    prod = np.full_like(x, np.exp(logC))
+    for zl, pl in zip(z, p):
+        prod = prod * ((x + zl) / (x + pl))
+    return np.log(prod) - power * np.log(x)
+
+
+def _newton_level(logC, z, p, power, xs, iters=30):
+    """Solve E(x_i) = (-1)^i eta for the 2n+2 reference points by Newton's method."""
+    n = z.size
+    sgn = (-1.0) ** np.arange(xs.size)
+    eta = 0.0
+    u = np.concatenate([[logC], np.log(z), np.log(p), [eta]])
+    for _ in range(iters):
+        logC, lz, lp, eta = u[0], u[1:n + 1], u[n + 1:2 * n + 1], u[-1]
+        z, p = np.exp(lz), np.exp(lp)
+        F = _log_error(logC, z, p, power, xs) - sgn * eta
+        J = np.empty((xs.size, 2 * n + 2))
+        J[:, 0] = 1.0
+        J[:, 1:n + 1] = z[None, :] / (xs[:, None] + z[None, :])
+        J[:, n + 1:2 * n + 1] = -p[None, :] / (xs[:, None] + p[None, :])
+        J[:, -1] = -sgn
+        du = np.linalg.solve(J, -F)
+        u = u + du
+        if np.max(np.abs(du[:-1])) < 1e-14:
+            break
+    return u[0], np.exp(u[1:n + 1]), np.exp(u[n + 1:2 * n + 1]), u[-1]
+
+
+def remez_power(power, lo, hi, n, steps=None, tol_level=1e-3, max_exchange=40):
+    """Best relative (n, n) rational approximation of x^power on [lo, hi], -1 < power < 1.
+
+    Returns (c0, residues, poles, err) with r(x) = c0 + sum_k residues[k] / (x + poles[k])
+    and err = max_x |r(x) / x^power - 1|.
+    """
+    if not (-1.0 < power < 1.0) or power == 0.0:
+        raise ValueError("power must lie in (-1, 0) or (0, 1)")
+    target = -abs(power)
+    # 1. Zolotarev start for -1/2
+    c0, res, poles, _ = zolotarev_inv_sqrt(n, lo, hi)
+    poles = np.sort(poles)
+    # zeros of R from the partial fractions: recover them as the roots of the numerator by
+    # using the closed form again (zeros interlace the poles)
+    kappa = hi / lo
+    mprime = 1.0 - 1.0 / kappa
+    Kp = special.ellipk(mprime)
+    l = np.arange(1, 2 * n + 1)
+    sn, cn, _, _ = special.ellipj(l * Kp / (2 * n + 1), mprime)
+    c = sn ** 2 / cn ** 2
+    z = lo * c[1::2]
+    p = lo * c[0::2]
+    logC = np.log(c0)
+    ext = error_extrema(lambda x: _log_error(logC, z, p, -0.5, x), lo, hi, floor=0.1)
+    xs = np.array([x for x, _ in ext])
+    # 2. continuation in the power
+    nsteps = steps if steps is not None else max(1, int(round(abs(target + 0.5) / 0.025)))
+    path = np.linspace(-0.5, target, nsteps + 1)[1:] if target != -0.5 else np.array([-0.5])
+    for step, pw in enumerate(path):
+        final = step == len(path) - 1
+        for _ in range(max_exchange if final else 4):
+            logC, z, p, eta = _newton_level(logC, z, p, pw, xs)
+            # floor 0.1: the true extrema are within a small factor of each other, while rounding
+            # noise of the ~1e-13 errors of the largest cases makes spurious sign runs near zeros
+            ext = error_extrema(lambda x: _log_error(logC, z, p, pw, x), lo, hi, floor=0.1)
+            vals = np.abs([v for _, v in ext])
+            if len(ext) == 2 * n + 2:
+                new = np.array([x for x, _ in ext])
+                moved = np.max(np.abs(np.log(new / xs)))
+                xs = new
+                # level, or the reference no longer moves (rounding noise limits the levelling)
+                if vals.max() / vals.min() - 1 < tol_level or moved < 1e-5:
+                    break
+    # 3. reciprocal for a positive power
+    if power > 0:
+        logC, z, p = -logC, p, z
+    order = np.argsort(p)
+    z, p = z, p[order]
+    C = np.exp(logC)
+    c0, res = product_to_partial_fractions(C, z, p)
+    err = max_relative_error(c0, res, p, power, lo, hi)
+    return c0, res, p, err

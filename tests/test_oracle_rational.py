@@ -53,3 +53,59 @@ def test_error_decreases_geometrically_with_poles():
     assert all(b < a for a, b in zip(errs, errs[1:]))
     ratios = [b / a for a, b in zip(errs, errs[1:])]
     assert max(ratios) / min(ratios) < 1.2
+
+
+@pytest.mark.parametrize("n,mass", [(12, 0.1), (16, 0.02)])
+def test_remez_quarter_power_equioscillates(n, mass):
+    lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
+    c0, res, poles, err = rational.remez_power(0.25, lo, hi, n)
+    ext = rational.error_extrema(lambda x: rational.relative_error(c0, res, poles, 0.25, x), lo, hi, floor=0.1)
+    vals = np.array([v for _, v in ext])
+    assert vals.size == 2 * n + 2
+    assert np.all(np.sign(vals[1:]) == -np.sign(vals[:-1]))
+    assert np.max(np.abs(vals)) / np.min(np.abs(vals)) < 1.02
+    # sign structure of x^{1/4}: c0 > 0, residues < 0, poles > 0
+    assert c0 > 0 and np.all(res < 0) and np.all(poles > 0)
+    assert err < 1e-10
+
+
+def test_remez_reproduces_zolotarev_for_inverse_sqrt():
+    lo, hi, n = 0.01, 16.01, 10
+    c0, res, poles, err = rational.remez_power(-0.5, lo, hi, n)
+    zc0, zres, zpoles, zerr = rational.zolotarev_inv_sqrt(n, lo, hi)
+    assert np.allclose(np.sort(poles), np.sort(zpoles), rtol=1e-6)
+    assert abs(err - zerr) < 0.02 * zerr
+
+
+def test_appendix_claim_24_poles_quarter_power():
+    # Appendix: degree 24/24 approximation of x^{1/4} on [5e-5, 34] has error below 1e-12
+    c0, res, poles, err = rational.remez_power(0.25, 5e-5, 34.0, 24)
+    assert err < 1e-12
+    ext = rational.error_extrema(lambda x: rational.relative_error(c0, res, poles, 0.25, x), 5e-5, 34.0, floor=0.1)
+    vals = np.array([v for _, v in ext])
+    assert vals.size == 50 and np.all(np.sign(vals[1:]) == -np.sign(vals[:-1]))
+
+
+def test_quarter_squared_times_inverse_sqrt_is_one():
+    # r_{1/4}(x)^2 r_{-1/2}(x) = 1 up to the combined approximation errors on the whole interval
+    lo, hi, n = 0.0016, 16.0016, 16
+    a = rational.remez_power(0.25, lo, hi, n)
+    b = rational.zolotarev_inv_sqrt(n, lo, hi)
+    x = np.exp(np.linspace(np.log(lo), np.log(hi), 5001))
+    prod = rational.rational_eval(*a[:3], x) ** 2 * rational.rational_eval(*b[:3], x)
+    assert np.max(np.abs(prod - 1)) <= 2.2 * a[3] + 1.1 * b[3]
+
+
+def test_quarter_power_of_a_dense_operator():
+    from oracle import staggered
+    from paper_1710_09178_gb300 import inputs
+
+    dims, mass = (4, 4, 4, 4), 0.1
+    U = inputs.gauge_field(dims, seed=1)
+    A = staggered.dense_A(U, mass, dims)
+    w, Q = np.linalg.eigh(A)
+    lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
+    c0, res, poles, err = rational.remez_power(0.25, lo, hi, 12)
+    rA = c0 * np.eye(A.shape[0]) + sum(c * np.linalg.inv(A + d * np.eye(A.shape[0])) for c, d in zip(res, poles))
+    exact = (Q * w ** 0.25) @ Q.conj().T
+    assert np.linalg.norm(rA - exact, 2) <= 1.5 * err * np.max(w ** 0.25)
