@@ -95,3 +95,29 @@ def test_rational_coeffs_rejects_bad_interval(lib):
     for args in [(-0.5, 0.0, 1.0, 4), (-0.5, 2.0, 1.0, 4), (-0.5, 0.1, 1.0, 0), (-0.5, 0.1, 1.0, 40)]:
         with pytest.raises(LqcdError):
             rational_coeffs(*args)
+
+
+@pytest.mark.parametrize("power,n,mass", [(0.25, 12, 0.1), (0.25, 16, 0.02), (-0.25, 14, 0.05)])
+def test_rational_coeffs_remez_match_oracle(lib, power, n, mass):
+    from oracle import rational
+    from paper_1710_09178_gb300 import rational_coeffs
+
+    lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
+    c0, res, poles, err = rational_coeffs(power, lo, hi, n)
+    oc0, ores, opoles, oerr = rational.remez_power(power, lo, hi, n)
+    assert np.allclose(np.sort(poles), np.sort(opoles), rtol=1e-4, atol=0)
+    assert abs(c0 - oc0) < 1e-4 * abs(oc0)  # both level the error only to its ~1e-3 rounding noise
+    # the library's result satisfies the alternation theorem under the oracle's own scan
+    ext = rational.error_extrema(lambda x: rational.relative_error(c0, res, poles, power, x), lo, hi, floor=0.1)
+    vals = np.array([v for _, v in ext])
+    assert vals.size == 2 * n + 2 and np.all(np.sign(vals[1:]) == -np.sign(vals[:-1]))
+    assert np.max(np.abs(vals)) <= 1.05 * oerr
+
+
+def test_rational_coeffs_appendix_case(lib):
+    # Appendix: 24/24 approximation of x^{1/4} on [5e-5, 34] with error below 1e-12
+    from oracle import rational
+    from paper_1710_09178_gb300 import rational_coeffs
+
+    c0, res, poles, err = rational_coeffs(0.25, 5e-5, 34.0, 24)
+    assert rational.max_relative_error(c0, res, poles, 0.25, 5e-5, 34.0) < 1e-12
