@@ -261,6 +261,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_target(kind, prec_name):
+    """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
+    `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1710_09178_gb300 as lq
+    from paper_1710_09178_gb300 import inputs
+
+    prec = lq.PRECISIONS[prec_name]
+    ctx = lq.Context(DIMS, MASS)
+    ctx.set_gauge(torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda())
+    if kind == "dslash":
+        vin = ctx.new_vector(prec)
+        vout = ctx.new_vector(prec)
+        vin.view(torch.float32 if prec != lq.FP64 else torch.float64).normal_()
+        for r in range(8):
+            lq.dslash_eo(ctx, vout, vin, r & 1, prec)
+    else:
+        ctx.set_option(lq.OPT_USE_GRAPH, 0)
+        b = torch.from_numpy(inputs.gaussian_vector(DIMS, VEC_SEED)).cuda()
+        c0, res, poles, _ = lq.rational_coeffs(-0.5, 4 * MASS * MASS, 16 + 4 * MASS * MASS, NPOLES)
+        xs = [torch.empty_like(b) for _ in range(NPOLES)]
+        y = torch.empty_like(b)
+        rc, st = lq.mshift_cg(ctx, poles, res, c0, b, xs, y, tol=TOL, prec=prec)
+        print(json.dumps({"profile": "solve", "rc": rc, "iterations": st["iterations"],
+                          "refine_iterations": st["refine_iterations"], "launches": ctx.launch_count()}))
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -268,8 +301,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="mixed mode only (for profiling runs)")
+    ap.add_argument("--quick", action="store_true", help="mixed mode only")
+    ap.add_argument("--profile", choices=["dslash", "solve"], help="run a small fixed workload for ncu and exit")
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix"])
     args = ap.parse_args()
+    if args.profile:
+        run_profile_target(args.profile, args.prec)
+        return
     args.warmup = max(args.warmup, 3)
 
     rank = env_int("RANK", 0)

@@ -67,6 +67,7 @@ typedef struct {
   int reliable_updates;   /* FP64 residual recomputations */
   int refine_iterations;  /* CG iterations spent in per-shift refinement */
   int refined_shifts;     /* shifts that needed refinement */
+  int refine_rounds;      /* refinement passes (each: one batched solve, then FP64 residual checks) */
   int kernel_launches;    /* kernels this call launched (graph nodes counted) */
   int n_shifts;
   double true_residual[LQCD_MAX_SHIFTS]; /* |b - (A + d_k) x_k| / |b| in FP64, per shift */

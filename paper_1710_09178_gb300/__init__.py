@@ -56,6 +56,7 @@ class SolveStats(ctypes.Structure):
         ("reliable_updates", ctypes.c_int),
         ("refine_iterations", ctypes.c_int),
         ("refined_shifts", ctypes.c_int),
+        ("refine_rounds", ctypes.c_int),
         ("kernel_launches", ctypes.c_int),
         ("n_shifts", ctypes.c_int),
         ("true_residual", ctypes.c_double * MAX_SHIFTS),
@@ -66,6 +67,7 @@ class SolveStats(ctypes.Structure):
         n = self.n_shifts
         return dict(iterations=self.iterations, reliable_updates=self.reliable_updates,
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
+                    refine_rounds=self.refine_rounds,
                     kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms)
 
 

@@ -82,6 +82,7 @@ int lqcd_create(lqcd_ctx** out, const int dims[4], double mass, void* stream) {
 int lqcd_destroy(lqcd_ctx* ctx) {
   if (!ctx) return LQCD_OK;
   free_workspace(ctx);
+  mrhs_release(ctx);
   void* bufs[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->partials, ctx->tickets, ctx->scalars,
                   ctx->tmp_odd};
   for (void* b : bufs)
@@ -235,6 +236,7 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
     default: return fail(ctx, LQCD_ERR_ARG, "unknown option");
   }
   free_workspace(ctx);  // captured graphs depend on the options
+  mrhs_release(ctx);
   return LQCD_OK;
 }
 

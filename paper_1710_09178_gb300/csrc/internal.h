@@ -60,6 +60,7 @@ struct GaugeCopies {
 };
 
 struct Workspace;
+struct MrhsWorkspace;
 
 }  // namespace lqcd
 
@@ -79,6 +80,7 @@ struct lqcd_ctx {
   int use_graph = 1;
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;
+  lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
   double* partials = nullptr;  // reduction scratch, one double per block
   void* tmp_odd = nullptr;     // odd-parity temporary of lqcd_apply_A (sized for FP64)
   unsigned* tickets = nullptr;  // reduction tickets for stand-alone reductions
@@ -124,5 +126,12 @@ int dslash_grid_blocks(const Geom& g, int prec, int tps);
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
                double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats);
 void free_workspace(lqcd_ctx* ctx);
+
+// mrhs.cu: many shifted systems (A + sigma_j) e_j = r_j solved together (per-shift refinement)
+int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out);
+int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter, cudaStream_t st,
+               int* iters, int* status);
+void* const* mrhs_solutions(lqcd_ctx* ctx);
+void mrhs_release(lqcd_ctx* ctx);
 
 }  // namespace lqcd

@@ -1,0 +1,526 @@
+// mrhs.cu - many independent shifted CG solves sharing one operator:
+//     (A + sigma_j) e_j = r_j,   j = 1..m,   A = 4m^2 - D_eo D_oe,
+// used for the per-shift refinement of the shifted CG (each shift's FP64 true residual is the
+// right-hand side of its correction equation).  The systems advance in lock step; the
+// Dslash kernels load every link once per group of G systems and apply it to each of them
+// (multi-right-hand-side Dslash), so link traffic per system drops by G.  Every system has
+// its own alpha, beta and stopping test (FP64 dot products); a system that has converged
+// leaves the compacted list of active systems and costs nothing afterwards.
+//
+// One iteration is four kernels: D_oe on the p_j, D_eo with the A-apply and (p_j, q_j) epilogue,
+// the e/r update with (r_j, r_j), the p update.  A CUDA graph with a conditional while-node
+// repeats two iterations per pass until every system has converged (bounded by a pass count).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lqcd {
+
+constexpr int kMrhsMax = kMaxShifts;
+constexpr int kMrhsGroup = 8;  // systems per link load in the multi-RHS Dslash
+
+struct MrhsDev {
+  int m;
+  int n_active;
+  int list[kMrhsMax];  // active system ids, compacted
+  int iter, maxiter, done, status;
+  int passes, max_passes;
+  unsigned ticket[4];
+  double a[kMrhsMax];  // 4 m^2 + sigma_j
+  double rr[kMrhsMax], stop2[kMrhsMax], alpha[kMrhsMax], beta[kMrhsMax];
+};
+
+struct MrhsVecs {
+  void* p[kMrhsMax];
+  void* q[kMrhsMax];
+  void* r[kMrhsMax];
+  void* e[kMrhsMax];
+  void* tmp[kMrhsMax];
+};
+
+template <typename T>
+struct V2Of;
+template <>
+struct V2Of<float> {
+  typedef float2 type;
+};
+template <>
+struct V2Of<double> {
+  typedef double2 type;
+};
+
+// acc -= M^dagger v
+template <typename T>
+__device__ __forceinline__ void mdv_sub(Vec3<T>& out, const Mat3<T>& M, const Vec3<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const Cplx<T>& m = M.e[b][a];
+      out.c[a].re = fma(-m.re, v.c[b].re, out.c[a].re);
+      out.c[a].re = fma(-m.im, v.c[b].im, out.c[a].re);
+      out.c[a].im = fma(-m.re, v.c[b].im, out.c[a].im);
+      out.c[a].im = fma(m.im, v.c[b].re, out.c[a].im);
+    }
+  }
+}
+
+template <int LF>
+__device__ __forceinline__ auto mrhs_link(const void* links, int p, int mu, int i, int vh, int sign, uint64_t pol) {
+  if constexpr (LF == 0) return load_link64(static_cast<const double2*>(links), p, mu, i, vh, pol);
+  else if constexpr (LF == 1) return load_link32(static_cast<const float*>(links), p, mu, i, vh, pol);
+  else return load_link12(static_cast<const float4*>(links), p, mu, i, vh, 0.5f * (float)sign, pol);
+}
+
+// Multi-RHS half Dslash over the systems list[blockIdx.y*G .. +G).  AAPPLY: out = a_j aux - D in,
+// with Re<aux, out> per system; otherwise out = D in.
+template <int LF, typename T, bool AAPPLY>
+__global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* links, MrhsVecs vv, int out_parity,
+                                                          MrhsDev* md, double* partials) {
+  typedef typename V2Of<T>::type V2;
+  const int n_act = md->n_active;
+  if (md->done) return;
+  const int g0 = blockIdx.y * kMrhsGroup;
+  if (g0 >= n_act) return;  // uniform over the blocks of this group
+  const int ng = min(kMrhsGroup, n_act - g0);
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = out_parity;
+  int sys[kMrhsGroup];
+#pragma unroll
+  for (int q = 0; q < kMrhsGroup; ++q) sys[q] = (q < ng) ? md->list[g0 + q] : 0;
+  Vec3<T> acc[kMrhsGroup];
+#pragma unroll
+  for (int q = 0; q < kMrhsGroup; ++q) acc[q] = vzero<T>();
+  if (i < vh) {
+    Site s = site_of(g, p, i);
+    const uint64_t pol = (LF == 0) ? policy_evict_first() : policy_evict_last();
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int mu = h >> 1;
+      const bool fwd = (h & 1) == 0;
+      const int j = (fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu)) >> 1;
+      const int sg = (LF == 2) ? (fwd ? link_sign_fwd(g, s, mu) : link_sign_bwd(g, s, mu)) : 1;
+      auto W = fwd ? mrhs_link<LF>(links, p, mu, i, vh, sg, pol) : mrhs_link<LF>(links, 1 - p, mu, j, vh, sg, pol);
+#pragma unroll
+      for (int q = 0; q < kMrhsGroup; ++q) {
+        if (q < ng) {
+          const V2* in = static_cast<const V2*>(AAPPLY ? vv.tmp[sys[q]] : vv.p[sys[q]]);
+          Vec3<T> v = ldg_vec(in, j, vh);
+          if (fwd) mv_acc(acc[q], W, v);
+          else mdv_sub(acc[q], W, v);
+        }
+      }
+    }
+  }
+  if constexpr (!AAPPLY) {
+    if (i < vh) {
+#pragma unroll
+      for (int q = 0; q < kMrhsGroup; ++q)
+        if (q < ng) store_vec(static_cast<V2*>(vv.tmp[sys[q]]), i, vh, acc[q]);
+    }
+  } else {
+    for (int q = 0; q < kMrhsGroup; ++q) {
+      if (q >= ng) break;  // uniform
+      T d = 0;
+      if (i < vh) {
+        const int sj = sys[q];
+        const T a = (T)md->a[sj];
+        Vec3<T> pv = load_vec(static_cast<const V2*>(vv.p[sj]), i, vh);
+        Vec3<T> qv;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          qv.c[c].re = a * pv.c[c].re - acc[q].c[c].re;
+          qv.c[c].im = a * pv.c[c].im - acc[q].c[c].im;
+          d += pv.c[c].re * qv.c[c].re + pv.c[c].im * qv.c[c].im;
+        }
+        store_vec(static_cast<V2*>(vv.q[sj]), i, vh, qv);
+      }
+      double bsum = block_sum_mixed(d);
+      if (threadIdx.x == 0) partials[(size_t)(g0 + q) * gridDim.x + blockIdx.x] = bsum;
+    }
+    // last block over the whole grid (all groups): alpha_j = (r_j, r_j) / (p_j, q_j)
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned nblk = gridDim.x * (unsigned)((n_act + kMrhsGroup - 1) / kMrhsGroup);
+      last = (atomicAdd(&md->ticket[0], 1u) == nblk - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      for (int pos = 0; pos < n_act; ++pos) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
+        v = block_sum(v);
+        if (threadIdx.x == 0) {
+          int sj = md->list[pos];
+          double alpha = md->rr[sj] / v;
+          if (!(v > 0.0) || !isfinite(alpha)) {
+            md->status = LQCD_ERR_NONFINITE;
+            md->done = 1;
+          }
+          md->alpha[sj] = alpha;
+        }
+      }
+      if (threadIdx.x == 0) md->ticket[0] = 0u;
+    }
+  }
+}
+
+// e_j += alpha_j p_j;  r_j -= alpha_j q_j;  (r_j, r_j) -> beta_j, stopping test, list compaction
+template <typename T>
+__global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, MrhsDev* md, double* partials) {
+  typedef typename V2Of<T>::type V2;
+  const int n_act = md->n_active;
+  if (md->done) return;
+  const int g0 = blockIdx.y * kMrhsGroup;
+  if (g0 >= n_act) return;
+  const int ng = min(kMrhsGroup, n_act - g0);
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int q = 0; q < ng; ++q) {
+    const int sj = md->list[g0 + q];
+    const T alpha = (T)md->alpha[sj];
+    T d = 0;
+    if (i < vh) {
+      Vec3<T> pv = load_vec(static_cast<const V2*>(vv.p[sj]), i, vh);
+      Vec3<T> qv = load_vec(static_cast<const V2*>(vv.q[sj]), i, vh);
+      Vec3<T> rv = load_vec(static_cast<const V2*>(vv.r[sj]), i, vh);
+      Vec3<T> ev = load_vec(static_cast<const V2*>(vv.e[sj]), i, vh);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        ev.c[c].re = fma(alpha, pv.c[c].re, ev.c[c].re);
+        ev.c[c].im = fma(alpha, pv.c[c].im, ev.c[c].im);
+        rv.c[c].re = fma(-alpha, qv.c[c].re, rv.c[c].re);
+        rv.c[c].im = fma(-alpha, qv.c[c].im, rv.c[c].im);
+        d += rv.c[c].re * rv.c[c].re + rv.c[c].im * rv.c[c].im;
+      }
+      store_vec(static_cast<V2*>(vv.e[sj]), i, vh, ev);
+      store_vec(static_cast<V2*>(vv.r[sj]), i, vh, rv);
+    }
+    double bsum = block_sum_mixed(d);
+    if (threadIdx.x == 0) partials[(size_t)(g0 + q) * gridDim.x + blockIdx.x] = bsum;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned nblk = gridDim.x * (unsigned)((n_act + kMrhsGroup - 1) / kMrhsGroup);
+    last = (atomicAdd(&md->ticket[1], 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ int keep[kMrhsMax];
+  for (int pos = 0; pos < n_act; ++pos) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+      int sj = md->list[pos];
+      double beta = v / md->rr[sj];
+      if (!isfinite(v)) {
+        md->status = LQCD_ERR_NONFINITE;
+        md->done = 1;
+      }
+      md->beta[sj] = beta;
+      md->rr[sj] = v;
+      keep[pos] = !(v <= md->stop2[sj]);
+    }
+  }
+  if (threadIdx.x == 0) {
+    int w = 0;
+    for (int pos = 0; pos < n_act; ++pos)
+      if (keep[pos]) md->list[w++] = md->list[pos];
+    md->n_active = w;
+    md->iter += 1;
+    if (w == 0 || md->iter >= md->maxiter) md->done = 1;
+    md->ticket[1] = 0u;
+  }
+}
+
+// p_j = r_j + beta_j p_j for the systems still active
+template <typename T>
+__global__ void __launch_bounds__(256) mrhs_pupdate_kernel(Geom g, MrhsVecs vv, MrhsDev* md) {
+  typedef typename V2Of<T>::type V2;
+  if (md->done) return;
+  const int n_act = md->n_active;
+  const int g0 = blockIdx.y * kMrhsGroup;
+  if (g0 >= n_act) return;
+  const int ng = min(kMrhsGroup, n_act - g0);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 3 * g.vh) return;
+  for (int q = 0; q < ng; ++q) {
+    const int sj = md->list[g0 + q];
+    const T beta = (T)md->beta[sj];
+    V2 rv = static_cast<const V2*>(vv.r[sj])[k];
+    V2 pv = static_cast<V2*>(vv.p[sj])[k];
+    pv.x = fma(beta, pv.x, rv.x);
+    pv.y = fma(beta, pv.y, rv.y);
+    static_cast<V2*>(vv.p[sj])[k] = pv;
+  }
+}
+
+// e_j = 0, p_j = r_j, (r_j, r_j); the last block sets the scalars of a fresh solve
+struct MrhsInit {
+  int m, maxiter;
+  double a[kMrhsMax];
+  double rel2[kMrhsMax];  // squared relative reduction each system must reach
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) mrhs_init_kernel(Geom g, MrhsVecs vv, MrhsDev* md, MrhsInit in,
+                                                        double* partials) {
+  typedef typename V2Of<T>::type V2;
+  const int g0 = blockIdx.y * kMrhsGroup;
+  const int ng = min(kMrhsGroup, in.m - g0);
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int q = 0; q < ng; ++q) {
+    const int sj = g0 + q;
+    T d = 0;
+    if (i < vh) {
+      Vec3<T> rv = load_vec(static_cast<const V2*>(vv.r[sj]), i, vh);
+      store_vec(static_cast<V2*>(vv.p[sj]), i, vh, rv);
+      store_vec(static_cast<V2*>(vv.e[sj]), i, vh, vzero<T>());
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d += rv.c[c].re * rv.c[c].re + rv.c[c].im * rv.c[c].im;
+    }
+    double bsum = block_sum_mixed(d);
+    if (threadIdx.x == 0) partials[(size_t)sj * gridDim.x + blockIdx.x] = bsum;
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(&md->ticket[2], 1u) == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int sj = 0; sj < in.m; ++sj) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)sj * gridDim.x + b);
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+      md->rr[sj] = v;
+      md->stop2[sj] = in.rel2[sj] * v;
+      md->a[sj] = in.a[sj];
+      md->alpha[sj] = md->beta[sj] = 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    int w = 0;
+    for (int sj = 0; sj < in.m; ++sj)
+      if (md->rr[sj] > md->stop2[sj] && md->rr[sj] > 0.0) md->list[w++] = sj;
+    md->m = in.m;
+    md->n_active = w;
+    md->iter = 0;
+    md->maxiter = in.maxiter;
+    md->status = LQCD_OK;
+    md->done = (w == 0) ? 1 : 0;
+    md->passes = 0;
+    md->max_passes = in.maxiter / 2 + 2;
+    md->ticket[2] = 0u;
+  }
+}
+
+__global__ void mrhs_ctl_kernel(cudaGraphConditionalHandle handle, MrhsDev* md) {
+  if (threadIdx.x != 0) return;
+  int np = md->passes + 1;
+  md->passes = np;
+  cudaGraphSetConditional(handle, (!md->done && np < md->max_passes) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+struct MrhsWorkspace {
+  int prec = -1;
+  int m_cap = 0;
+  size_t vbytes = 0;
+  MrhsVecs vv;
+  MrhsDev* md = nullptr;
+  double* partials = nullptr;
+  int nbx = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_m = -1;
+  int graph_prec = -1;
+  int nodes_per_pass = 0;
+};
+
+static void mrhs_free(MrhsWorkspace* mw) {
+  if (!mw) return;
+  if (mw->graph) cudaGraphExecDestroy(mw->graph);
+  for (int j = 0; j < kMrhsMax; ++j) {
+    void* bufs[] = {mw->vv.p[j], mw->vv.q[j], mw->vv.r[j], mw->vv.e[j], mw->vv.tmp[j]};
+    for (void* b : bufs)
+      if (b) cudaFree(b);
+  }
+  if (mw->md) cudaFree(mw->md);
+  if (mw->partials) cudaFree(mw->partials);
+  delete mw;
+}
+
+void mrhs_release(lqcd_ctx* ctx) {
+  mrhs_free(ctx->mrhs);
+  ctx->mrhs = nullptr;
+}
+
+// Buffers for m systems of precision prec (FP64 vectors for LQCD_FP64, FP32 otherwise).
+int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out) {
+  MrhsWorkspace* mw = ctx->mrhs;
+  const bool dbl = prec == LQCD_FP64;
+  if (!mw || mw->prec != (dbl ? 1 : 0) || mw->m_cap < m) {
+    mrhs_release(ctx);
+    mw = new MrhsWorkspace();
+    memset(&mw->vv, 0, sizeof(mw->vv));
+    ctx->mrhs = mw;
+    mw->prec = dbl ? 1 : 0;
+    mw->m_cap = m;
+    mw->vbytes = (dbl ? 48 : 24) * (size_t)ctx->Vh;
+    cudaError_t e;
+    for (int j = 0; j < m; ++j) {
+      void** bufs[] = {&mw->vv.p[j], &mw->vv.q[j], &mw->vv.r[j], &mw->vv.e[j], &mw->vv.tmp[j]};
+      for (void** b : bufs)
+        if ((e = cudaMalloc(b, mw->vbytes)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc(mrhs)");
+    }
+    if ((e = cudaMalloc(&mw->md, sizeof(MrhsDev))) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc(mrhs)");
+    mw->nbx = (int)((ctx->Vh + 127) / 128);
+    if ((e = cudaMalloc(&mw->partials, sizeof(double) * kMrhsMax * (size_t)mw->nbx)) != cudaSuccess)
+      return cuda_check(ctx, e, "cudaMalloc(mrhs)");
+    if ((e = cudaMemset(mw->md, 0, sizeof(MrhsDev))) != cudaSuccess) return cuda_check(ctx, e, "cudaMemset(mrhs)");
+  }
+  *rhs_out = mw->vv.r;
+  return LQCD_OK;
+}
+
+template <typename T>
+static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, const Geom& g, int prec, int groups,
+                                          cudaStream_t st, int* nl) {
+  dim3 grid(mw->nbx, groups);
+  const void* links = prec == LQCD_FP64 ? (const void*)ctx->gauge.u64
+                      : prec == LQCD_FP32_R12 ? (const void*)ctx->gauge.u12 : (const void*)ctx->gauge.u32;
+  if (prec == LQCD_FP64) {
+    mrhs_dslash_kernel<0, double, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
+    mrhs_dslash_kernel<0, double, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+  } else if (prec == LQCD_FP32_R12) {
+    mrhs_dslash_kernel<2, float, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
+    mrhs_dslash_kernel<2, float, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+  } else {
+    mrhs_dslash_kernel<1, float, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
+    mrhs_dslash_kernel<1, float, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+  }
+  mrhs_update_kernel<T><<<grid, 128, 0, st>>>(g, mw->vv, mw->md, mw->partials);
+  dim3 grid3((3 * g.vh + 255) / 256, groups);
+  mrhs_pupdate_kernel<T><<<grid3, 256, 0, st>>>(g, mw->vv, mw->md);
+  *nl += 4;
+  return cudaGetLastError();
+}
+
+// Solve (A + sigma_j) e_j = r_j (r_j already in the workspace's r buffers) until
+// |r_j| <= rel_j |r_j(0)| for every j, or maxiter.  Returns iterations in *iters.
+int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter,
+               cudaStream_t st, int* iters, int* status) {
+  MrhsWorkspace* mw = ctx->mrhs;
+  Geom g = make_geom(ctx);
+  const int groups = (m + kMrhsGroup - 1) / kMrhsGroup;
+  MrhsInit in;
+  memset(&in, 0, sizeof(in));
+  in.m = m;
+  in.maxiter = maxiter;
+  for (int j = 0; j < m; ++j) {
+    in.a[j] = 4.0 * ctx->mass * ctx->mass + sigma[j];
+    in.rel2[j] = rel[j] * rel[j];
+  }
+  dim3 grid(mw->nbx, groups);
+  int nl = 0;
+  if (prec == LQCD_FP64) mrhs_init_kernel<double><<<grid, 128, 0, st>>>(g, mw->vv, mw->md, in, mw->partials);
+  else mrhs_init_kernel<float><<<grid, 128, 0, st>>>(g, mw->vv, mw->md, in, mw->partials);
+  nl += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs_init");
+  if (!ctx->use_graph) {
+    // plain launches, the host polls the done flag every two iterations
+    int hs[4] = {0, 0, 0, 0};
+    for (int pass = 0; pass < maxiter / 2 + 2; ++pass) {
+      for (int it = 0; it < 2 && e == cudaSuccess; ++it)
+        e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nl)
+                                : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nl);
+      if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs iteration");
+      if ((e = cudaMemcpyAsync(hs, &mw->md->iter, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_check(ctx, e, "mrhs readback");
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_check(ctx, e, "mrhs sync");
+      if (hs[2]) break;
+    }
+    ctx->launches += nl;
+    *iters = hs[0];
+    *status = hs[3];
+    return LQCD_OK;
+  }
+  if (!mw->graph || mw->graph_m != m || mw->graph_prec != prec) {
+    if (mw->graph) cudaGraphExecDestroy(mw->graph);
+    mw->graph = nullptr;
+    cudaGraph_t graph;
+    if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return cuda_check(ctx, e, "cudaGraphCreate");
+    cudaGraphConditionalHandle handle;
+    if ((e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return cuda_check(ctx, e, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if ((e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess)
+      return cuda_check(ctx, e, "cudaGraphAddNode");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return cuda_check(ctx, e, "cudaStreamBeginCaptureToGraph");
+    int nodes = 0;
+    for (int it = 0; it < 2 && e == cudaSuccess; ++it)
+      e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nodes)
+                              : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nodes);
+    if (e == cudaSuccess) {
+      mrhs_ctl_kernel<<<1, 32, 0, st>>>(handle, mw->md);
+      nodes += 1;
+      e = cudaGetLastError();
+    }
+    cudaGraph_t captured;
+    cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs capture");
+    if (e2 != cudaSuccess) return cuda_check(ctx, e2, "mrhs capture");
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGraphInstantiate(mrhs)");
+    mw->graph = exec;
+    mw->graph_m = m;
+    mw->graph_prec = prec;
+    mw->nodes_per_pass = nodes;
+  }
+  if ((e = cudaGraphLaunch(mw->graph, st)) != cudaSuccess) return cuda_check(ctx, e, "cudaGraphLaunch(mrhs)");
+  int hs[4];
+  if ((e = cudaMemcpyAsync(hs, &mw->md->iter, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_check(ctx, e, "mrhs readback");
+  int passes = 0;
+  if ((e = cudaMemcpyAsync(&passes, &mw->md->passes, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_check(ctx, e, "mrhs readback");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_check(ctx, e, "mrhs sync");
+  ctx->launches += nl + (long long)passes * mw->nodes_per_pass;
+  *iters = hs[0];
+  *status = hs[3] != LQCD_OK ? hs[3] : LQCD_OK;
+  return LQCD_OK;
+}
+
+void* const* mrhs_solutions(lqcd_ctx* ctx) { return ctx->mrhs->vv.e; }
+
+}  // namespace lqcd

@@ -731,19 +731,52 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   return LQCD_OK;
 }
 
-// FP64 true residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts
+// r (FP64 internal) -> dst in the refinement precision (FP32 copy or FP64 copy)
+__global__ void keep_residual_kernel(int n3, const double2* __restrict__ r64, void* __restrict__ dst, int to_f32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double2 v = r64[i];
+  if (to_f32) static_cast<float2*>(dst)[i] = make_float2((float)v.x, (float)v.y);
+  else static_cast<double2*>(dst)[i] = v;
+}
+
+// x (FP64) += e (FP32 or FP64)
+__global__ void add_correction_kernel(int n3, double2* __restrict__ x, const void* __restrict__ e, int from_f32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double2 a = x[i];
+  if (from_f32) {
+    float2 b = static_cast<const float2*>(e)[i];
+    a.x += (double)b.x;
+    a.y += (double)b.y;
+  } else {
+    double2 b = static_cast<const double2*>(e)[i];
+    a.x += b.x;
+    a.y += b.y;
+  }
+  x[i] = a;
+}
+
+// FP64 true residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts; when keep is not
+// null each residual is also stored in keep[k] (refinement precision) as a right-hand side.
 static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts,
-                          const std::vector<int>& ks, double bnorm2, double* out) {
+                          const std::vector<int>& ks, double bnorm2, double* out, void* const* keep, int keep_f32) {
   Workspace* w = ctx->ws;
   Launcher L{ctx, w, make_geom(ctx), 0};
+  const int n3 = 3 * L.g.vh;
   for (size_t j = 0; j < ks.size(); ++j) {
     int k = ks[j];
     LQ_CUDA(enqueue_resid64(L, xs[k], b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
+    if (keep) {
+      keep_residual_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->r64, keep[k], keep_f32);
+      L.nlaunch += 1;
+      LQ_CUDA(cudaGetLastError());
+    }
   }
   LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->scal[4], sizeof(double) * ks.size(), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
   ctx->launches += L.nlaunch;
-  for (size_t j = 0; j < ks.size(); ++j) out[j] = sqrt(w->host_scal[j] / bnorm2);
+  for (size_t j = 0; j < ks.size(); ++j) out[ks[j]] = sqrt(w->host_scal[j] / bnorm2);
   return LQCD_OK;
 }
 
@@ -769,39 +802,48 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
 
   double tres[kMaxShifts];
   for (int k = 0; k < n; ++k) tres[k] = 0.0;
-  int refine_iters = 0, refined = 0, status = st_main;
+  int refine_iters = 0, refined = 0, rounds_done = 0, status = st_main;
   if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
     std::vector<int> all(n);
     for (int k = 0; k < n; ++k) all[k] = k;
-    rc = true_residuals(ctx, w->b64, w->xk, shifts, all, bb, tres);
+    const bool refine = ctx->refine && st_main == LQCD_OK;
+    void* const* rhs = nullptr;
+    const int f32 = prec != LQCD_FP64;
+    if (refine) {
+      rc = mrhs_prepare(ctx, prec, n, &rhs);
+      if (rc != LQCD_OK) return rc;
+    }
+    rc = true_residuals(ctx, w->b64, w->xk, shifts, all, bb, tres, rhs, f32);
     if (rc != LQCD_OK) return rc;
-    if (ctx->refine && st_main == LQCD_OK) {
-      // per-shift refinement: (A + d_k) e = b - (A + d_k) x_k, warm start x_k, until the true residual <= tol
+    // Per-shift refinement, all shifts at once: (A + d_k) e_k = b - (A + d_k) x_k for every shift whose
+    // FP64 true residual is above tol, each reduced by 0.5 tol / residual, then x_k += e_k and a new check.
+    for (int round = 0; refine && round < 4; ++round) {
+      std::vector<int> todo;
+      double rel[kMaxShifts];
       for (int k = 0; k < n; ++k) {
-        int rounds = 0;
-        while (tres[k] > tol && rounds < 4) {
-          Launcher L{ctx, w, g, 0};
-          LQ_CUDA(enqueue_resid64(L, w->xk[k], w->b64, shifts[k], &w->sd->scal[1], nullptr));
-          LQ_CUDA(cudaMemcpyAsync(w->rb64, w->r64, w->dbytes, cudaMemcpyDeviceToDevice, w->st));
-          ctx->launches += L.nlaunch;
-          double inner_tol = std::min(0.5, 0.5 * tol / tres[k]);
-          int it2 = 0, ru2 = 0, st2 = LQCD_OK;
-          double2* es[1] = {w->e64};
-          rc = solve_core(ctx, w->rb64, es, &shifts[k], 1, inner_tol, maxiter, prec != LQCD_FP64, &it2, &ru2, &st2);
-          if (rc != LQCD_OK) return rc;
-          refine_iters += it2;
-          n_ru += ru2;
-          axpy64_kernel<<<(3 * g.vh + 255) / 256, 256, 0, w->st>>>(3 * g.vh, w->xk[k], w->e64);
-          ctx->launches += 1;
-          LQ_CUDA(cudaGetLastError());
-          std::vector<int> one(1, k);
-          rc = true_residuals(ctx, w->b64, w->xk, shifts, one, bb, &tres[k]);
-          if (rc != LQCD_OK) return rc;
-          ++rounds;
-          if (st2 == LQCD_ERR_NONFINITE) break;
+        rel[k] = 1e300;  // systems already below tol are not iterated
+        if (tres[k] > tol) {
+          todo.push_back(k);
+          rel[k] = std::min(0.5, 0.5 * tol / tres[k]);
         }
-        if (rounds > 0) ++refined;
       }
+      if (todo.empty()) break;
+      int it2 = 0, st2 = LQCD_OK;
+      rc = mrhs_solve(ctx, prec, n, shifts, rel, maxiter, w->st, &it2, &st2);
+      if (rc != LQCD_OK) return rc;
+      refine_iters += it2;
+      void* const* es = mrhs_solutions(ctx);
+      const int n3 = 3 * g.vh;
+      for (int k : todo) {
+        add_correction_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->xk[k], es[k], f32);
+        ctx->launches += 1;
+      }
+      LQ_CUDA(cudaGetLastError());
+      if (round == 0) refined = (int)todo.size();
+      rounds_done = round + 1;
+      rc = true_residuals(ctx, w->b64, w->xk, shifts, todo, bb, tres, rhs, f32);
+      if (rc != LQCD_OK) return rc;
+      if (st2 == LQCD_ERR_NONFINITE) break;
     }
     if (status == LQCD_OK)
       for (int k = 0; k < n; ++k)
@@ -840,6 +882,7 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
     stats->reliable_updates = n_ru;
     stats->refine_iterations = refine_iters;
     stats->refined_shifts = refined;
+    stats->refine_rounds = rounds_done;
     stats->kernel_launches = (int)(ctx->launches - launches0);
     stats->n_shifts = n;
     for (int k = 0; k < n; ++k) stats->true_residual[k] = tres[k];

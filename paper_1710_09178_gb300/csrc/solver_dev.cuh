@@ -90,7 +90,14 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
       sd->chi[k][m] = 0.0;
       sd->zeta_prev[k] = z;
       sd->zeta[k] = zn;
-      if (zn * zn * rr_new <= sd->stop2) sd->active[k] = 0;
+      if (zn * zn * rr_new <= sd->stop2) {
+        // stopped: the rest of this window's residuals must not enter its x_k / p_k update
+        sd->active[k] = 0;
+        for (int i = m + 1; i < kWindow; ++i) {
+          sd->pi[k][i] = 0.0;
+          sd->chi[k][i] = 0.0;
+        }
+      }
     }
     still = sd->active[k];
   }
