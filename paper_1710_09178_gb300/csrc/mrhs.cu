@@ -155,11 +155,13 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
     __syncthreads();
     if (last) {
       __threadfence();
-      for (int pos = 0; pos < n_act; ++pos) {
+      // one warp per system: strided partial sums in a fixed order, then a fixed shuffle tree
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
-        v = block_sum(v);
-        if (threadIdx.x == 0) {
+        for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
+        v = warp_sum(v);
+        if (lane == 0) {
           int sj = md->list[pos];
           double alpha = md->rr[sj] / v;
           if (!(v > 0.0) || !isfinite(alpha)) {
@@ -219,11 +221,12 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
   if (!last) return;
   __threadfence();
   __shared__ int keep[kMrhsMax];
-  for (int pos = 0; pos < n_act; ++pos) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
-    v = block_sum(v);
-    if (threadIdx.x == 0) {
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
+    v = warp_sum(v);
+    if (lane == 0) {
       int sj = md->list[pos];
       double beta = v / md->rr[sj];
       if (!isfinite(v)) {
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
       keep[pos] = !(v <= md->stop2[sj]);
     }
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int w = 0;
     for (int pos = 0; pos < n_act; ++pos)
@@ -305,17 +309,19 @@ __global__ void __launch_bounds__(128) mrhs_init_kernel(Geom g, MrhsVecs vv, Mrh
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int sj = 0; sj < in.m; ++sj) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sj = threadIdx.x >> 5; sj < in.m; sj += nw) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(partials + (size_t)sj * gridDim.x + b);
-    v = block_sum(v);
-    if (threadIdx.x == 0) {
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partials + (size_t)sj * gridDim.x + b);
+    v = warp_sum(v);
+    if (lane == 0) {
       md->rr[sj] = v;
       md->stop2[sj] = in.rel2[sj] * v;
       md->a[sj] = in.a[sj];
       md->alpha[sj] = md->beta[sj] = 0.0;
     }
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int w = 0;
     for (int sj = 0; sj < in.m; ++sj)

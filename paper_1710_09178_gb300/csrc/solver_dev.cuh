@@ -19,104 +19,125 @@
 
 namespace lqcd {
 
+// The steps run in one warp of the last block; every lane k < n owns shift k.  All loads of a
+// lane are issued before any store (the state lives in global memory and a chain of dependent
+// round trips would cost far more than the arithmetic, most of which is FP64).
+
 // last block, all threads call; pq identical in every thread
 __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
-  __shared__ double s_alpha;
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    double alpha = sd->rr / pq;
-    int ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
+  if (threadIdx.x >= 32) return;
+  const int k = threadIdx.x;
+  const double rr = sd->rr, alpha_prev = sd->alpha_prev, beta_prev = sd->beta_prev;
+  const int n = sd->n, m = sd->m;
+  const bool mine = k < n;
+  const int act = mine ? sd->active[k] : 0;
+  double z = 1.0, zp = 1.0, sk = 0.0, P = 0.0, X = 0.0, pi[kWindow], chi[kWindow];
+  if (act) {
+    z = sd->zeta[k];
+    zp = sd->zeta_prev[k];
+    sk = sd->s[k];
+    P = sd->P[k];
+    X = sd->X[k];
+#pragma unroll
+    for (int i = 0; i < kWindow; ++i) {
+      pi[i] = (i < m) ? sd->pi[k][i] : 0.0;
+      chi[i] = (i < m) ? sd->chi[k][i] : 0.0;
+    }
+  }
+  const double alpha = rr / pq;
+  const bool ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
+  if (k == 0) {
     sd->pq = pq;
     sd->alpha = alpha;
     if (!ok) {
       sd->status = LQCD_ERR_NONFINITE;
       sd->done = 1;
     }
-    s_alpha = alpha;
-    s_ok = ok;
   }
-  __syncthreads();
-  if (!s_ok) return;
-  int k = threadIdx.x;
-  if (k < sd->n && sd->active[k]) {
-    double alpha = s_alpha;
-    double z = sd->zeta[k], zp = sd->zeta_prev[k];
-    double den = alpha * sd->beta_prev * (zp - z) + zp * sd->alpha_prev * (1.0 + sd->s[k] * alpha);
-    double zn = z * zp * sd->alpha_prev / den;
-    double ak = alpha * zn / z;
-    sd->zeta_new[k] = zn;
-    double P = sd->P[k];
-    sd->X[k] += ak * P;
-    int m = sd->m;
-    for (int i = 0; i < m; ++i) sd->chi[k][i] += ak * sd->pi[k][i];
-  }
+  if (!ok || !act) return;
+  const double den = alpha * beta_prev * (zp - z) + zp * alpha_prev * (1.0 + sk * alpha);
+  const double zn = z * zp * alpha_prev / den;
+  const double ak = alpha * zn / z;
+  sd->zeta_new[k] = zn;
+  sd->X[k] = X + ak * P;
+#pragma unroll
+  for (int i = 0; i < kWindow; ++i)
+    if (i < m) sd->chi[k][i] = chi[i] + ak * pi[i];
 }
 
 // last block, all threads call; rr_new identical in every thread
 __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
-  __shared__ double s_beta;
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    double beta = rr_new / sd->rr;
-    int ok = isfinite(rr_new) && isfinite(beta);
-    if (!ok) {
+  if (threadIdx.x >= 32) return;
+  const int k = threadIdx.x;
+  const double rr = sd->rr, stop2 = sd->stop2, alpha = sd->alpha;
+  const int n = sd->n, m = sd->m, iter = sd->iter, maxiter = sd->maxiter;
+  const int iter_ru = sd->iter_ru, ru_interval = sd->ru_interval;
+  const double ru_delta2 = sd->ru_delta2, rr_ru_max = sd->rr_ru_max;
+  const bool mine = k < n;
+  const int act = mine ? sd->active[k] : 0;
+  double z = 1.0, zn = 1.0, P = 0.0, pi[kWindow];
+  if (act) {
+    z = sd->zeta[k];
+    zn = sd->zeta_new[k];
+    P = sd->P[k];
+#pragma unroll
+    for (int i = 0; i < kWindow; ++i) pi[i] = (i < m) ? sd->pi[k][i] : 0.0;
+  }
+  const double beta = rr_new / rr;
+  const bool ok = isfinite(rr_new) && isfinite(beta);
+  if (!ok) {
+    if (k == 0) {
+      sd->beta = beta;
       sd->status = LQCD_ERR_NONFINITE;
       sd->done = 1;
     }
-    sd->beta = beta;
-    s_beta = beta;
-    s_ok = ok;
+    return;
   }
-  __syncthreads();
-  if (!s_ok) return;
-  int k = threadIdx.x;
-  int m = sd->m;
   if (m >= kWindow) {  // the host flushes every kWindow iterations; never index past the window
-    if (threadIdx.x == 0) {
+    if (k == 0) {
+      sd->beta = beta;
       sd->status = LQCD_ERR_STATE;
       sd->done = 1;
     }
     return;
   }
   int still = 0;
-  if (k < sd->n) {
-    if (sd->active[k]) {
-      double zn = sd->zeta_new[k], z = sd->zeta[k];
-      double ratio = zn / z;
-      double bk = s_beta * ratio * ratio;
-      sd->P[k] *= bk;
-      for (int i = 0; i < m; ++i) sd->pi[k][i] *= bk;
-      sd->pi[k][m] = zn;
-      sd->chi[k][m] = 0.0;
-      sd->zeta_prev[k] = z;
-      sd->zeta[k] = zn;
-      if (zn * zn * rr_new <= sd->stop2) {
-        // stopped: the rest of this window's residuals must not enter its x_k / p_k update
-        sd->active[k] = 0;
-        for (int i = m + 1; i < kWindow; ++i) {
-          sd->pi[k][i] = 0.0;
-          sd->chi[k][i] = 0.0;
-        }
-      }
+  if (act) {
+    const double ratio = zn / z;
+    const double bk = beta * ratio * ratio;
+    sd->P[k] = P * bk;
+    const bool stop = zn * zn * rr_new <= stop2;
+#pragma unroll
+    for (int i = 0; i < kWindow; ++i) {
+      if (i < m) sd->pi[k][i] = pi[i] * bk;
+      // this iteration's residual enters at position m; a shift that stops here takes no later one
+      else if (i == m) sd->pi[k][i] = zn;
+      else if (stop) sd->pi[k][i] = 0.0;
+      if (i == m || (i > m && stop)) sd->chi[k][i] = 0.0;
     }
-    still = sd->active[k];
+    sd->zeta_prev[k] = z;
+    sd->zeta[k] = zn;
+    if (stop) sd->active[k] = 0;
+    still = !stop;
   }
   // count shifts still active (warp 0 holds all of them, n <= 32)
-  if (threadIdx.x < 32) {
-    unsigned bal = __ballot_sync(0xffffffffu, still);
-    if (threadIdx.x == 0) {
-      sd->n_active = __popc(bal);
-      sd->m = m + 1;
-      sd->rr = rr_new;
-      sd->alpha_prev = sd->alpha;
-      sd->beta_prev = s_beta;
-      sd->iter += 1;
-      if (sd->n_active == 0 || sd->iter >= sd->maxiter) sd->done = 1;
-      double rmax = fmax(sd->rr_ru_max, rr_new);
-      sd->rr_ru_max = rmax;
-      int due = (sd->iter - sd->iter_ru >= sd->ru_interval) || (rr_new < sd->ru_delta2 * rmax);
-      sd->ru_skip = (sd->done || !due) ? 1 : 0;
-    }
+  const unsigned bal = __ballot_sync(0xffffffffu, still);
+  if (k == 0) {
+    const int n_active = __popc(bal);
+    const int it = iter + 1;
+    const int done = (n_active == 0 || it >= maxiter) ? 1 : 0;
+    sd->beta = beta;
+    sd->n_active = n_active;
+    sd->m = m + 1;
+    sd->rr = rr_new;
+    sd->alpha_prev = alpha;
+    sd->beta_prev = beta;
+    sd->iter = it;
+    if (done) sd->done = 1;
+    const double rmax = fmax(rr_ru_max, rr_new);
+    sd->rr_ru_max = rmax;
+    const int due = (it - iter_ru >= ru_interval) || (rr_new < ru_delta2 * rmax);
+    sd->ru_skip = (done || !due) ? 1 : 0;
   }
 }
 
