@@ -212,6 +212,27 @@ int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n
               lqcd_solve_stats* stats);
 
 /*
+ * fermion_force - derivative of the pseudofermion action S_f = phi^+ r(A) phi,
+ * r(A) = c0 + sum_k c_k (A + d_k)^{-1}, with respect to the links: the force of the
+ * momentum equation of the MD step (Section 3.1; r from Eq. ratapprx, usually the x^{-1/2}
+ * approximation).  Runs mshift_cg for X_k = (A + d_k)^{-1} phi (same arguments and rules),
+ * forms Y_k = D_oe X_k and evaluates
+ *   dS_f = sum_k c_k [ X_k^+ dD_eo Y_k - Y_k^+ dD_oe X_k ]
+ * link by link.  Convention: for U_mu(x) -> exp(i w^a lambda^a / 2) U_mu(x) (Gell-Mann lambda^a),
+ *   dS_f / dw^a = tr(lambda^a F_mu(x)),  F_mu(x) traceless Hermitian.
+ *   phi_dev    : device complex128 [Vh][3], even sites (canonical)
+ *   F_dev      : device complex128 [V][4][3][3] (canonical link layout) or NULL
+ *   Falg_dev   : device double [V][4][8], the components dS_f/dw^a, or NULL
+ *   action_host: host double receiving S_f (FP64), or NULL
+ *   prec       : LQCD_FP64 computes Y_k and F in FP64; the other modes solve in mixed precision
+ *                and form Y_k and F in FP32 from the FP64 solutions
+ * At least one output must be given.  Synchronises the context stream.
+ */
+int fermion_force(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* phi_dev,
+                  double* F_dev, double* Falg_dev, double* action_host, double tol, int maxiter, int prec,
+                  lqcd_solve_stats* stats);
+
+/*
  * lqcd_rational_coeffs - host-side coefficients of Eq. ratapprx (Appendix):
  * best relative-error rational approximation of type (n, n) to x^power on [lo, hi],
  *   r(x) = c0 + sum_{k<n} residues[k] / (x + poles[k]).

@@ -47,6 +47,7 @@ EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
+    "fermion_force",
 ]
 
 
@@ -108,6 +109,8 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(d)]),
         "lqcd_launch_count": (ctypes.c_longlong, [vp]),
         "lqcd_apply_A_noalloc": (i, [vp, vp, vp, d, i, ctypes.POINTER(d)]),
+        "fermion_force": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), i, d, vp, vp, vp, ctypes.POINTER(d), d, i, i,
+                              ctypes.POINTER(SolveStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +237,62 @@ def mshift_cg(ctx: Context, shifts, residues, c0, b, xs=None, y=None, tol=1e-10,
     if raise_on_error and rc not in (LQCD_OK,):
         ctx.check(rc)
     return rc, st.as_dict()
+
+
+def fermion_force(ctx: Context, shifts, residues, c0, phi, F=None, Falg=None, want_action=True, tol=1e-10,
+                  maxiter=20000, prec=FP32, raise_on_error=True):
+    """Force of S_f = phi^+ r(A) phi: F (V,4,3,3 complex128) and/or Falg (V,4,8 float64) device tensors.
+
+    Returns (status, S_f or None, stats dict).  dS_f/dw^a = tr(lambda^a F) = Falg[..., a] for
+    U -> exp(i w.lambda/2) U.
+    """
+    lib = load_library()
+    n = len(shifts)
+    sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
+    rs = (ctypes.c_double * n)(*[float(c) for c in residues])
+    act = ctypes.c_double(0.0)
+    st = SolveStats()
+    rc = lib.fermion_force(ctx.handle, sh, rs, n, float(c0), _ptr(phi), _ptr(F), _ptr(Falg),
+                           ctypes.byref(act) if want_action else None, float(tol), int(maxiter), int(prec),
+                           ctypes.byref(st))
+    if raise_on_error and rc != LQCD_OK:
+        ctx.check(rc)
+    return rc, (act.value if want_action else None), st.as_dict()
+
+
+class FermionAction:
+    """torch.autograd.Function for S_f(U) = phi^+ r(A[U]) phi in the algebra coordinates w of
+    U -> exp(i w.lambda/2) U at w = 0: forward returns S_f, backward returns dS_f/dw from the
+    library's adjoint kernel (fermion_force)."""
+
+    _fn = None
+
+    @classmethod
+    def function(cls):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(actx, w, ctx, shifts, residues, c0, phi, tol, prec):
+                    if bool(torch.any(w != 0)):
+                        raise ValueError("FermionAction is evaluated at w = 0 (update U itself, then reset w)")
+                    Falg = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device=phi.device)
+                    rc, S, st = fermion_force(ctx, shifts, residues, c0, phi, Falg=Falg, tol=tol, prec=prec)
+                    actx.save_for_backward(Falg)
+                    return torch.tensor(S, dtype=torch.float64, device=phi.device)
+
+                @staticmethod
+                def backward(actx, grad):
+                    (Falg,) = actx.saved_tensors
+                    return grad * Falg, None, None, None, None, None, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+    @classmethod
+    def apply(cls, w, ctx, shifts, residues, c0, phi, tol=1e-10, prec=FP32):
+        return cls.function().apply(w, ctx, shifts, residues, c0, phi, tol, prec)
 
 
 def lqcd_rational_coeffs(power, lo, hi, n):

@@ -83,6 +83,7 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   if (!ctx) return LQCD_OK;
   free_workspace(ctx);
   mrhs_release(ctx);
+  force_release(ctx);
   void* bufs[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->partials, ctx->tickets, ctx->scalars,
                   ctx->tmp_odd};
   for (void* b : bufs)

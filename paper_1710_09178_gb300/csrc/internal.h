@@ -81,6 +81,7 @@ struct lqcd_ctx {
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
+  void* force_ws = nullptr;             // fermion-force buffers (force.cu)
   double* partials = nullptr;  // reduction scratch, one double per block
   void* tmp_odd = nullptr;     // odd-parity temporary of lqcd_apply_A (sized for FP64)
   unsigned* tickets = nullptr;  // reduction tickets for stand-alone reductions
@@ -126,6 +127,12 @@ int dslash_grid_blocks(const Geom& g, int prec, int tps);
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
                double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats);
 void free_workspace(lqcd_ctx* ctx);
+// FP64 internal solutions x_k of the last mshift_cg call on this context, and its stream
+double2* const* workspace_solutions(lqcd_ctx* ctx);
+cudaStream_t workspace_stream(lqcd_ctx* ctx);
+
+// force.cu
+void force_release(lqcd_ctx* ctx);
 
 // mrhs.cu: many shifted systems (A + sigma_j) e_j = r_j solved together (per-shift refinement)
 int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out);

@@ -411,6 +411,9 @@ static size_t vec_bytes(long long vh, int prec) {
   return 0;
 }
 
+double2* const* workspace_solutions(lqcd_ctx* ctx) { return ctx->ws ? ctx->ws->xk : nullptr; }
+cudaStream_t workspace_stream(lqcd_ctx* ctx) { return ctx->ws ? ctx->ws->st : nullptr; }
+
 void free_workspace(lqcd_ctx* ctx) {
   Workspace* w = ctx->ws;
   if (!w) return;
