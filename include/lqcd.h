@@ -232,6 +232,55 @@ int fermion_force(lqcd_ctx* ctx, const double* shifts, const double* residues, i
                   double* F_dev, double* Falg_dev, double* action_host, double tol, int maxiter, int prec,
                   lqcd_solve_stats* stats);
 
+/* Parameters of rhmc_trajectory. */
+typedef struct {
+  double beta;                 /* Wilson gauge action S_g = beta sum_{x,mu<nu} (1 - Re tr U_plaq / 3) */
+  double tau;                  /* trajectory length */
+  int nsteps;                  /* Omelyan 2MN steps */
+  double lambda;               /* Omelyan parameter; 0 selects 0.1931833275037836 */
+  int n_act;                   /* x^{-1/2} approximation: action and MD force */
+  const double* act_shifts;
+  const double* act_residues;
+  double act_c0;
+  int n_heat;                  /* x^{1/4} approximation: heatbath phi = r(A) xi */
+  const double* heat_shifts;
+  const double* heat_residues;
+  double heat_c0;
+  double tol;                  /* true residual of the heatbath and Hamiltonian solves */
+  double md_tol;               /* true residual of the MD force solves (0: tol) */
+  int maxiter;
+  int prec;                    /* precision mode of the MD force solves */
+  int prec_action;             /* precision mode of the heatbath and Hamiltonian solves */
+  int phi_given;               /* 1: xi_dev already is the pseudofermion phi (no heatbath) */
+  double* mom_out;             /* optional device double [V][4][8]: momenta at the end of the MD */
+  double* links_out;           /* optional device complex128 [V][4][3][3]: the proposed links */
+} lqcd_rhmc_params;
+
+/* Result of rhmc_trajectory (FP64 energies). */
+typedef struct {
+  double dH, H0, H1;
+  double kinetic0, kinetic1, gauge0, gauge1, fermion0, fermion1;
+  int accepted;
+  int solves;                  /* shifted-CG solves run */
+  int iterations;              /* their iterations, refinement included */
+  double ms;                   /* host wall time of the call */
+} lqcd_traj_result;
+
+/*
+ * rhmc_trajectory - one RHMC trajectory for two staggered flavours (Section 3.1):
+ *   phi = r_{1/4}(A) xi; H = 1/2 sum p^2 + S_g + phi^+ r_{-1/2}(A) phi;
+ *   MD: dU/dt = i P U (P = sum_a p^a lambda^a / 2), dp^a/dt = -dS/dw^a (gauge + fermion_force),
+ *   Omelyan 2MN with nsteps steps of tau/nsteps; accept if uniform < exp(-dH).
+ *   U_dev   : device complex128 [V][4][3][3] (canonical); replaced by the new links when accepted,
+ *             unchanged otherwise.  The context's gauge field follows U_dev on return.
+ *   mom_dev : device double [V][4][8], the momenta p^a drawn by the caller (unchanged)
+ *   xi_dev  : device complex128 [Vh][3] Gaussian (Re, Im ~ N(0, 1/2)) or phi (phi_given)
+ *   uniform : the Metropolis random number in [0, 1)
+ * Links, momenta, actions and dH are FP64; links are reprojected onto SU(3) after every update.
+ */
+int rhmc_trajectory(lqcd_ctx* ctx, const lqcd_rhmc_params* prm, double* U_dev, const double* mom_dev,
+                    const double* xi_dev, double uniform, lqcd_traj_result* res);
+
 /*
  * lqcd_rational_coeffs - host-side coefficients of Eq. ratapprx (Appendix):
  * best relative-error rational approximation of type (n, n) to x^power on [lo, hi],

@@ -47,7 +47,7 @@ EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
-    "fermion_force",
+    "fermion_force", "rhmc_trajectory",
 ]
 
 
@@ -70,6 +70,31 @@ class SolveStats(ctypes.Structure):
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
                     refine_rounds=self.refine_rounds,
                     kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms)
+
+
+class RhmcParams(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double), ("tau", ctypes.c_double), ("nsteps", ctypes.c_int), ("lambda_", ctypes.c_double),
+        ("n_act", ctypes.c_int), ("act_shifts", ctypes.POINTER(ctypes.c_double)),
+        ("act_residues", ctypes.POINTER(ctypes.c_double)), ("act_c0", ctypes.c_double),
+        ("n_heat", ctypes.c_int), ("heat_shifts", ctypes.POINTER(ctypes.c_double)),
+        ("heat_residues", ctypes.POINTER(ctypes.c_double)), ("heat_c0", ctypes.c_double),
+        ("tol", ctypes.c_double), ("md_tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
+        ("prec_action", ctypes.c_int), ("phi_given", ctypes.c_int), ("mom_out", ctypes.c_void_p),
+        ("links_out", ctypes.c_void_p),
+    ]
+
+
+class TrajResult(ctypes.Structure):
+    _fields_ = [
+        ("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+        ("kinetic0", ctypes.c_double), ("kinetic1", ctypes.c_double), ("gauge0", ctypes.c_double),
+        ("gauge1", ctypes.c_double), ("fermion0", ctypes.c_double), ("fermion1", ctypes.c_double),
+        ("accepted", ctypes.c_int), ("solves", ctypes.c_int), ("iterations", ctypes.c_int), ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class LqcdError(RuntimeError):
@@ -111,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "lqcd_apply_A_noalloc": (i, [vp, vp, vp, d, i, ctypes.POINTER(d)]),
         "fermion_force": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), i, d, vp, vp, vp, ctypes.POINTER(d), d, i, i,
                               ctypes.POINTER(SolveStats)]),
+        "rhmc_trajectory": (i, [vp, ctypes.POINTER(RhmcParams), vp, vp, vp, d, ctypes.POINTER(TrajResult)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -293,6 +319,36 @@ class FermionAction:
     @classmethod
     def apply(cls, w, ctx, shifts, residues, c0, phi, tol=1e-10, prec=FP32):
         return cls.function().apply(w, ctx, shifts, residues, c0, phi, tol, prec)
+
+
+def rhmc_trajectory(ctx: Context, U, mom, xi, uniform, beta, tau, nsteps, act, heat=None, tol=1e-10, md_tol=0.0,
+                    maxiter=20000, prec=FP32, prec_action=FP64, phi_given=False, mom_out=None, links_out=None,
+                    lam=0.0, raise_on_error=True):
+    """One RHMC trajectory (see include/lqcd.h).  act = (c0, residues, shifts) of x^{-1/2},
+    heat = (c0, residues, shifts) of x^{1/4}; U (V,4,3,3) complex128 updated in place if accepted;
+    mom (V,4,8) float64; xi (Vh,3) complex128.  Returns (status, result dict)."""
+    lib = load_library()
+    arr = lambda v: (ctypes.c_double * len(v))(*[float(x) for x in v])
+    a_c0, a_res, a_sh = act
+    keep = [arr(a_sh), arr(a_res)]
+    prm = RhmcParams()
+    prm.beta, prm.tau, prm.nsteps, prm.lambda_ = float(beta), float(tau), int(nsteps), float(lam)
+    prm.n_act, prm.act_shifts, prm.act_residues, prm.act_c0 = len(a_sh), keep[0], keep[1], float(a_c0)
+    if heat is not None:
+        h_c0, h_res, h_sh = heat
+        keep += [arr(h_sh), arr(h_res)]
+        prm.n_heat, prm.heat_shifts, prm.heat_residues, prm.heat_c0 = len(h_sh), keep[2], keep[3], float(h_c0)
+    prm.tol, prm.md_tol, prm.maxiter, prm.prec, prm.prec_action = float(tol), float(md_tol), int(maxiter), int(prec), int(
+        prec_action)
+    prm.phi_given = 1 if phi_given else 0
+    prm.mom_out = _ptr(mom_out)
+    prm.links_out = _ptr(links_out)
+    res = TrajResult()
+    rc = lib.rhmc_trajectory(ctx.handle, ctypes.byref(prm), _ptr(U), _ptr(mom), _ptr(xi), float(uniform),
+                             ctypes.byref(res))
+    if raise_on_error and rc != LQCD_OK:
+        ctx.check(rc)
+    return rc, res.as_dict()
 
 
 def lqcd_rational_coeffs(power, lo, hi, n):

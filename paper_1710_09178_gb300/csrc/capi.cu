@@ -84,6 +84,7 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   free_workspace(ctx);
   mrhs_release(ctx);
   force_release(ctx);
+  traj_release(ctx);
   void* bufs[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->partials, ctx->tickets, ctx->scalars,
                   ctx->tmp_odd};
   for (void* b : bufs)

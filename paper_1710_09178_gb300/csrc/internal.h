@@ -82,6 +82,7 @@ struct lqcd_ctx {
   lqcd::Workspace* ws = nullptr;
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
   void* force_ws = nullptr;             // fermion-force buffers (force.cu)
+  void* traj_ws = nullptr;              // trajectory buffers (trajectory.cu)
   double* partials = nullptr;  // reduction scratch, one double per block
   void* tmp_odd = nullptr;     // odd-parity temporary of lqcd_apply_A (sized for FP64)
   unsigned* tickets = nullptr;  // reduction tickets for stand-alone reductions
@@ -131,8 +132,9 @@ void free_workspace(lqcd_ctx* ctx);
 double2* const* workspace_solutions(lqcd_ctx* ctx);
 cudaStream_t workspace_stream(lqcd_ctx* ctx);
 
-// force.cu
+// force.cu, trajectory.cu
 void force_release(lqcd_ctx* ctx);
+void traj_release(lqcd_ctx* ctx);
 
 // mrhs.cu: many shifted systems (A + sigma_j) e_j = r_j solved together (per-shift refinement)
 int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out);

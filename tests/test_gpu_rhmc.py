@@ -1,0 +1,87 @@
+"""GPU parity of rhmc_trajectory (Section 3.1) against the oracle trajectory, and reversibility.
+
+Bars (FP64 solves to 1e-12): Hamiltonian pieces within 1e-9 relative; dH within 1e-7 absolute;
+proposed links and final momenta within 1e-8; integrating back with -p returns the links to 1e-10.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import make_context, to_dev
+from oracle import rational, rhmc
+from paper_1710_09178_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64 = 0
+DIMS, MASS, BETA, TAU, NSTEPS = (4, 4, 4, 4), 0.1, 5.4, 0.3, 3
+
+
+def _coeffs():
+    lo, hi = 4 * MASS ** 2, 16 + 4 * MASS ** 2
+    return rational.zolotarev_inv_sqrt(8, lo, hi)[:3], rational.remez_power(0.25, lo, hi, 8)[:3]
+
+
+def _momenta(seed):
+    V = int(np.prod(DIMS))
+    return inputs.counter_normal_pairs(seed, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
+
+
+def test_trajectory_matches_oracle():
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    act, heat = _coeffs()
+    ctx, U0 = make_context(DIMS, MASS, gauge_seed=31)
+    p0 = _momenta(32)
+    xi = inputs.gaussian_vector(DIMS, 33)
+    V = int(np.prod(DIMS))
+    Ud = to_dev(U0)
+    links = torch.empty_like(Ud)
+    mom = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+    rc, res = lq.rhmc_trajectory(ctx, Ud, to_dev(p0), to_dev(xi), 0.999999, BETA, TAU, NSTEPS,
+                                 (act[0], act[1], act[2]), (heat[0], heat[1], heat[2]), tol=1e-12, prec=FP64,
+                                 prec_action=FP64, mom_out=mom, links_out=links)
+    assert rc == 0
+    Uo, acc, info = rhmc.trajectory(U0, p0, xi, 0.999999, DIMS, MASS, BETA, TAU, NSTEPS, act, heat, tol=1e-12)
+    for k in ("kinetic", "gauge", "fermion"):
+        assert abs(res[k + "0"] - info["parts0"][k]) <= 1e-9 * abs(info["parts0"][k])
+        assert abs(res[k + "1"] - info["parts1"][k]) <= 1e-9 * abs(info["parts1"][k])
+    assert abs(res["dH"] - info["dH"]) <= 1e-7
+    assert np.max(np.abs(links.cpu().numpy() - info["U1"])) <= 1e-8
+    assert np.max(np.abs(mom.cpu().numpy() - info["p1"])) <= 1e-8
+    assert res["accepted"] == int(acc)
+    assert res["solves"] == 2 * NSTEPS + 1 + 3  # MD forces + heatbath + two Hamiltonians
+    torch.cuda.synchronize()
+    if res["accepted"]:
+        assert np.array_equal(Ud.cpu().numpy(), links.cpu().numpy())
+
+
+def test_trajectory_is_reversible_and_reject_keeps_links():
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    act, heat = _coeffs()
+    ctx, U0 = make_context(DIMS, MASS, gauge_seed=41)
+    p0 = _momenta(42)
+    phi = rhmc.heatbath(U0, inputs.gaussian_vector(DIMS, 43), MASS, DIMS, heat, tol=1e-13)
+    V = int(np.prod(DIMS))
+    Ud = to_dev(U0)
+    links = torch.empty_like(Ud)
+    mom = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+    # uniform = 1: reject whatever dH is (exp(-dH) < 1 unless dH <= 0); links must stay
+    rc, r1 = lq.rhmc_trajectory(ctx, Ud, to_dev(p0), to_dev(phi), 1.0 + 1e9, BETA, TAU, NSTEPS, act, tol=1e-13,
+                                prec=FP64, prec_action=FP64, phi_given=True, mom_out=mom, links_out=links)
+    assert rc == 0 and r1["accepted"] == 0
+    assert np.array_equal(Ud.cpu().numpy(), U0)
+    # backwards from the proposal with reversed momenta
+    U1 = links.clone()
+    back_links = torch.empty_like(Ud)
+    back_mom = torch.empty_like(mom)
+    rc, r2 = lq.rhmc_trajectory(ctx, U1, -mom, to_dev(phi), 1.0 + 1e9, BETA, TAU, NSTEPS, act, tol=1e-13,
+                                prec=FP64, prec_action=FP64, phi_given=True, mom_out=back_mom, links_out=back_links)
+    assert rc == 0
+    assert np.max(np.abs(back_links.cpu().numpy() - U0)) < 1e-10
+    assert np.max(np.abs(back_mom.cpu().numpy() + p0)) < 1e-9
+    assert abs(r1["dH"] + r2["dH"]) < 1e-8
