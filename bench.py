@@ -261,6 +261,44 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+TRAJ_DIMS, TRAJ_MASS, TRAJ_BETA, TRAJ_TAU, TRAJ_STEPS, TRAJ_POLES = (24, 24, 24, 6), 0.025, 5.4, 1.0, 25, 16
+
+
+def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS):
+    """RHMC trajectories on 24^3x6 (beta 5.4, m 0.025, 16-pole x^{-1/2} and x^{1/4}, Omelyan tau 1, 25 steps).
+
+    Momenta, Gaussian sources and Metropolis numbers come from the counter-based generator (seed 9
+    and per-trajectory streams).  MD force solves in mixed precision to md_tol; heatbath and
+    Hamiltonian solves in mixed precision to a true FP64 residual of 1e-10."""
+    from paper_1710_09178_gb300 import inputs
+
+    lo, hi = 4 * TRAJ_MASS ** 2, 16 + 4 * TRAJ_MASS ** 2
+    ca, ra, pa, _ = lq.rational_coeffs(-0.5, lo, hi, TRAJ_POLES)
+    ch, rh, ph, _ = lq.rational_coeffs(0.25, lo, hi, TRAJ_POLES)
+    V = int(np.prod(TRAJ_DIMS))
+    ctx = lq.Context(TRAJ_DIMS, TRAJ_MASS)
+    U = torch.from_numpy(inputs.gauge_field(TRAJ_DIMS, seed=9)).cuda()
+    ctx.set_gauge(U)
+    out = []
+    for t in range(n_traj):
+        mom = inputs.counter_normal_pairs(9000 + t, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
+        xi = inputs.gaussian_vector(TRAJ_DIMS, 9500 + t)
+        uni = float(inputs.counter_uniform(9999, np.array([t], dtype=np.uint64), 0)[0])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        md = torch.from_numpy(mom).cuda()
+        xd = torch.from_numpy(xi).cuda()
+        e0.record()
+        rc, res = lq.rhmc_trajectory(ctx, U, md, xd, uni, TRAJ_BETA, TRAJ_TAU, nsteps, (ca, ra, pa), (ch, rh, ph),
+                                     tol=1e-10, md_tol=md_tol, prec=lq.FP32, prec_action=lq.FP32)
+        e1.record()
+        e1.synchronize()
+        res["event_ms"] = e0.elapsed_time(e1)
+        out.append(res)
+    ctx.close()
+    return out
+
+
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch."""
@@ -304,7 +342,31 @@ def main():
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
     ap.add_argument("--profile", choices=["dslash", "solve"], help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix"])
+    ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
+    ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
     args = ap.parse_args()
+    if args.rhmc:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_1710_09178_gb300 as lq
+
+        tr = run_trajectories(lq, torch, args.rhmc, nsteps=args.traj_steps)
+        dh = np.array([r["dH"] for r in tr])
+        ex = np.exp(-dh)
+        print(json.dumps({"rhmc": {"workload": "24^3x6", "beta": TRAJ_BETA, "mass": TRAJ_MASS, "tau": TRAJ_TAU,
+                                   "steps": args.traj_steps, "trajectories": len(tr),
+                                   "acceptance": float(np.mean([r["accepted"] for r in tr])),
+                                   "mean_exp_minus_dH": float(ex.mean()),
+                                   "stderr_exp_minus_dH": float(ex.std(ddof=1) / np.sqrt(len(ex))) if len(ex) > 1 else None,
+                                   "dH": dh.tolist(), "ms_per_trajectory": [r["event_ms"] for r in tr],
+                                   "solves_per_trajectory": tr[-1]["solves"],
+                                   "iterations_per_trajectory": tr[-1]["iterations"],
+                                   "plaquette_action_per_site": [r["gauge1"] / TRAJ_BETA / (6 * np.prod(TRAJ_DIMS)) for r in tr]}}),
+              flush=True)
+        return
     if args.profile:
         run_profile_target(args.profile, args.prec)
         return
@@ -415,6 +477,15 @@ def main():
     assert np.array_equal(y_host.numpy(), y.cpu().numpy())
     nbytes = b.nbytes
 
+    # ---- one RHMC trajectory on 24^3x6 (NEXT rows: force + integrator), after one warm-up ----
+    traj = None
+    if not args.quick:
+        tr = run_trajectories(lq, torch, 2)
+        t = tr[-1]
+        traj = {"workload": "24^3x6, beta 5.4, m 0.025, 16 poles, Omelyan tau 1, 25 steps",
+                "ms_per_trajectory": t["event_ms"], "dH": t["dH"], "accepted": t["accepted"],
+                "solves": t["solves"], "iterations": t["iterations"]}
+
     # ---- CPU baseline: the oracle, bounded sample, scaled by the FP64 iteration count -------
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -447,6 +518,7 @@ def main():
         "roofline": roofline,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/solve", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
+        "rhmc_trajectory": traj,
         "gpu_launches": launches_timed,
         "clocks": clk,
         "wall_s_timed": t_wall,
