@@ -299,6 +299,61 @@ def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS):
     return out
 
 
+C4_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 4), (16, 16, 16, 4), (16, 16, 16, 8)]
+C4_MASSES = [0.02, 0.05, 0.1]
+
+
+def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True):
+    """64 independent lattices (sizes and masses drawn uniformly, seed 7), 4 Gaussian pseudofermions
+    each, 12-pole x^{-1/2} shifted CG to 1e-10 in FP32 mode: sequential vs mshift_cg_batch."""
+    from paper_1710_09178_gb300 import inputs
+
+    owners, problems, picks, tps = [], [], [], []
+    for l in range(n_lat):
+        vi = int(inputs.counter_uniform(7, np.array([l], dtype=np.uint64), 0)[0] * len(C4_VOLUMES))
+        mi = int(inputs.counter_uniform(7, np.array([l], dtype=np.uint64), 1)[0] * len(C4_MASSES))
+        dims, mass = C4_VOLUMES[vi], C4_MASSES[mi]
+        picks.append((dims, mass))
+        owner = lq.Context(dims, mass)
+        owner.set_gauge(torch.from_numpy(inputs.gauge_field(dims, seed=7000 + l)).cuda())
+        if autotune:
+            tps.append(owner.autotune(lq.FP32))
+        owners.append(owner)
+        c0, res, poles, _ = lq.rational_coeffs(-0.5, 4 * mass * mass, 16 + 4 * mass * mass, npoles)
+        for f in range(n_pf):
+            ctx = lq.Context(dims, mass)
+            ctx.share_gauge(owner)
+            if autotune:
+                ctx.set_option(lq.OPT_DSLASH_TPS, tps[-1])
+            b = torch.from_numpy(inputs.gaussian_vector(dims, 8 + f * 100000 + l)).cuda()
+            xs = [torch.empty_like(b) for _ in range(npoles)]
+            problems.append(dict(ctx=ctx, shifts=poles, residues=res, c0=c0, b=b, xs=xs, y=torch.empty_like(b),
+                                 tol=1e-10, prec=lq.FP32))
+    # warm-up (workspace allocation, graph capture), then timed runs
+    lq.mshift_cg_batch(problems, nthreads=nthreads)
+    torch.cuda.synchronize()
+    out = {}
+    for name, nt in (("sequential", 1), ("batched", nthreads)):
+        t0 = time.perf_counter()
+        rc, st, stats = lq.mshift_cg_batch(problems, nthreads=nt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"ms": dt * 1e3, "problems_per_s": len(problems) / dt, "status_ok": all(x == 0 for x in st),
+                     "max_true_residual": max(max(s["true_residual"]) for s in stats)}
+    sites = sum(int(np.prod(d)) // 2 for d, _ in picks) * n_pf
+    out.update({"lattices": n_lat, "pseudofermions": n_pf, "poles": npoles, "problems": len(problems),
+                "even_sites_total": sites, "threads": nthreads,
+                "speedup": out["sequential"]["ms"] / out["batched"]["ms"],
+                "volumes_drawn": {str(v): sum(1 for d, _ in picks if d == v) for v in C4_VOLUMES},
+                "autotuned_tps": {str(v): sorted(set(t for (d, _), t in zip(picks, tps) if d == v)) for v in C4_VOLUMES}
+                if autotune else None})
+    for p in problems:
+        p["ctx"].close()
+    for o in owners:
+        o.close()
+    return out
+
+
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch."""
@@ -344,7 +399,18 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
+    ap.add_argument("--batch", action="store_true", help="run the 64-lattice batched workload, print one JSON line")
     args = ap.parse_args()
+    if args.batch:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_1710_09178_gb300 as lq
+
+        print(json.dumps({"batch": run_batch(lq, torch)}), flush=True)
+        return
     if args.rhmc:
         import torch
 

@@ -102,6 +102,14 @@ int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
 int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev);
 
 /*
+ * lqcd_share_gauge - let ctx use src's internal gauge copies instead of its own (same lattice
+ * extents; src must have a gauge field and must outlive ctx and keep that field while ctx uses
+ * it).  Several solves of one lattice (e.g. pseudofermions in mshift_cg_batch) then read the
+ * same links.  lqcd_set_gauge on a borrowing context returns LQCD_ERR_STATE.
+ */
+int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src);
+
+/*
  * lqcd_vector_bytes - bytes of one internal half-lattice vector of precision prec:
  *   LQCD_FP64                : 48*Vh, [3 colours][Vh] double2 (re, im)
  *   LQCD_FP32, LQCD_FP32_R12 : 24*Vh, [3 colours][Vh] float2
@@ -231,6 +239,42 @@ int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n
 int fermion_force(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* phi_dev,
                   double* F_dev, double* Falg_dev, double* action_host, double tol, int maxiter, int prec,
                   lqcd_solve_stats* stats);
+
+/* One problem of mshift_cg_batch: the arguments of mshift_cg plus its own context. */
+typedef struct {
+  lqcd_ctx* ctx;              /* distinct per problem: its lattice, mass, gauge field and workspace */
+  const double* shifts;
+  const double* residues;
+  int n;
+  double c0;
+  const double* b_dev;
+  double* const* x_dev;
+  double* y_dev;
+  double tol;
+  int maxiter;
+  int prec;
+  lqcd_solve_stats* stats;    /* may be NULL */
+  int status;                 /* output: mshift_cg's status for this problem */
+} lqcd_batch_problem;
+
+/*
+ * mshift_cg_batch - many independent shifted-CG solves (independent lattices of any size and
+ * several pseudofermions per lattice, as in the batched RHMC workloads) run concurrently: a
+ * pool of nthreads host threads takes problems in order, and every problem's solve graph runs on
+ * its own context's stream, so solves of small lattices share the GPU.  Each problem's results
+ * are exactly those of mshift_cg on its own.  Returns LQCD_OK when every problem did, else the
+ * first failing status (every problem's status is stored).  LQCD_ERR_ARG if two problems share a
+ * context.  The calling thread's current device is used by all workers.
+ */
+int mshift_cg_batch(lqcd_batch_problem* problems, int nprob, int nthreads);
+
+/*
+ * lqcd_autotune - time the half-Dslash of precision prec (LQCD_FP32 or LQCD_FP32_R12) with 1, 2,
+ * 4 and 8 threads per output site on this context's lattice and gauge field, keep the fastest
+ * (as LQCD_OPT_DSLASH_TPS) and store it in *best_tps (may be NULL).  Allocates and frees two
+ * temporary vectors; synchronises the context stream.
+ */
+int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps);
 
 /* Parameters of rhmc_trajectory. */
 typedef struct {

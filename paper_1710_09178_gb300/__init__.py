@@ -47,7 +47,8 @@ EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
-    "fermion_force", "rhmc_trajectory",
+    "fermion_force", "rhmc_trajectory", "mshift_cg_batch", "lqcd_autotune",
+    "lqcd_share_gauge",
 ]
 
 
@@ -70,6 +71,16 @@ class SolveStats(ctypes.Structure):
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
                     refine_rounds=self.refine_rounds,
                     kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms)
+
+
+class BatchProblem(ctypes.Structure):
+    _fields_ = [
+        ("ctx", ctypes.c_void_p), ("shifts", ctypes.POINTER(ctypes.c_double)),
+        ("residues", ctypes.POINTER(ctypes.c_double)), ("n", ctypes.c_int), ("c0", ctypes.c_double),
+        ("b_dev", ctypes.c_void_p), ("x_dev", ctypes.POINTER(ctypes.c_void_p)), ("y_dev", ctypes.c_void_p),
+        ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
+        ("stats", ctypes.POINTER(SolveStats)), ("status", ctypes.c_int),
+    ]
 
 
 class RhmcParams(ctypes.Structure):
@@ -137,6 +148,9 @@ def load_library(path: str = LIB_PATH):
         "fermion_force": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), i, d, vp, vp, vp, ctypes.POINTER(d), d, i, i,
                               ctypes.POINTER(SolveStats)]),
         "rhmc_trajectory": (i, [vp, ctypes.POINTER(RhmcParams), vp, vp, vp, d, ctypes.POINTER(TrajResult)]),
+        "mshift_cg_batch": (i, [ctypes.POINTER(BatchProblem), i, i]),
+        "lqcd_autotune": (i, [vp, i, ctypes.POINTER(ctypes.c_int)]),
+        "lqcd_share_gauge": (i, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -202,6 +216,11 @@ class Context:
         assert tuple(U.shape) == (self.V, 4, 3, 3) and U.is_contiguous()
         return self.check(load_library().lqcd_set_gauge(self.handle, _ptr(U)))
 
+    def share_gauge(self, src):
+        """Use src's gauge copies (lqcd_share_gauge); src must outlive this context."""
+        self._gauge_src = src  # keep the owner alive
+        return self.check(load_library().lqcd_share_gauge(self.handle, src.handle))
+
     def vector_bytes(self, prec):
         return int(load_library().lqcd_vector_bytes(self.handle, prec))
 
@@ -235,6 +254,12 @@ class Context:
 
     def set_option(self, key, value):
         return self.check(load_library().lqcd_set_option(self.handle, int(key), float(value)))
+
+    def autotune(self, prec=FP32):
+        """Pick the fastest Dslash threads-per-site on this lattice (lqcd_autotune); returns it."""
+        best = ctypes.c_int(0)
+        self.check(load_library().lqcd_autotune(self.handle, int(prec), ctypes.byref(best)))
+        return best.value
 
     def launch_count(self):
         return int(load_library().lqcd_launch_count(self.handle))
@@ -319,6 +344,40 @@ class FermionAction:
     @classmethod
     def apply(cls, w, ctx, shifts, residues, c0, phi, tol=1e-10, prec=FP32):
         return cls.function().apply(w, ctx, shifts, residues, c0, phi, tol, prec)
+
+
+def mshift_cg_batch(problems, nthreads=16, raise_on_error=True):
+    """Run independent shifted-CG problems concurrently (mshift_cg_batch).
+
+    problems: list of dicts with keys ctx, shifts, residues, c0, b, xs (list or None), y (or None),
+    tol, maxiter, prec.  Returns (status, [status per problem], [stats dict per problem]).
+    """
+    lib = load_library()
+    n = len(problems)
+    arr = (BatchProblem * n)()
+    keep = []
+    stats = [SolveStats() for _ in range(n)]
+    for i, pr in enumerate(problems):
+        ns = len(pr["shifts"])
+        sh = (ctypes.c_double * ns)(*[float(v) for v in pr["shifts"]])
+        rs = (ctypes.c_double * ns)(*[float(v) for v in pr["residues"]])
+        xs = pr.get("xs")
+        xp = (ctypes.c_void_p * ns)(*[_ptr(x) for x in xs]) if xs is not None else None
+        keep += [sh, rs, xp]
+        a = arr[i]
+        a.ctx = pr["ctx"].handle
+        a.shifts, a.residues, a.n, a.c0 = sh, rs, ns, float(pr.get("c0", 0.0))
+        a.b_dev = _ptr(pr["b"])
+        a.x_dev = xp
+        a.y_dev = _ptr(pr.get("y"))
+        a.tol, a.maxiter, a.prec = float(pr.get("tol", 1e-10)), int(pr.get("maxiter", 20000)), int(pr.get("prec", FP32))
+        a.stats = ctypes.pointer(stats[i])
+    rc = lib.mshift_cg_batch(arr, n, int(nthreads))
+    st = [arr[i].status for i in range(n)]
+    if raise_on_error and rc != LQCD_OK:
+        bad = st.index(rc) if rc in st else 0
+        problems[bad]["ctx"].check(rc)
+    return rc, st, [s.as_dict() for s in stats]
 
 
 def rhmc_trajectory(ctx: Context, U, mom, xi, uniform, beta, tau, nsteps, act, heat=None, tol=1e-10, md_tol=0.0,

@@ -85,8 +85,12 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   mrhs_release(ctx);
   force_release(ctx);
   traj_release(ctx);
-  void* bufs[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->partials, ctx->tickets, ctx->scalars,
-                  ctx->tmp_odd};
+  if (ctx->gauge.owned) {
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12};
+    for (void* b : g)
+      if (b) cudaFree(b);
+  }
+  void* bufs[] = {ctx->partials, ctx->tickets, ctx->scalars, ctx->tmp_odd};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -101,9 +105,27 @@ int lqcd_set_stream(lqcd_ctx* ctx, void* stream) {
   return LQCD_OK;
 }
 
+int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src) {
+  if (!ctx || !src) return LQCD_ERR_ARG;
+  if (src == ctx) return fail(ctx, LQCD_ERR_ARG, "lqcd_share_gauge: a context cannot borrow from itself");
+  for (int d = 0; d < 4; ++d)
+    if (ctx->dims[d] != src->dims[d]) return fail(ctx, LQCD_ERR_DIMS, "lqcd_share_gauge: lattices differ");
+  if (!src->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_share_gauge: source has no gauge field");
+  if (ctx->gauge.owned) {
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12};
+    for (void* b : g)
+      if (b) cudaFree(b);
+  }
+  ctx->gauge = src->gauge;
+  ctx->gauge.owned = false;
+  free_workspace(ctx);  // captured graphs refer to the old link copies
+  return LQCD_OK;
+}
+
 int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
   if (!ctx) return LQCD_ERR_ARG;
   if (!U_dev) return fail(ctx, LQCD_ERR_ARG, "lqcd_set_gauge: null gauge pointer");
+  if (!ctx->gauge.owned) return fail(ctx, LQCD_ERR_STATE, "lqcd_set_gauge: this context borrows its gauge field");
   Geom g = make_geom(ctx);
   GaugeCopies& gc = ctx->gauge;
   cudaError_t e;

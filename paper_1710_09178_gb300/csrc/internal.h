@@ -57,6 +57,7 @@ struct GaugeCopies {
   float* u32 = nullptr;    // [2][4][18][Vh] floats (float4 x4 + float2), 1/2 eta*bc folded in
   float4* u12 = nullptr;   // [2][4][3][Vh] float4, rows 0-1, no sign
   bool loaded = false;
+  bool owned = true;       // false when borrowed from another context (lqcd_share_gauge)
 };
 
 struct Workspace;
