@@ -16,6 +16,7 @@ paper (Gupta & Majumdar, arXiv:1710.09178) line by line rather than to be fast:
   encode16.py  16-bit fixed-point colour-vector storage       (Section 5 "half precision")
   force.py     fermion force dS_f/dU of phi^dagger r(A) phi   (Section 3.1 MD equations)
   rhmc.py      gauge action and force, heatbath, Omelyan MD, Metropolis (Section 3.1)
+  linkcomp.py  8-real and 16-bit compressed SU(3) link storage   (Section 5 outlook)
 
 Each function names the passage it follows.  Where the paper is silent or
 ambiguous the oracle takes one stated reading (listed in the design doc).
@@ -23,4 +24,4 @@ Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 against closed forms, invariants, dense linear algebra or brute force.
 """
 
-from . import lattice, staggered, solvers, rational, encode16, force, rhmc  # noqa: F401
+from . import lattice, staggered, solvers, rational, encode16, force, rhmc, linkcomp  # noqa: F401
