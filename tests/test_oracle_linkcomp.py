@@ -45,10 +45,24 @@ def test_r8_loses_half_the_digits_where_c1_vanishes():
     assert 1e-12 < err < 4 * np.sqrt(np.finfo(float).eps)
 
 
-def test_r8_cannot_hold_the_unit_link():
+def test_r8_block_diagonal_links():
+    # N = 0: the unit link and a1 (+) U(2) blocks with det = conj(a1) round-trip exactly
     E = np.eye(3, dtype=np.complex128)
     assert linkcomp.r8_norm(E) == 0
-    assert not np.all(np.isfinite(linkcomp.decode_r8(linkcomp.encode_r8(E))))
+    assert linkcomp.encode_r8(E)[7] == linkcomp.R8_MARK
+    assert np.array_equal(linkcomp.decode_r8(linkcomp.encode_r8(E)), E)
+    a1 = np.exp(0.7j)
+    B = _rot(0, 1, 0.4)[:2, :2] @ np.diag(np.exp(1j * np.array([0.3, -0.3])))  # SU(2)
+    M = np.zeros((3, 3), dtype=np.complex128)
+    M[0, 0] = a1
+    M[1:, 1:] = np.conj(a1) ** 0.5 * B  # det of the block = conj(a1)
+    assert abs(np.linalg.det(M) - 1) < 1e-14
+    assert np.max(np.abs(linkcomp.decode_r8(linkcomp.encode_r8(M)) - M)) < 1e-15
+    # just below the threshold the dropped entries (|.| <= sqrt N) are the only error
+    eps = 1e-8
+    Mn = _rot(0, 1, eps) @ M
+    assert linkcomp.r8_norm(Mn) < linkcomp.R8_DEGENERATE_N
+    assert np.max(np.abs(linkcomp.decode_r8(linkcomp.encode_r8(Mn)) - Mn)) <= 2 * eps
 
 
 def test_r8_detects_a_wrong_reconstruction():
