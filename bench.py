@@ -43,7 +43,8 @@ NPOLES = 16
 TOL = 1e-10
 GAUGE_SEED, VEC_SEED = 5, 6
 # Dslash algorithmic bytes per output site (8 links + 1 input + 1 output vector, each crossing HBM once)
-DSLASH_BYTES_PER_SITE = {"fp32": 8 * 72 + 24 + 24, "fp32_r12": 8 * 48 + 24 + 24, "fp64": 8 * 144 + 48 + 48}
+DSLASH_BYTES_PER_SITE = {"fp32": 8 * 72 + 24 + 24, "fp32_r12": 8 * 48 + 24 + 24, "fp32_r8": 8 * 32 + 24 + 24,
+                         "fp32_l16": 8 * 24 + 24 + 24, "fp64": 8 * 144 + 48 + 48}
 DSLASH_FLOPS_PER_SITE = 570
 
 
@@ -396,7 +397,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
     ap.add_argument("--profile", choices=["dslash", "solve"], help="run a small fixed workload for ncu and exit")
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
     ap.add_argument("--batch", action="store_true", help="run the 64-lattice batched workload, print one JSON line")
@@ -496,7 +497,8 @@ def main():
     extra = {}
     if not args.quick:
         # FP64 solve (the plain method) and the other storage modes
-        for name, prec in (("fp64", lq.FP64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX)):
+        for name, prec in (("fp64", lq.FP64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX),
+                           ("fp32_r8", lq.FP32_R8), ("fp32_l16", lq.FP32_L16)):
             tms, sts = time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
             extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
                            "reliable_updates": sts[-1]["reliable_updates"],
@@ -507,7 +509,8 @@ def main():
     peak, peak_kind = read_peaks()
     vh = int(np.prod(DIMS)) // 2
     dsl = {}
-    for name, prec in (("fp32", lq.FP32), ("fp32_r12", lq.FP32_R12), ("fp64", lq.FP64)):
+    for name, prec in (("fp32", lq.FP32), ("fp32_r12", lq.FP32_R12), ("fp32_r8", lq.FP32_R8),
+                       ("fp32_l16", lq.FP32_L16), ("fp64", lq.FP64)):
         if args.quick and name != "fp32":
             continue
         mean_ms, med_ms = time_dslash(lq, torch, ctx, name, prec, 40, flush_buf)

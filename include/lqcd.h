@@ -56,6 +56,8 @@ extern "C" {
 #define LQCD_FP32 1     /* FP32 18-real links and vectors, FP32 arithmetic */
 #define LQCD_FP32_R12 2 /* FP32 12-real links (third row rebuilt), FP32 vectors */
 #define LQCD_FP16FIX 3  /* FP32 links; shifted Krylov vectors in 16-bit fixed point + per-site scale */
+#define LQCD_FP32_R8 4  /* FP32 8-real links (a2, a3, b1, arg a1, arg c1; the rest rebuilt), FP32 vectors */
+#define LQCD_FP32_L16 5 /* 16-bit fixed-point links (rows 0-1, q = rint(32767 u); row 2 rebuilt), FP32 vectors */
 
 #define LQCD_MAX_SHIFTS 32
 
@@ -96,8 +98,14 @@ int lqcd_set_stream(lqcd_ctx* ctx, void* stream);
  * lqcd_set_gauge - load a gauge field (Section 2: 3x3 complex SU(3) matrices on links).
  *   U_dev : device complex128 [V][4][3][3], canonical layout.  Read only.
  * Builds the internal copies (FP64 and FP32 with 1/2 eta_mu and the boundary sign
- * folded in; FP32 12-real rows 0-1 without signs).  The 12-real form assumes
- * the links are in SU(3).  Returns LQCD_ERR_ARG on a NULL pointer.
+ * folded in; FP32 12-real rows 0-1 without signs; the compressed forms of Section 5's outlook,
+ * without signs: 8-real FP32 and 16-bit rows 0-1).  The 12-real, 8-real and 16-bit forms
+ * assume the links are in SU(3).  8-real form, rows a, b, c: [a2, a3 | b1, arg a1, arg c1]
+ * with a1 = sqrt(1-N) e^{i arg a1}, N = |a2|^2 + |a3|^2, c1 = sqrt(N - |b1|^2) e^{i arg c1},
+ * and b2, b3, c2, c3 from the orthogonality of the rows and c = conj(a x b); links with
+ * N < 1e-14 are block-diagonal and store [b2, b3 | 0, arg a1, 8].  16-bit form: int16 codes
+ * q = rint(32767 u) (half to even) of the real and imaginary parts of rows a and b, decoded as
+ * q / 32767, row c = conj(a x b).  Returns LQCD_ERR_ARG on a NULL pointer.
  */
 int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev);
 
@@ -112,7 +120,8 @@ int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src);
 /*
  * lqcd_vector_bytes - bytes of one internal half-lattice vector of precision prec:
  *   LQCD_FP64                : 48*Vh, [3 colours][Vh] double2 (re, im)
- *   LQCD_FP32, LQCD_FP32_R12 : 24*Vh, [3 colours][Vh] float2
+ *   LQCD_FP32, LQCD_FP32_R12,
+ *   LQCD_FP32_R8, LQCD_FP32_L16 : 24*Vh, [3 colours][Vh] float2
  *   LQCD_FP16FIX             : 16*Vh, [Vh] x 16 bytes: six int16 codes q_i then a
  *                              float32 scale s; component i = q_i * s (order re0,
  *                              im0, re1, im1, re2, im2)
@@ -134,8 +143,8 @@ int lqcd_unpack_vector(lqcd_ctx* ctx, double* dst_dev, const void* src_dev, int 
  * dslash_eo - half-lattice hopping operator (Section 3.2; Fig. evenodd).
  *   out_parity = 1: out = D_oe in  (in on even sites, out on odd sites)
  *   out_parity = 0: out = D_eo in  (in on odd sites, out on even sites)
- *   prec       : LQCD_FP64, LQCD_FP32 or LQCD_FP32_R12 (which link copy is used);
- *                in_dev and out_dev are internal vectors of that precision
+ *   prec       : LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8 or LQCD_FP32_L16 (which
+ *                link copy is used); in_dev and out_dev are internal vectors of that precision
  *                (lqcd_vector_bytes(ctx, prec) bytes each, must not overlap).
  * Requires a gauge field (LQCD_ERR_STATE otherwise).  Asynchronous.
  */
@@ -143,7 +152,7 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
 
 /*
  * lqcd_apply_A - q = (A + sigma) p on even sites, A = 4 m^2 - D_eo D_oe (Section 3.2),
- * internal vectors of precision prec (FP64, FP32 or FP32_R12).  If pq_host is not
+ * internal vectors of precision prec (FP64, FP32, FP32_R12, FP32_R8 or FP32_L16).  If pq_host is not
  * NULL the call synchronises and stores Re<p, q> (FP64 accumulation) there.
  */
 int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
@@ -209,9 +218,10 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
  *   tol        : requested relative residual; the call returns LQCD_OK only when
  *                the FP64 true residual |b - (A+d_k)x_k|/|b| <= tol for every k
  *   maxiter    : cap on base iterations (and on each refinement solve)
- *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12 or LQCD_FP16FIX
- *                (FP32 arithmetic, FP64 dot products, solution accumulation,
- *                reliable updates and final residuals)
+ *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12, LQCD_FP16FIX, LQCD_FP32_R8
+ *                or LQCD_FP32_L16 (FP32 arithmetic with that link copy in the shifted CG,
+ *                FP64 dot products, solution accumulation, reliable updates and final
+ *                residuals; the refinement solves of R8 and L16 use the FP32 18-real links)
  *   stats      : host lqcd_solve_stats or NULL
  * Synchronises the context stream before returning.  b = 0 gives x_k = 0, y = 0.
  */
@@ -269,7 +279,8 @@ typedef struct {
 int mshift_cg_batch(lqcd_batch_problem* problems, int nprob, int nthreads);
 
 /*
- * lqcd_autotune - time the half-Dslash of precision prec (LQCD_FP32 or LQCD_FP32_R12) with 1, 2,
+ * lqcd_autotune - time the half-Dslash of precision prec (LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8
+ * or LQCD_FP32_L16) with 1, 2,
  * 4 and 8 threads per output site on this context's lattice and gauge field, keep the fastest
  * (as LQCD_OPT_DSLASH_TPS) and store it in *best_tps (may be NULL).  Allocates and frees two
  * temporary vectors; synchronises the context stream.

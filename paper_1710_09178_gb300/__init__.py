@@ -32,7 +32,10 @@ FP64 = 0
 FP32 = 1
 FP32_R12 = 2
 FP16FIX = 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_r12": FP32_R12, "fp16fix": FP16FIX}
+FP32_R8 = 4
+FP32_L16 = 5
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_r12": FP32_R12, "fp16fix": FP16FIX, "fp32_r8": FP32_R8,
+              "fp32_l16": FP32_L16}
 
 OPT_RELIABLE_INTERVAL = 1
 OPT_REFINE = 2

@@ -25,7 +25,7 @@ using namespace lqcd;
 
 extern "C" int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps) {
   if (!ctx) return LQCD_ERR_ARG;
-  if (!(prec == LQCD_FP32 || prec == LQCD_FP32_R12)) return fail(ctx, LQCD_ERR_ARG, "lqcd_autotune: FP32 modes only");
+  if (!vec_fp32(prec)) return fail(ctx, LQCD_ERR_ARG, "lqcd_autotune: FP32-vector modes only");
   if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_autotune: no gauge field loaded");
   Geom g = make_geom(ctx);
   size_t vb = 24 * (size_t)ctx->Vh;

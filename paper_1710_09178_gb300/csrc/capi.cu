@@ -36,7 +36,7 @@ int cuda_check(lqcd_ctx* ctx, cudaError_t e, const char* what) {
 }
 
 static bool prec_valid(int prec) {
-  return prec == LQCD_FP64 || prec == LQCD_FP32 || prec == LQCD_FP32_R12 || prec == LQCD_FP16FIX;
+  return prec == LQCD_FP64 || vec_fp32(prec) || prec == LQCD_FP16FIX;
 }
 
 static int ensure_scratch(lqcd_ctx* ctx) {
@@ -86,7 +86,7 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   force_release(ctx);
   traj_release(ctx);
   if (ctx->gauge.owned) {
-    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12};
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -112,7 +112,7 @@ int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src) {
     if (ctx->dims[d] != src->dims[d]) return fail(ctx, LQCD_ERR_DIMS, "lqcd_share_gauge: lattices differ");
   if (!src->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_share_gauge: source has no gauge field");
   if (ctx->gauge.owned) {
-    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12};
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -136,6 +136,10 @@ int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
     return cuda_check(ctx, e, "cudaMalloc(gauge fp32)");
   if (!gc.u12 && (e = cudaMalloc(&gc.u12, 2 * 4 * 3 * vh * sizeof(float4))) != cudaSuccess)
     return cuda_check(ctx, e, "cudaMalloc(gauge r12)");
+  if (!gc.u8 && (e = cudaMalloc(&gc.u8, 2 * 4 * 2 * vh * sizeof(float4))) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge r8)");
+  if (!gc.u16 && (e = cudaMalloc(&gc.u16, 2 * 4 * 24 * vh)) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge l16)");
   e = launch_pack_gauge(g, reinterpret_cast<const double2*>(U_dev), gc, ctx->stream);
   ctx->launches += 1;
   if (e != cudaSuccess) return cuda_check(ctx, e, "pack_gauge");
@@ -148,7 +152,9 @@ size_t lqcd_vector_bytes(const lqcd_ctx* ctx, int prec) {
   switch (prec) {
     case LQCD_FP64: return 48 * (size_t)ctx->Vh;
     case LQCD_FP32:
-    case LQCD_FP32_R12: return 24 * (size_t)ctx->Vh;
+    case LQCD_FP32_R12:
+    case LQCD_FP32_R8:
+    case LQCD_FP32_L16: return 24 * (size_t)ctx->Vh;
     case LQCD_FP16FIX: return 16 * (size_t)ctx->Vh;
   }
   return 0;

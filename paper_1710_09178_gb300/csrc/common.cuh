@@ -317,6 +317,20 @@ __device__ __forceinline__ double2 ld_stream(const double2* p, uint64_t pol) {
   return r;
 }
 
+__device__ __forceinline__ int4 ld_stream(const int4* p, uint64_t pol) {
+  int4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ int2 ld_stream(const int2* p, uint64_t pol) {
+  int2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol));
+  return r;
+}
+
 __device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol) {
   double2 r;
   asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
@@ -336,6 +350,8 @@ __device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t pol) {
 //   L64 : [p][mu][9][Vh] double2, row-major complex entries, times 1/2 eta*bc
 //   L32 : [p][mu] { float4 [4][Vh] ; float2 [Vh] }, same entry order, times 1/2 eta*bc
 //   L12 : [p][mu][3][Vh] float4  rows 0 and 1 only, no sign (third row rebuilt)
+//   L8  : [p][mu][2][Vh] float4  (a2, a3), (b1, arg a1, arg c1), no sign (8-real form)
+//   L16 : [p][mu] { int4 [Vh] ; int2 [Vh] }  int16 codes of rows 0 and 1, no sign
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Mat3<double> load_link64(const double2* __restrict__ U, int p, int mu, int i, int vh,
                                                    uint64_t pol) {
@@ -370,18 +386,8 @@ __device__ __forceinline__ Mat3<float> load_link32(const float* __restrict__ U, 
   return M;
 }
 
-// rows 0,1 from memory; row 2 = conj(row0 x row1) (exact for SU(3)); then scale by 1/2 * sign
-__device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U, int p, int mu, int i, int vh,
-                                                   float scale, uint64_t pol) {
-  const float4* blk = U + (size_t)(p * 4 + mu) * 3 * vh;
-  float4 a = ld_stream(blk + i, pol), b = ld_stream(blk + vh + i, pol), c = ld_stream(blk + 2 * vh + i, pol);
-  Mat3<float> M;
-  M.e[0][0] = cmake(a.x, a.y);
-  M.e[0][1] = cmake(a.z, a.w);
-  M.e[0][2] = cmake(b.x, b.y);
-  M.e[1][0] = cmake(b.z, b.w);
-  M.e[1][1] = cmake(c.x, c.y);
-  M.e[1][2] = cmake(c.z, c.w);
+// row 2 = conj(row0 x row1): exact for SU(3)
+__device__ __forceinline__ void complete_third_row(Mat3<float>& M) {
   // (r0 x r1)_k = r0_{k+1} r1_{k+2} - r0_{k+2} r1_{k+1}; row 2 is its complex conjugate
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -393,6 +399,9 @@ __device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U,
     float im = a1.re * b2.im + a1.im * b2.re - (a2.re * b1.im + a2.im * b1.re);
     M.e[2][k] = cmake(re, -im);
   }
+}
+
+__device__ __forceinline__ void scale_link(Mat3<float>& M, float scale) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -400,7 +409,118 @@ __device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U,
       M.e[r][c].re *= scale;
       M.e[r][c].im *= scale;
     }
+}
+
+// rows 0,1 from memory (three float4), row 2 rebuilt; then scale by 1/2 * sign
+__device__ __forceinline__ Mat3<float> decode_link12(float4 a, float4 b, float4 c, float scale) {
+  Mat3<float> M;
+  M.e[0][0] = cmake(a.x, a.y);
+  M.e[0][1] = cmake(a.z, a.w);
+  M.e[0][2] = cmake(b.x, b.y);
+  M.e[1][0] = cmake(b.z, b.w);
+  M.e[1][1] = cmake(c.x, c.y);
+  M.e[1][2] = cmake(c.z, c.w);
+  complete_third_row(M);
+  scale_link(M, scale);
   return M;
+}
+
+__device__ __forceinline__ Mat3<float> load_link12(const float4* __restrict__ U, int p, int mu, int i, int vh,
+                                                   float scale, uint64_t pol) {
+  const float4* blk = U + (size_t)(p * 4 + mu) * 3 * vh;
+  return decode_link12(ld_stream(blk + i, pol), ld_stream(blk + vh + i, pol), ld_stream(blk + 2 * vh + i, pol), scale);
+}
+
+__device__ __forceinline__ Cplx<float> cmulf(Cplx<float> a, Cplx<float> b) {
+  return cmake(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ Cplx<float> cconjf(Cplx<float> a) { return cmake(a.re, -a.im); }
+
+// 8-real form (rows a, b, c of an SU(3) link): stored a2, a3, b1, arg a1, arg c1.
+//   N = |a2|^2 + |a3|^2, a1 = sqrt(1 - N) e^{i arg a1}, c1 = sqrt(N - |b1|^2) e^{i arg c1};
+//   orthogonality of the rows and c = conj(a x b), b = conj(c x a) give the 2x2 systems
+//   [conj a2, conj a3; -a3, a2] (b2, b3) = (-conj(a1) b1, conj c1),
+//   [conj a2, conj a3; -a3, a2] (c2, c3) = (-conj(a1) c1, -conj b1), determinant N.
+// Block-diagonal links (N < 1e-14 at packing; the arg c1 slot holds 8) store b2, b3 in the
+// a2, a3 slots: a1 = e^{i arg a1}, c2 = -conj(b3 a1), c3 = conj(b2 a1).  Then scale by 1/2 * sign.
+__device__ __forceinline__ Mat3<float> decode_link8(float4 A, float4 B, float scale) {
+  float sa, ca;
+  __sincosf(B.z, &sa, &ca);
+  const Cplx<float> x2 = cmake(A.x, A.y), x3 = cmake(A.z, A.w);
+  Mat3<float> M;
+  if (B.w > 4.f) {
+    const Cplx<float> a1 = cmake(ca, sa), z = cmake(0.f, 0.f);
+    const Cplx<float> t2 = cmulf(x2, a1), t3 = cmulf(x3, a1);
+    M.e[0][0] = a1;
+    M.e[0][1] = z;
+    M.e[0][2] = z;
+    M.e[1][0] = z;
+    M.e[1][1] = x2;
+    M.e[1][2] = x3;
+    M.e[2][0] = z;
+    M.e[2][1] = cmake(-t3.re, t3.im);
+    M.e[2][2] = cconjf(t2);
+  } else {
+    float sc, cc;
+    __sincosf(B.w, &sc, &cc);
+    const Cplx<float> b1 = cmake(B.x, B.y);
+    const float N = A.x * A.x + A.y * A.y + A.z * A.z + A.w * A.w;
+    const float ma = sqrtf(fmaxf(1.f - N, 0.f));
+    const float mc = sqrtf(fmaxf(N - (B.x * B.x + B.y * B.y), 0.f));
+    const float rN = __frcp_rn(N);
+    const Cplx<float> a1 = cmake(ma * ca, ma * sa), c1 = cmake(mc * cc, mc * sc);
+    const Cplx<float> t = cmulf(cconjf(a1), b1), u = cmulf(cconjf(a1), c1);
+    const Cplx<float> cx2 = cconjf(x2), cx3 = cconjf(x3), cb1 = cconjf(b1), cc1 = cconjf(c1);
+    Cplx<float> p1 = cmulf(x2, t), p2 = cmulf(cx3, cc1);
+    M.e[1][1] = cmake(-(p1.re + p2.re) * rN, -(p1.im + p2.im) * rN);
+    p1 = cmulf(cx2, cc1);
+    p2 = cmulf(x3, t);
+    M.e[1][2] = cmake((p1.re - p2.re) * rN, (p1.im - p2.im) * rN);
+    p1 = cmulf(cx3, cb1);
+    p2 = cmulf(x2, u);
+    M.e[2][1] = cmake((p1.re - p2.re) * rN, (p1.im - p2.im) * rN);
+    p1 = cmulf(cx2, cb1);
+    p2 = cmulf(x3, u);
+    M.e[2][2] = cmake(-(p1.re + p2.re) * rN, -(p1.im + p2.im) * rN);
+    M.e[0][0] = a1;
+    M.e[0][1] = x2;
+    M.e[0][2] = x3;
+    M.e[1][0] = b1;
+    M.e[2][0] = c1;
+  }
+  scale_link(M, scale);
+  return M;
+}
+
+__device__ __forceinline__ Mat3<float> load_link8(const float4* __restrict__ U, int p, int mu, int i, int vh,
+                                                  float scale, uint64_t pol) {
+  const float4* blk = U + (size_t)(p * 4 + mu) * 2 * vh;
+  return decode_link8(ld_stream(blk + i, pol), ld_stream(blk + vh + i, pol), scale);
+}
+
+// 16-bit form: int16 codes q of (re, im) of rows 0 and 1, entry = q / 32767; row 2 rebuilt
+__device__ __forceinline__ float code_lo(int w) { return (float)(short)(w & 0xffff); }
+__device__ __forceinline__ float code_hi(int w) { return (float)(w >> 16); }
+
+__device__ __forceinline__ Mat3<float> decode_link16(int4 a, int2 b, float scale) {
+  const float k = 1.f / 32767.f;
+  Mat3<float> M;
+  M.e[0][0] = cmake(code_lo(a.x) * k, code_hi(a.x) * k);
+  M.e[0][1] = cmake(code_lo(a.y) * k, code_hi(a.y) * k);
+  M.e[0][2] = cmake(code_lo(a.z) * k, code_hi(a.z) * k);
+  M.e[1][0] = cmake(code_lo(a.w) * k, code_hi(a.w) * k);
+  M.e[1][1] = cmake(code_lo(b.x) * k, code_hi(b.x) * k);
+  M.e[1][2] = cmake(code_lo(b.y) * k, code_hi(b.y) * k);
+  complete_third_row(M);
+  scale_link(M, scale);
+  return M;
+}
+
+__device__ __forceinline__ Mat3<float> load_link16(const char* __restrict__ U, int p, int mu, int i, int vh,
+                                                   float scale, uint64_t pol) {
+  const char* blk = U + (size_t)(p * 4 + mu) * 24 * vh;
+  return decode_link16(ld_stream(reinterpret_cast<const int4*>(blk) + i, pol),
+                       ld_stream(reinterpret_cast<const int2*>(blk + 16 * (size_t)vh) + i, pol), scale);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,7 @@
 
 namespace lqcd {
 
-enum LinkFmt { kL64 = 0, kL32 = 1, kL12 = 2 };
+enum LinkFmt { kL64 = 0, kL32 = 1, kL12 = 2, kL8 = 3, kL16 = 4 };  // kL12 and up: signs applied after loading
 
 struct KArgs {
   void* out;
@@ -44,16 +44,56 @@ struct LinkTraits<kL64> {
   typedef double T;
 };
 
+// A link as loaded from memory (the compact forms stay compact while their loads are in flight)
+// and its decoding into a 3x3 matrix scaled by 1/2 * sign (signs are folded into L64 and L32).
 template <int LF>
-__device__ __forceinline__ Mat3<typename LinkTraits<LF>::T> load_link(const void* links, int p, int mu, int i, int vh,
-                                                                      int sign, uint64_t pol) {
+struct RawLink {
+  Mat3<typename LinkTraits<LF>::T> m;
+};
+template <>
+struct RawLink<kL12> {
+  float4 a, b, c;
+};
+template <>
+struct RawLink<kL8> {
+  float4 a, b;
+};
+template <>
+struct RawLink<kL16> {
+  int4 a;
+  int2 b;
+};
+
+template <int LF>
+__device__ __forceinline__ RawLink<LF> load_raw(const void* links, int p, int mu, int i, int vh, uint64_t pol) {
+  RawLink<LF> r;
   if constexpr (LF == kL64) {
-    return load_link64(static_cast<const double2*>(links), p, mu, i, vh, pol);
+    r.m = load_link64(static_cast<const double2*>(links), p, mu, i, vh, pol);
   } else if constexpr (LF == kL32) {
-    return load_link32(static_cast<const float*>(links), p, mu, i, vh, pol);
+    r.m = load_link32(static_cast<const float*>(links), p, mu, i, vh, pol);
+  } else if constexpr (LF == kL12) {
+    const float4* blk = static_cast<const float4*>(links) + (size_t)(p * 4 + mu) * 3 * vh;
+    r.a = ld_stream(blk + i, pol);
+    r.b = ld_stream(blk + vh + i, pol);
+    r.c = ld_stream(blk + 2 * vh + i, pol);
+  } else if constexpr (LF == kL8) {
+    const float4* blk = static_cast<const float4*>(links) + (size_t)(p * 4 + mu) * 2 * vh;
+    r.a = ld_stream(blk + i, pol);
+    r.b = ld_stream(blk + vh + i, pol);
   } else {
-    return load_link12(static_cast<const float4*>(links), p, mu, i, vh, 0.5f * (float)sign, pol);
+    const char* blk = static_cast<const char*>(links) + (size_t)(p * 4 + mu) * 24 * vh;
+    r.a = ld_stream(reinterpret_cast<const int4*>(blk) + i, pol);
+    r.b = ld_stream(reinterpret_cast<const int2*>(blk + 16 * (size_t)vh) + i, pol);
   }
+  return r;
+}
+
+template <int LF>
+__device__ __forceinline__ Mat3<typename LinkTraits<LF>::T> decode(const RawLink<LF>& r, int sign) {
+  if constexpr (LF == kL64 || LF == kL32) return r.m;
+  else if constexpr (LF == kL12) return decode_link12(r.a, r.b, r.c, 0.5f * (float)sign);
+  else if constexpr (LF == kL8) return decode_link8(r.a, r.b, 0.5f * (float)sign);
+  else return decode_link16(r.a, r.b, 0.5f * (float)sign);
 }
 
 // Which colours lane `sub` of a TPS group stores: TPS = 1 all; TPS = 2 lane 0 -> {0, 2},
@@ -91,10 +131,10 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
       const int mu = h >> 1;
       if ((h & 1) == 0) {
         nb[q] = neighbour_fwd(g, s, mu) >> 1;
-        sg[q] = (LF == kL12) ? link_sign_fwd(g, s, mu) : 1;
+        sg[q] = (LF >= kL12) ? link_sign_fwd(g, s, mu) : 1;
       } else {
         nb[q] = neighbour_bwd(g, s, mu) >> 1;
-        sg[q] = (LF == kL12) ? link_sign_bwd(g, s, mu) : 1;
+        sg[q] = (LF >= kL12) ? link_sign_bwd(g, s, mu) : 1;
       }
     }
     // FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
@@ -102,14 +142,13 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
     // two-stage software pipeline: the loads of hop q+1 are in flight while hop q is computed
     auto link_of = [&](int q) {
       const int h = sub + q * TPS;
-      return (h & 1) ? load_link<LF>(k.links, 1 - p, h >> 1, nb[q], vh, sg[q], pol)
-                     : load_link<LF>(k.links, p, h >> 1, i, vh, sg[q], pol);
+      return (h & 1) ? load_raw<LF>(k.links, 1 - p, h >> 1, nb[q], vh, pol) : load_raw<LF>(k.links, p, h >> 1, i, vh, pol);
     };
-    Mat3<T> Wn = link_of(0);
+    RawLink<LF> Wn = link_of(0);
     Vec3<T> vn = ldg_vec(in, nb[0], vh);
 #pragma unroll
     for (int q = 0; q < NH; ++q) {
-      Mat3<T> W = Wn;
+      const Mat3<T> W = decode<LF>(Wn, sg[q]);
       Vec3<T> v = vn;
       if (q + 1 < NH) {
         Wn = link_of(q + 1);
@@ -230,6 +269,8 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
   switch (a.prec) {
     case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, st);
     case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, st);
+    case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, st);
+    case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, st);
     default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st);
   }
 }

@@ -15,6 +15,11 @@ struct Geom;
 // Device-resident state of one shifted-CG solve (scalars, per-shift recurrences
 // and the coefficients of the pending window of shift-vector updates).
 constexpr int kMaxShifts = LQCD_MAX_SHIFTS;
+
+// precision modes whose vectors are [3][Vh] float2 (every FP32-arithmetic mode but the 16-bit one)
+__host__ __device__ inline bool vec_fp32(int prec) {
+  return prec == LQCD_FP32 || prec == LQCD_FP32_R12 || prec == LQCD_FP32_R8 || prec == LQCD_FP32_L16;
+}
 constexpr int kWindow = 10;  // iterations folded into one update of x_k, p_k
 
 struct SolverDev {
@@ -56,6 +61,8 @@ struct GaugeCopies {
   double2* u64 = nullptr;  // [2][4][9][Vh] double2, 1/2 eta*bc folded in
   float* u32 = nullptr;    // [2][4][18][Vh] floats (float4 x4 + float2), 1/2 eta*bc folded in
   float4* u12 = nullptr;   // [2][4][3][Vh] float4, rows 0-1, no sign
+  float4* u8 = nullptr;    // [2][4][2][Vh] float4, 8-real form, no sign
+  char* u16 = nullptr;     // [2][4] { int4 [Vh]; int2 [Vh] }, int16 codes of rows 0-1, no sign
   bool loaded = false;
   bool owned = true;       // false when borrowed from another context (lqcd_share_gauge)
 };

@@ -17,9 +17,17 @@ __device__ __forceinline__ Site site_from_address(const Geom& g, int l) {
   return s;
 }
 
-// One thread per (site, mu): canonical complex128 [V][4][3][3] -> three internal copies.
+__device__ __forceinline__ int pack_codes(double re, double im) {
+  // q = rint(32767 u), half to even, clamped to the symmetric int16 range
+  int qr = min(max(__double2int_rn(re * 32767.0), -32767), 32767);
+  int qi = min(max(__double2int_rn(im * 32767.0), -32767), 32767);
+  return (qr & 0xffff) | (qi << 16);
+}
+
+// One thread per (site, mu): canonical complex128 [V][4][3][3] -> five internal copies.
 __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2* __restrict__ u64,
-                                  float* __restrict__ u32, float4* __restrict__ u12) {
+                                  float* __restrict__ u32, float4* __restrict__ u12, float4* __restrict__ u8,
+                                  char* __restrict__ u16) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long V = 2LL * g.vh;
   if (t >= 4 * V) return;
@@ -56,13 +64,33 @@ __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2
       blk[(size_t)q * vh + i] =
           make_float4((float)e[2 * q].x, (float)e[2 * q].y, (float)e[2 * q + 1].x, (float)e[2 * q + 1].y);
   }
+  if (u8) {
+    // entries e[3 r + c]: a = e[0..2], b = e[3..5], c = e[6..8]
+    float4* blk = u8 + (size_t)(p * 4 + mu) * 2 * vh;
+    const double N = e[1].x * e[1].x + e[1].y * e[1].y + e[2].x * e[2].x + e[2].y * e[2].y;
+    const double tha = atan2(e[0].y, e[0].x);
+    if (N < 1e-14) {  // block-diagonal: keep b2, b3 and mark the arg c1 slot
+      blk[i] = make_float4((float)e[4].x, (float)e[4].y, (float)e[5].x, (float)e[5].y);
+      blk[vh + i] = make_float4(0.f, 0.f, (float)tha, 8.f);
+    } else {
+      blk[i] = make_float4((float)e[1].x, (float)e[1].y, (float)e[2].x, (float)e[2].y);
+      blk[vh + i] = make_float4((float)e[3].x, (float)e[3].y, (float)tha, (float)atan2(e[6].y, e[6].x));
+    }
+  }
+  if (u16) {
+    char* blk = u16 + (size_t)(p * 4 + mu) * 24 * vh;
+    reinterpret_cast<int4*>(blk)[i] =
+        make_int4(pack_codes(e[0].x, e[0].y), pack_codes(e[1].x, e[1].y), pack_codes(e[2].x, e[2].y),
+                  pack_codes(e[3].x, e[3].y));
+    reinterpret_cast<int2*>(blk + 16 * (size_t)vh)[i] = make_int2(pack_codes(e[4].x, e[4].y), pack_codes(e[5].x, e[5].y));
+  }
 }
 
 cudaError_t launch_pack_gauge(const Geom& g, const double2* U, GaugeCopies& gc, cudaStream_t st) {
   long long n = 8LL * g.vh;  // 4 V threads
   int bs = 256;
   long long nb = (n + bs - 1) / bs;
-  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12);
+  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12, gc.u8, gc.u16);
   return cudaGetLastError();
 }
 
@@ -77,7 +105,7 @@ __global__ void pack_vector_kernel(Geom g, void* __restrict__ dst, int prec, con
     d[i] = c0;
     d[vh + i] = c1;
     d[2 * vh + i] = c2;
-  } else if (prec == LQCD_FP32 || prec == LQCD_FP32_R12) {
+  } else if (vec_fp32(prec)) {
     float2* d = static_cast<float2*>(dst);
     d[i] = make_float2((float)c0.x, (float)c0.y);
     d[vh + i] = make_float2((float)c1.x, (float)c1.y);
@@ -100,7 +128,7 @@ __global__ void unpack_vector_kernel(Geom g, double2* __restrict__ dst, const vo
     const double2* s = static_cast<const double2*>(src);
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] = s[k * vh + i];
-  } else if (prec == LQCD_FP32 || prec == LQCD_FP32_R12) {
+  } else if (vec_fp32(prec)) {
     const float2* s = static_cast<const float2*>(src);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

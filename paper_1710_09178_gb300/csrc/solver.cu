@@ -405,7 +405,9 @@ static size_t vec_bytes(long long vh, int prec) {
   switch (prec) {
     case LQCD_FP64: return 48 * (size_t)vh;
     case LQCD_FP32:
-    case LQCD_FP32_R12: return 24 * (size_t)vh;
+    case LQCD_FP32_R12:
+    case LQCD_FP32_R8:
+    case LQCD_FP32_L16: return 24 * (size_t)vh;
     case LQCD_FP16FIX: return 16 * (size_t)vh;
   }
   return 0;

@@ -18,7 +18,7 @@ from paper_1710_09178_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32, FP32_R12, FP16FIX = 0, 1, 2, 3
+FP64, FP32, FP32_R12, FP16FIX, FP32_R8, FP32_L16 = 0, 1, 2, 3, 4, 5
 
 
 def _problem(dims, mass, npoles, gseed, vseed):
@@ -54,7 +54,7 @@ def _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec, tol=1e-10):
     return st, xs, y
 
 
-@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX])
+@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX, FP32_R8, FP32_L16])
 def test_converged_solve_matches_oracle_4444(prec):
     dims, mass = (4, 4, 4, 4), 0.1
     ctx, U, b, c0, res, poles = _problem(dims, mass, 12, 1, 2)
@@ -68,7 +68,7 @@ def test_converged_solve_matches_oracle_4444(prec):
     assert rel_norm(y, oy) <= (16 / lmin) * 2e-10
 
 
-@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX])
+@pytest.mark.parametrize("prec", [FP64, FP32, FP32_R12, FP16FIX, FP32_R8, FP32_L16])
 def test_converged_solve_16c8(prec):
     dims, mass = (16, 16, 16, 8), 0.05
     ctx, U, b, c0, res, poles = _problem(dims, mass, 14, 3, 4)
