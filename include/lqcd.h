@@ -201,6 +201,9 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
 #define LQCD_OPT_DSLASH_TPS 5        /* threads per output site in the FP32 Dslash (1, 2, 4 or 8; 0 = tuned) */
 #define LQCD_OPT_RELIABLE_DELTA 6    /* a reliable update is also due once |r| drops below delta times its
                                         largest value since the last one (default 0.01) */
+#define LQCD_OPT_PDL 7               /* 1 = kernels inside the captured solve graphs use programmatic dependent
+                                        launch, each starting while its predecessor drains (default; falls
+                                        back to 0 by itself where the driver refuses it), 0 = off */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*

@@ -43,6 +43,7 @@ OPT_BATCH = 3
 OPT_USE_GRAPH = 4
 OPT_DSLASH_TPS = 5
 OPT_RELIABLE_DELTA = 6
+OPT_PDL = 7
 
 MAX_SHIFTS = 32
 

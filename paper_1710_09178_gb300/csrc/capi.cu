@@ -259,6 +259,7 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
       ctx->batch = v;
       break;
     case LQCD_OPT_USE_GRAPH: ctx->use_graph = v ? 1 : 0; break;
+    case LQCD_OPT_PDL: ctx->use_pdl = v ? 1 : 0; break;
     case LQCD_OPT_DSLASH_TPS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return fail(ctx, LQCD_ERR_ARG, "tps must be 0,1,2,4,8");
       ctx->dslash_tps = v;

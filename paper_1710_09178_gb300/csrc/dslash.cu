@@ -109,8 +109,6 @@ template <int LF, int TPS, int EPI>
 __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   typedef typename LinkTraits<LF>::T T;
   typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
-  if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
-
   const int vh = g.vh;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt / TPS;
@@ -119,12 +117,18 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   const int p = k.out_parity;
   const V2* in = static_cast<const V2*>(k.in);
 
-  Vec3<T> accf = vzero<T>(), accb = vzero<T>();
+  // hops of this lane: h = sub, sub + TPS, ...; h even = forward, odd = backward along mu = h / 2
+  constexpr int NH = 8 / TPS;
+  int nb[NH] = {}, sg[NH] = {};
+  // FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
+  const uint64_t pol = (LF == kL64) ? policy_evict_first() : policy_evict_last();
+  auto link_of = [&](int q) {
+    const int h = sub + q * TPS;
+    return (h & 1) ? load_raw<LF>(k.links, 1 - p, h >> 1, nb[q], vh, pol) : load_raw<LF>(k.links, p, h >> 1, i, vh, pol);
+  };
+  RawLink<LF> Wn;
   if (valid) {
     Site s = site_of(g, p, i);
-    // hops of this lane: h = sub, sub + TPS, ...; h even = forward, odd = backward along mu = h / 2
-    constexpr int NH = 8 / TPS;
-    int nb[NH], sg[NH];
 #pragma unroll
     for (int q = 0; q < NH; ++q) {
       const int h = sub + q * TPS;  // TPS divides 8, so h < 8 and its parity is sub's
@@ -137,14 +141,15 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
         sg[q] = (LF >= kL12) ? link_sign_bwd(g, s, mu) : 1;
       }
     }
-    // FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
-    const uint64_t pol = (LF == kL64) ? policy_evict_first() : policy_evict_last();
+    Wn = link_of(0);  // links are never written by the kernels of a solve: fetched before the wait
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
+
+  Vec3<T> accf = vzero<T>(), accb = vzero<T>();
+  if (valid) {
     // two-stage software pipeline: the loads of hop q+1 are in flight while hop q is computed
-    auto link_of = [&](int q) {
-      const int h = sub + q * TPS;
-      return (h & 1) ? load_raw<LF>(k.links, 1 - p, h >> 1, nb[q], vh, pol) : load_raw<LF>(k.links, p, h >> 1, i, vh, pol);
-    };
-    RawLink<LF> Wn = link_of(0);
     Vec3<T> vn = ldg_vec(in, nb[0], vh);
 #pragma unroll
     for (int q = 0; q < NH; ++q) {
@@ -218,26 +223,25 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
 }
 
 template <int LF, int TPS>
-static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream_t st, int bs) {
+static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream_t st, int bs, bool pdl) {
   long long threads = (long long)g.vh * TPS;
   unsigned nb = (unsigned)((threads + bs - 1) / bs);
   switch (epi) {
-    case Epi::Plain: dslash_kernel<LF, TPS, 0><<<nb, bs, 0, st>>>(g, k); break;
-    case Epi::AApply: dslash_kernel<LF, TPS, 1><<<nb, bs, 0, st>>>(g, k); break;
-    case Epi::Resid: dslash_kernel<LF, TPS, 2><<<nb, bs, 0, st>>>(g, k); break;
+    case Epi::Plain: return launch_k(pdl, dslash_kernel<LF, TPS, 0>, dim3(nb), dim3(bs), st, g, k);
+    case Epi::AApply: return launch_k(pdl, dslash_kernel<LF, TPS, 1>, dim3(nb), dim3(bs), st, g, k);
+    default: return launch_k(pdl, dslash_kernel<LF, TPS, 2>, dim3(nb), dim3(bs), st, g, k);
   }
-  return cudaGetLastError();
 }
 
 template <int LF>
-static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cudaStream_t st) {
+static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cudaStream_t st, bool pdl) {
   const int bs = 128;
-  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, bs);  // FP64 is arithmetic-bound: 1 thread/site
+  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);  // FP64 is arithmetic-bound
   switch (tps) {
-    case 1: return launch_tps<LF, 1>(g, k, epi, st, bs);
-    case 2: return launch_tps<LF, 2>(g, k, epi, st, bs);
-    case 4: return launch_tps<LF, 4>(g, k, epi, st, bs);
-    default: return launch_tps<LF, 8>(g, k, epi, st, bs);
+    case 1: return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);
+    case 2: return launch_tps<LF, 2>(g, k, epi, st, bs, pdl);
+    case 4: return launch_tps<LF, 4>(g, k, epi, st, bs, pdl);
+    default: return launch_tps<LF, 8>(g, k, epi, st, bs, pdl);
   }
 }
 
@@ -267,11 +271,11 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
   if (tps != 1 && tps != 2 && tps != 4 && tps != 8) return cudaErrorInvalidValue;
   if (nlaunch) *nlaunch += 1;
   switch (a.prec) {
-    case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, st);
-    case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, st);
-    case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, st);
-    case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, st);
-    default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st);
+    case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, st, a.pdl);
+    case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, st, a.pdl);
+    case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, st, a.pdl);
+    case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, st, a.pdl);
+    default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st, a.pdl);
   }
 }
 

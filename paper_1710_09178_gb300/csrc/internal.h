@@ -86,6 +86,7 @@ struct lqcd_ctx {
   int refine = 1;
   int batch = 20;  // iterations per host-polled batch when graphs are off
   int use_graph = 1;
+  int use_pdl = 1;         // programmatic dependent launch inside captured graphs
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
@@ -128,6 +129,7 @@ struct DslashArgs {
   const int* done = nullptr;     // if non-null and *done, the kernel returns at entry
   double* partials = nullptr;
   unsigned* ticket = nullptr;
+  bool pdl = false;              // programmatic dependent launch (inside captured solve graphs)
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
 int dslash_grid_blocks(const Geom& g, int prec, int tps);

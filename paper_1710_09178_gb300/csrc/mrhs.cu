@@ -83,6 +83,8 @@ template <int LF, typename T, bool AAPPLY>
 __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* links, MrhsVecs vv, int out_parity,
                                                           MrhsDev* md, double* partials) {
   typedef typename V2Of<T>::type V2;
+  pdl_wait();
+  pdl_trigger();
   const int n_act = md->n_active;
   if (md->done) return;
   const int g0 = blockIdx.y * kMrhsGroup;
@@ -180,6 +182,8 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
 template <typename T>
 __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, MrhsDev* md, double* partials) {
   typedef typename V2Of<T>::type V2;
+  pdl_wait();
+  pdl_trigger();
   const int n_act = md->n_active;
   if (md->done) return;
   const int g0 = blockIdx.y * kMrhsGroup;
@@ -254,6 +258,8 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
 template <typename T>
 __global__ void __launch_bounds__(256) mrhs_pupdate_kernel(Geom g, MrhsVecs vv, MrhsDev* md) {
   typedef typename V2Of<T>::type V2;
+  pdl_wait();
+  pdl_trigger();
   if (md->done) return;
   const int n_act = md->n_active;
   const int g0 = blockIdx.y * kMrhsGroup;
@@ -408,27 +414,39 @@ int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out) {
   return LQCD_OK;
 }
 
+// One iteration's four kernels.  With pdl, each kernel but the first of a captured body
+// (*chained false) is launched with a programmatic dependency on the one before it.
 template <typename T>
 static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, const Geom& g, int prec, int groups,
-                                          cudaStream_t st, int* nl) {
+                                          cudaStream_t st, int* nl, bool pdl, bool* chained) {
   dim3 grid(mw->nbx, groups);
   const void* links = prec == LQCD_FP64 ? (const void*)ctx->gauge.u64
                       : prec == LQCD_FP32_R12 ? (const void*)ctx->gauge.u12 : (const void*)ctx->gauge.u32;
+  auto next = [&]() {
+    bool r = pdl && *chained;
+    *chained = true;
+    return r;
+  };
+  const bool p1 = next(), p2 = next(), p3 = next(), p4 = next();
+  cudaError_t e;
   if (prec == LQCD_FP64) {
-    mrhs_dslash_kernel<0, double, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
-    mrhs_dslash_kernel<0, double, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+    e = launch_k(p1, mrhs_dslash_kernel<0, double, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
+    if (e == cudaSuccess)
+      e = launch_k(p2, mrhs_dslash_kernel<0, double, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
   } else if (prec == LQCD_FP32_R12) {
-    mrhs_dslash_kernel<2, float, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
-    mrhs_dslash_kernel<2, float, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+    e = launch_k(p1, mrhs_dslash_kernel<2, float, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
+    if (e == cudaSuccess)
+      e = launch_k(p2, mrhs_dslash_kernel<2, float, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
   } else {
-    mrhs_dslash_kernel<1, float, false><<<grid, 128, 0, st>>>(g, links, mw->vv, 1, mw->md, mw->partials);
-    mrhs_dslash_kernel<1, float, true><<<grid, 128, 0, st>>>(g, links, mw->vv, 0, mw->md, mw->partials);
+    e = launch_k(p1, mrhs_dslash_kernel<1, float, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
+    if (e == cudaSuccess)
+      e = launch_k(p2, mrhs_dslash_kernel<1, float, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
   }
-  mrhs_update_kernel<T><<<grid, 128, 0, st>>>(g, mw->vv, mw->md, mw->partials);
+  if (e == cudaSuccess) e = launch_k(p3, mrhs_update_kernel<T>, grid, dim3(128), st, g, mw->vv, mw->md, mw->partials);
   dim3 grid3((3 * g.vh + 255) / 256, groups);
-  mrhs_pupdate_kernel<T><<<grid3, 256, 0, st>>>(g, mw->vv, mw->md);
+  if (e == cudaSuccess) e = launch_k(p4, mrhs_pupdate_kernel<T>, grid3, dim3(256), st, g, mw->vv, mw->md);
   *nl += 4;
-  return cudaGetLastError();
+  return e;
 }
 
 // Solve (A + sigma_j) e_j = r_j (r_j already in the workspace's r buffers) until
@@ -457,9 +475,10 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
     // plain launches, the host polls the done flag every two iterations
     int hs[4] = {0, 0, 0, 0};
     for (int pass = 0; pass < maxiter / 2 + 2; ++pass) {
+      bool chained = false;
       for (int it = 0; it < 2 && e == cudaSuccess; ++it)
-        e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nl)
-                                : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nl);
+        e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nl, false, &chained)
+                                : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nl, false, &chained);
       if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs iteration");
       if ((e = cudaMemcpyAsync(hs, &mw->md->iter, 4 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_check(ctx, e, "mrhs readback");
@@ -474,40 +493,51 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
   if (!mw->graph || mw->graph_m != m || mw->graph_prec != prec) {
     if (mw->graph) cudaGraphExecDestroy(mw->graph);
     mw->graph = nullptr;
-    cudaGraph_t graph;
-    if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return cuda_check(ctx, e, "cudaGraphCreate");
-    cudaGraphConditionalHandle handle;
-    if ((e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
-      return cuda_check(ctx, e, "cudaGraphConditionalHandleCreate");
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    if ((e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess)
-      return cuda_check(ctx, e, "cudaGraphAddNode");
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-        cudaSuccess)
-      return cuda_check(ctx, e, "cudaStreamBeginCaptureToGraph");
+    // with programmatic dependent launch first; captured again without it if refused
+    cudaGraphExec_t exec = nullptr;
     int nodes = 0;
-    for (int it = 0; it < 2 && e == cudaSuccess; ++it)
-      e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nodes)
-                              : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nodes);
-    if (e == cudaSuccess) {
-      mrhs_ctl_kernel<<<1, 32, 0, st>>>(handle, mw->md);
-      nodes += 1;
-      e = cudaGetLastError();
+    e = cudaErrorUnknown;
+    for (int attempt = 0; attempt < 2 && e != cudaSuccess; ++attempt) {
+      const bool pdl = attempt == 0 && ctx->use_pdl;
+      if (attempt == 1 && !ctx->use_pdl) break;
+      if (attempt == 1) {
+        cudaGetLastError();
+        ctx->use_pdl = 0;
+      }
+      cudaGraph_t graph;
+      if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) return cuda_check(ctx, e, "cudaGraphCreate");
+      cudaGraphConditionalHandle handle;
+      if ((e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return cuda_check(ctx, e, "cudaGraphConditionalHandleCreate");
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cnode;
+      if ((e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess)
+        return cuda_check(ctx, e, "cudaGraphAddNode");
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+          cudaSuccess)
+        return cuda_check(ctx, e, "cudaStreamBeginCaptureToGraph");
+      nodes = 0;
+      bool chained = false;
+      for (int it = 0; it < 2 && e == cudaSuccess; ++it)
+        e = (prec == LQCD_FP64) ? enqueue_mrhs_iteration<double>(ctx, mw, g, prec, groups, st, &nodes, pdl, &chained)
+                                : enqueue_mrhs_iteration<float>(ctx, mw, g, prec, groups, st, &nodes, pdl, &chained);
+      if (e == cudaSuccess) {
+        mrhs_ctl_kernel<<<1, 32, 0, st>>>(handle, mw->md);
+        nodes += 1;
+        e = cudaGetLastError();
+      }
+      cudaGraph_t captured;
+      cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
     }
-    cudaGraph_t captured;
-    cudaError_t e2 = cudaStreamEndCapture(st, &captured);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs capture");
-    if (e2 != cudaSuccess) return cuda_check(ctx, e2, "mrhs capture");
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGraphInstantiate(mrhs)");
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mrhs graph");
     mw->graph = exec;
     mw->graph_m = m;
     mw->graph_prec = prec;

@@ -158,6 +158,8 @@ template <typename T, int SF>
 __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
   typedef typename KTraits<T>::V2 V2;
   SolverDev* sd = a.sd;
+  pdl_wait();
+  pdl_trigger();
   if (sd->done) return;
   const int m = sd->m;
   const T alpha = (T)sd->alpha;
@@ -186,6 +188,8 @@ __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(256) p_update_kernel(Geom g, const void* r, void* p, const SolverDev* sd) {
   typedef typename KTraits<T>::V2 V2;
+  pdl_wait();
+  pdl_trigger();
   if (sd->done) return;
   const T beta = (T)sd->beta;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,6 +217,8 @@ struct FlushArgs {
 template <typename T, int SF>
 __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
   SolverDev* sd = a.sd;
+  pdl_wait();
+  pdl_trigger();
   const int m = sd->m;
   if (m == 0) return;  // nothing pending
   __shared__ T cP[kMaxShifts], cX[kMaxShifts], cpi[kMaxShifts][kWindow], cchi[kMaxShifts][kWindow];
@@ -292,6 +298,8 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
 template <typename T>
 __global__ void ru_finish_kernel(Geom g, const double2* __restrict__ r64, void* r, const SolverDev* sd) {
   typedef typename KTraits<T>::V2 V2;
+  pdl_wait();
+  pdl_trigger();
   if (sd->ru_skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 3 * g.vh) {
@@ -306,6 +314,8 @@ __global__ void ru_finish_kernel(Geom g, const double2* __restrict__ r64, void* 
 
 // bookkeeping of a reliable update, one thread, after ru_finish_kernel
 __global__ void ru_close_kernel(SolverDev* sd, int* ru_count) {
+  pdl_wait();
+  pdl_trigger();
   if (sd->ru_skip) return;
   double rr = sd->scal[0];
   if (!isfinite(rr)) {
@@ -497,6 +507,14 @@ struct Launcher {
   Workspace* w;
   Geom g;
   int nlaunch = 0;
+  bool pdl = false;      // launch with programmatic dependencies (captured graph bodies)
+  bool chained = false;  // a kernel of this launcher precedes the next one in the stream
+  // PDL for every kernel but the first of a captured body, whose predecessor is not ours
+  bool next_pdl() {
+    bool r = pdl && chained;
+    chained = true;
+    return r;
+  }
 };
 
 // the four kernels of one base iteration
@@ -512,9 +530,11 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   d1.prec = w->prec == LQCD_FP16FIX ? LQCD_FP32 : w->prec;
   d1.tps = ctx->dslash_tps;
   d1.done = done;
+  d1.pdl = L.next_pdl();
   cudaError_t e = launch_dslash(L.g, ctx->gauge, d1, st, &L.nlaunch);
   if (e != cudaSuccess) return e;
   DslashArgs d2 = d1;
+  d2.pdl = L.next_pdl();
   d2.out = w->q;
   d2.in = w->tmp;
   d2.out_parity = 0;
@@ -536,18 +556,20 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   ra.ticket = w->tickets + 1;
   int nb = (L.g.vh + 255) / 256;
   int nb3 = (3 * L.g.vh + 255) / 256;
+  const bool pr = L.next_pdl(), pp = L.next_pdl();
+  const void* rc = w->r;
   if (w->kprec == LQCD_FP64) {
-    r_update_kernel<double, kS64><<<nb, 256, 0, st>>>(L.g, ra);
-    p_update_kernel<double><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+    e = launch_k(pr, r_update_kernel<double, kS64>, dim3(nb), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
   } else if (w->sfmt == kS16) {
-    r_update_kernel<float, kS16><<<nb, 256, 0, st>>>(L.g, ra);
-    p_update_kernel<float><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+    e = launch_k(pr, r_update_kernel<float, kS16>, dim3(nb), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
   } else {
-    r_update_kernel<float, kS32><<<nb, 256, 0, st>>>(L.g, ra);
-    p_update_kernel<float><<<nb3, 256, 0, st>>>(L.g, w->r, w->p, w->sd);
+    e = launch_k(pr, r_update_kernel<float, kS32>, dim3(nb), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
   }
   L.nlaunch += 2;
-  return cudaGetLastError();
+  return e;
 }
 
 static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n) {
@@ -565,11 +587,11 @@ static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2*
   fa.partials = w->partials;
   fa.ticket = w->tickets + 2;
   int nb = (L.g.vh + 127) / 128;
-  if (w->sfmt == kS64) flush_kernel<double, kS64><<<nb, 128, 0, w->st>>>(L.g, fa);
-  else if (w->sfmt == kS16) flush_kernel<float, kS16><<<nb, 128, 0, w->st>>>(L.g, fa);
-  else flush_kernel<float, kS32><<<nb, 128, 0, w->st>>>(L.g, fa);
+  const bool pdl = L.next_pdl();
   L.nlaunch += 1;
-  return cudaGetLastError();
+  if (w->sfmt == kS64) return launch_k(pdl, flush_kernel<double, kS64>, dim3(nb), dim3(128), w->st, L.g, fa);
+  if (w->sfmt == kS16) return launch_k(pdl, flush_kernel<float, kS16>, dim3(nb), dim3(128), w->st, L.g, fa);
+  return launch_k(pdl, flush_kernel<float, kS32>, dim3(nb), dim3(128), w->st, L.g, fa);
 }
 
 // FP64 residual r64 = bvec - (A + sigma) x into r64, |r64|^2 into *dot (device)
@@ -583,9 +605,11 @@ static cudaError_t enqueue_resid64(Launcher& L, const double2* x, const double2*
   d1.out_parity = 1;
   d1.prec = LQCD_FP64;
   d1.done = done;
+  d1.pdl = L.next_pdl();
   cudaError_t e = launch_dslash(L.g, ctx->gauge, d1, w->st, &L.nlaunch);
   if (e != cudaSuccess) return e;
   DslashArgs d2 = d1;
+  d2.pdl = L.next_pdl();
   d2.out = w->r64;
   d2.in = w->tmp64;
   d2.out_parity = 0;
@@ -616,13 +640,16 @@ static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2*
           cudaSuccess)
         return e;
       int nb3 = (3 * L.g.vh + 255) / 256;
+      const bool pf = L.next_pdl(), pc = L.next_pdl();
+      const double2* r64 = w->r64;
+      const SolverDev* sdc = w->sd;
       if (w->kprec == LQCD_FP64)
-        ru_finish_kernel<double><<<nb3, 256, 0, w->st>>>(L.g, w->r64, w->r, w->sd);
+        e = launch_k(pf, ru_finish_kernel<double>, dim3(nb3), dim3(256), w->st, L.g, r64, w->r, sdc);
       else
-        ru_finish_kernel<float><<<nb3, 256, 0, w->st>>>(L.g, w->r64, w->r, w->sd);
-      ru_close_kernel<<<1, 1, 0, w->st>>>(w->sd, w->ru_count);
+        e = launch_k(pf, ru_finish_kernel<float>, dim3(nb3), dim3(256), w->st, L.g, r64, w->r, sdc);
+      if (e == cudaSuccess) e = launch_k(pc, ru_close_kernel, dim3(1), dim3(1), w->st, w->sd, w->ru_count);
       L.nlaunch += 2;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (e != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -661,36 +688,49 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
     auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0), k0);
     auto it = w->graphs.find(key);
     if (it == w->graphs.end()) {
-      cudaGraph_t graph;
-      LQ_CUDA(cudaGraphCreate(&graph, 0));
-      cudaGraphConditionalHandle handle;
-      LQ_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-      cudaGraphNodeParams cp = {};
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = handle;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      cudaGraphNode_t cnode;
-      LQ_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-      cudaGraph_t body = cp.conditional.phGraph_out[0];
-      Launcher C{ctx, w, L.g, 0};
-      LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
-      if (e == cudaSuccess) {
-        loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, w->sd);
-        C.nlaunch += 1;
-        e = cudaGetLastError();
+      // with programmatic dependent launch first; captured again without it if the driver
+      // refuses programmatic edges inside the conditional body
+      cudaGraphExec_t exec = nullptr;
+      int nodes = 0;
+      cudaError_t e = cudaErrorUnknown;
+      for (int attempt = 0; attempt < 2 && e != cudaSuccess; ++attempt) {
+        const bool pdl = attempt == 0 && ctx->use_pdl;
+        if (attempt == 1 && !ctx->use_pdl) break;
+        if (attempt == 1) {
+          cudaGetLastError();
+          ctx->use_pdl = 0;
+        }
+        cudaGraph_t graph;
+        LQ_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle handle;
+        LQ_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        LQ_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        Launcher C{ctx, w, L.g, 0};
+        C.pdl = pdl;
+        LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
+        if (e == cudaSuccess) {
+          loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, w->sd);
+          C.nlaunch += 1;
+          e = cudaGetLastError();
+        }
+        cudaGraph_t captured;
+        cudaError_t e2 = cudaStreamEndCapture(w->st, &captured);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        nodes = C.nlaunch;
       }
-      cudaGraph_t captured;
-      cudaError_t e2 = cudaStreamEndCapture(w->st, &captured);
-      LQ_CUDA(e);
-      LQ_CUDA(e2);
-      cudaGraphExec_t exec;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
       LQ_CUDA(e);
       w->graphs[key] = exec;
-      w->graph_nodes[key] = C.nlaunch;
+      w->graph_nodes[key] = nodes;
       it = w->graphs.find(key);
     }
     LQ_CUDA(cudaGraphLaunch(it->second, w->st));

@@ -137,6 +137,24 @@ def test_no_graph_path_matches_graph_path():
         assert np.array_equal(a, c)  # deterministic reductions: identical bits
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_programmatic_dependent_launch_matches_plain_launches(prec):
+    # the same graphs captured with and without programmatic dependencies between their kernels,
+    # refinement (its own multi-RHS graph) included: identical bits
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (16, 16, 16, 8), 0.05
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 14, 3, 4)
+    rc1, st1, xs1, y1 = gpu_mshift(ctx, b, poles, res, c0, prec=prec, want_y=True)
+    ctx.set_option(lq.OPT_PDL, 0)
+    rc2, st2, xs2, y2 = gpu_mshift(ctx, b, poles, res, c0, prec=prec, want_y=True)
+    assert rc1 == rc2 == 0
+    assert st1["iterations"] == st2["iterations"] and st1["refine_iterations"] == st2["refine_iterations"]
+    for a, c in zip(xs1, xs2):
+        assert np.array_equal(a, c)
+    assert np.array_equal(y1, y2)
+
+
 @pytest.mark.parametrize("dims,mass,npoles", [((4, 4, 4, 4), 0.1, 12), ((16, 16, 16, 8), 0.05, 14)])
 def test_fp64_unrefined_solve_matches_oracle_with_same_stopping_rule(dims, mass, npoles):
     # No refinement: every shift stops on |zeta_k| |r| <= tol |b| exactly as in the oracle, and

@@ -85,3 +85,38 @@ def test_trajectory_is_reversible_and_reject_keeps_links():
     assert np.max(np.abs(back_links.cpu().numpy() - U0)) < 1e-10
     assert np.max(np.abs(back_mom.cpu().numpy() + p0)) < 1e-9
     assert abs(r1["dH"] + r2["dH"]) < 1e-8
+
+
+def test_chain_satisfies_exp_minus_dH_identity():
+    # Section 3.1: the MD map is reversible and area-preserving, so over an equilibrium ensemble
+    # <exp(-dH)> = 1 exactly (and hence <dH> >= 0).  A 4^4 chain at beta 5.4, m 0.1, tau 1 in 12
+    # Omelyan steps: 30 thermalising trajectories from the random start, then 100 measured ones;
+    # bar 4 standard errors.
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    lo, hi = 4 * MASS ** 2, 16 + 4 * MASS ** 2
+    act = rational.zolotarev_inv_sqrt(12, lo, hi)[:3]
+    heat = rational.remez_power(0.25, lo, hi, 12)[:3]
+    ctx, U0 = make_context(DIMS, MASS, gauge_seed=41)
+    Ud = to_dev(U0)
+    n_therm, n_meas = 30, 100
+    dH, acc = [], []
+    for t in range(n_therm + n_meas):
+        p = _momenta(5000 + t)
+        xi = inputs.gaussian_vector(DIMS, 7000 + t)
+        u = float(inputs.counter_uniform(9000, np.array([t], dtype=np.uint64), 0)[0])
+        rc, res = lq.rhmc_trajectory(ctx, Ud, to_dev(p), to_dev(xi), u, BETA, 1.0, 12, act, heat, tol=1e-10,
+                                     md_tol=1e-9, prec=lq.FP32, prec_action=FP64)
+        assert rc == 0
+        if t >= n_therm:
+            dH.append(res["dH"])
+            acc.append(res["accepted"])
+    torch.cuda.synchronize()
+    dH = np.array(dH)
+    w = np.exp(-dH)
+    err = np.std(w, ddof=1) / np.sqrt(n_meas)
+    assert abs(np.mean(w) - 1.0) <= 4 * err, (np.mean(w), err, np.mean(dH))
+    assert np.mean(dH) >= -4 * np.std(dH, ddof=1) / np.sqrt(n_meas)
+    assert 0.3 < np.mean(acc) <= 1.0
