@@ -204,6 +204,9 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
 #define LQCD_OPT_PDL 7               /* 1 = kernels inside the captured solve graphs use programmatic dependent
                                         launch, each starting while its predecessor drains (default; falls
                                         back to 0 by itself where the driver refuses it), 0 = off */
+#define LQCD_OPT_DF_RESID 8          /* mixed modes: 1 = reliable updates and true-residual checks in
+                                        double-FP32 arithmetic (FP32 hi/lo pairs, exact products, TwoSum
+                                        accumulation; ~48-bit, FP32 units only) (default), 0 = FP64 */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*

@@ -44,6 +44,7 @@ OPT_USE_GRAPH = 4
 OPT_DSLASH_TPS = 5
 OPT_RELIABLE_DELTA = 6
 OPT_PDL = 7
+OPT_DF_RESID = 8
 
 MAX_SHIFTS = 32
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblqcd.so")
 
-CU_SOURCES = ["capi.cu", "pack.cu", "dslash.cu", "solver.cu", "mrhs.cu", "force.cu", "trajectory.cu", "batch.cu", "noalloc.cu"]
+CU_SOURCES = ["capi.cu", "pack.cu", "dslash.cu", "solver.cu", "mrhs.cu", "force.cu", "trajectory.cu", "batch.cu", "noalloc.cu", "df64.cu"]
 CPP_SOURCES = ["rational.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -86,7 +86,8 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   force_release(ctx);
   traj_release(ctx);
   if (ctx->gauge.owned) {
-    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16};
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16,
+                 ctx->gauge.u32lo};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -112,7 +113,8 @@ int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src) {
     if (ctx->dims[d] != src->dims[d]) return fail(ctx, LQCD_ERR_DIMS, "lqcd_share_gauge: lattices differ");
   if (!src->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_share_gauge: source has no gauge field");
   if (ctx->gauge.owned) {
-    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16};
+    void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16,
+                 ctx->gauge.u32lo};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -140,6 +142,8 @@ int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
     return cuda_check(ctx, e, "cudaMalloc(gauge r8)");
   if (!gc.u16 && (e = cudaMalloc(&gc.u16, 2 * 4 * 24 * vh)) != cudaSuccess)
     return cuda_check(ctx, e, "cudaMalloc(gauge l16)");
+  if (!gc.u32lo && (e = cudaMalloc(&gc.u32lo, 2 * 4 * 18 * vh * sizeof(float))) != cudaSuccess)
+    return cuda_check(ctx, e, "cudaMalloc(gauge fp32 rounding errors)");
   e = launch_pack_gauge(g, reinterpret_cast<const double2*>(U_dev), gc, ctx->stream);
   ctx->launches += 1;
   if (e != cudaSuccess) return cuda_check(ctx, e, "pack_gauge");
@@ -260,6 +264,7 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
       break;
     case LQCD_OPT_USE_GRAPH: ctx->use_graph = v ? 1 : 0; break;
     case LQCD_OPT_PDL: ctx->use_pdl = v ? 1 : 0; break;
+    case LQCD_OPT_DF_RESID: ctx->df_resid = v ? 1 : 0; break;
     case LQCD_OPT_DSLASH_TPS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return fail(ctx, LQCD_ERR_ARG, "tps must be 0,1,2,4,8");
       ctx->dslash_tps = v;

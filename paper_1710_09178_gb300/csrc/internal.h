@@ -63,6 +63,7 @@ struct GaugeCopies {
   float4* u12 = nullptr;   // [2][4][3][Vh] float4, rows 0-1, no sign
   float4* u8 = nullptr;    // [2][4][2][Vh] float4, 8-real form, no sign
   char* u16 = nullptr;     // [2][4] { int4 [Vh]; int2 [Vh] }, int16 codes of rows 0-1, no sign
+  float* u32lo = nullptr;  // as u32: fl32(1/2 eta bc U - u32), the FP32 rounding errors (double-FP32 residuals)
   bool loaded = false;
   bool owned = true;       // false when borrowed from another context (lqcd_share_gauge)
 };
@@ -87,6 +88,7 @@ struct lqcd_ctx {
   int batch = 20;  // iterations per host-polled batch when graphs are off
   int use_graph = 1;
   int use_pdl = 1;         // programmatic dependent launch inside captured graphs
+  int df_resid = 1;        // mixed modes: residuals in double-FP32 instead of FP64
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
@@ -133,6 +135,31 @@ struct DslashArgs {
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
 int dslash_grid_blocks(const Geom& g, int prec, int tps);
+
+// df64.cu: residuals b - (A + sigma) x in double-FP32 arithmetic
+struct DfArgs {
+  const float* links_hi = nullptr;  // GaugeCopies::u32
+  const float* links_lo = nullptr;  // GaugeCopies::u32lo
+  const float2* in_hi = nullptr;    // input vector (other parity) as (hi, lo)
+  const float2* in_lo = nullptr;
+  float2* out_hi = nullptr;         // plain: D in as (hi, lo)
+  float2* out_lo = nullptr;
+  const float2* x_hi = nullptr;     // residual: own-site x, b as (hi, lo)
+  const float2* x_lo = nullptr;
+  const float2* b_hi = nullptr;
+  const float2* b_lo = nullptr;
+  const double* a_dev = nullptr;    // 4 m^2 + sigma read from device memory, else a
+  double a = 0;
+  float2* r_out = nullptr;          // residual rounded to FP32
+  double* dot_out = nullptr;        // |r|^2
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  const int* done = nullptr;        // if non-null and *done, the kernel returns at entry
+  int out_parity = 0;
+};
+cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2* lo, const int* done, cudaStream_t st,
+                            bool pdl);
+cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, bool resid, cudaStream_t st, bool pdl);
 
 // solver.cu
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,

@@ -27,7 +27,7 @@ __device__ __forceinline__ int pack_codes(double re, double im) {
 // One thread per (site, mu): canonical complex128 [V][4][3][3] -> five internal copies.
 __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2* __restrict__ u64,
                                   float* __restrict__ u32, float4* __restrict__ u12, float4* __restrict__ u8,
-                                  char* __restrict__ u16) {
+                                  char* __restrict__ u16, float* __restrict__ u32lo) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long V = 2LL * g.vh;
   if (t >= 4 * V) return;
@@ -56,6 +56,18 @@ __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2
       f4[(size_t)q * vh + i] = make_float4(hs * (float)e[2 * q].x, hs * (float)e[2 * q].y,
                                            hs * (float)e[2 * q + 1].x, hs * (float)e[2 * q + 1].y);
     f2[i] = make_float2(hs * (float)e[8].x, hs * (float)e[8].y);
+  }
+  if (u32lo) {
+    // what the FP32 copy lost: fl32(1/2 sign u - fl32(1/2 sign u)), computed exactly in FP64
+    float* blk = u32lo + (size_t)(p * 4 + mu) * 18 * vh;
+    float4* f4 = reinterpret_cast<float4*>(blk);
+    float2* f2 = reinterpret_cast<float2*>(blk + 16 * (size_t)vh);
+    float hs = (float)half_sign;
+    auto lo = [&](double v) { return (float)(half_sign * v - (double)(hs * (float)v)); };
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      f4[(size_t)q * vh + i] = make_float4(lo(e[2 * q].x), lo(e[2 * q].y), lo(e[2 * q + 1].x), lo(e[2 * q + 1].y));
+    f2[i] = make_float2(lo(e[8].x), lo(e[8].y));
   }
   if (u12) {
     float4* blk = u12 + (size_t)(p * 4 + mu) * 3 * vh;
@@ -90,7 +102,7 @@ cudaError_t launch_pack_gauge(const Geom& g, const double2* U, GaugeCopies& gc, 
   long long n = 8LL * g.vh;  // 4 V threads
   int bs = 256;
   long long nb = (n + bs - 1) / bs;
-  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12, gc.u8, gc.u16);
+  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12, gc.u8, gc.u16, gc.u32lo);
   return cudaGetLastError();
 }
 

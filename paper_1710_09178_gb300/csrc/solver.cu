@@ -401,6 +401,9 @@ struct Workspace {
   void* pk[kMaxShifts] = {};
   double2* xk[kMaxShifts] = {};
   double2 *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr, *e64 = nullptr, *rb64 = nullptr;
+  // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
+  bool df = false;
+  float2 *dfx_h = nullptr, *dfx_l = nullptr, *dft_h = nullptr, *dft_l = nullptr, *dfb_h = nullptr, *dfb_l = nullptr;
   SolverDev* sd = nullptr;
   int* ru_count = nullptr;
   StatusWords* host_status = nullptr;  // pinned, 2 slots
@@ -430,7 +433,8 @@ void free_workspace(lqcd_ctx* ctx) {
   Workspace* w = ctx->ws;
   if (!w) return;
   for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
-  void* bufs[] = {w->r, w->p, w->q, w->tmp, w->ring, w->b64, w->r64, w->tmp64, w->e64, w->rb64, w->sd,
+  void* bufs[] = {w->dfx_h, w->dfx_l, w->dft_h, w->dft_l, w->dfb_h, w->dfb_l,
+                  w->r, w->p, w->q, w->tmp, w->ring, w->b64, w->r64, w->tmp64, w->e64, w->rb64, w->sd,
                   w->ru_count, w->partials, w->tickets};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -489,6 +493,11 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   LQ_CUDA(cudaMalloc(&w->tmp64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->e64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->rb64, w->dbytes));
+  w->df = prec != LQCD_FP64 && ctx->df_resid;
+  if (w->df) {
+    float2** dfb[] = {&w->dfx_h, &w->dfx_l, &w->dft_h, &w->dft_l, &w->dfb_h, &w->dfb_l};
+    for (float2** b : dfb) LQ_CUDA(cudaMalloc(b, 24 * (size_t)vh));
+  }
   LQ_CUDA(cudaMalloc(&w->sd, sizeof(SolverDev)));
   LQ_CUDA(cudaMemsetAsync(w->sd, 0, sizeof(SolverDev), w->st));
   LQ_CUDA(cudaMalloc(&w->ru_count, sizeof(int)));
@@ -624,6 +633,47 @@ static cudaError_t enqueue_resid64(Launcher& L, const double2* x, const double2*
   return launch_dslash(L.g, ctx->gauge, d2, w->st, &L.nlaunch);
 }
 
+// double-FP32 residual r_out = fl32(b - (A + sigma) x), |r_out|^2 into *dot (device); b is the
+// split copy of the solve's source.  Three kernels: split x, D_oe, D_eo with the residual epilogue.
+static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma, const double* a_dev, float2* r_out,
+                                    double* dot, const int* done) {
+  Workspace* w = L.w;
+  lqcd_ctx* ctx = L.ctx;
+  cudaError_t e = launch_split_df(L.g, x, w->dfx_h, w->dfx_l, done, w->st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  DfArgs d;
+  d.links_hi = ctx->gauge.u32;
+  d.links_lo = ctx->gauge.u32lo;
+  d.in_hi = w->dfx_h;
+  d.in_lo = w->dfx_l;
+  d.out_hi = w->dft_h;
+  d.out_lo = w->dft_l;
+  d.done = done;
+  d.out_parity = 1;
+  e = launch_df_dslash(L.g, d, false, w->st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  DfArgs r = d;
+  r.in_hi = w->dft_h;
+  r.in_lo = w->dft_l;
+  r.out_hi = r.out_lo = nullptr;
+  r.out_parity = 0;
+  r.x_hi = w->dfx_h;
+  r.x_lo = w->dfx_l;
+  r.b_hi = w->dfb_h;
+  r.b_lo = w->dfb_l;
+  r.a = 4.0 * ctx->mass * ctx->mass + sigma;
+  r.a_dev = a_dev;
+  r.r_out = r_out;
+  r.dot_out = dot;
+  r.partials = w->partials;
+  r.ticket = w->tickets + 3;
+  e = launch_df_dslash(L.g, r, true, w->st, L.next_pdl());
+  L.nlaunch += 1;
+  return e;
+}
+
 // iteration batch: windows x (kWindow iterations, flush, reliable update if due).  The reliable-update
 // kernels return at entry unless the beta step marked one as due (ru_skip == 0).
 static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2* b64, int n, int k0, double sigma0,
@@ -634,7 +684,15 @@ static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2*
     for (int it = 0; it < kWindow; ++it)
       if ((e = enqueue_iteration(L)) != cudaSuccess) return e;
     if ((e = enqueue_flush(L, xs, b64, n)) != cudaSuccess) return e;
-    if (use_ru) {
+    if (use_ru && w->df) {
+      // r = fl32(b - (A + sigma_0) x_0) in double-FP32 straight into the Krylov residual
+      if ((e = enqueue_resid_df(L, xs[k0], sigma0, &w->sd->a_diag, static_cast<float2*>(w->r), &w->sd->scal[0],
+                                &w->sd->ru_skip)) != cudaSuccess)
+        return e;
+      if ((e = launch_k(L.next_pdl(), ru_close_kernel, dim3(1), dim3(1), w->st, w->sd, w->ru_count)) != cudaSuccess)
+        return e;
+      L.nlaunch += 1;
+    } else if (use_ru) {
       // r64 = b - (A + sigma_0) x_0 in FP64 with FP64 links, then r <- r64 and |r|^2 <- |r64|^2
       if ((e = enqueue_resid64(L, xs[k0], b64, sigma0, &w->sd->scal[0], &w->sd->ru_skip, &w->sd->a_diag)) !=
           cudaSuccess)
@@ -811,6 +869,12 @@ static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs,
   const int n3 = 3 * L.g.vh;
   for (size_t j = 0; j < ks.size(); ++j) {
     int k = ks[j];
+    if (w->df) {
+      // straight into the refinement right-hand side (FP32), else into a scratch vector
+      float2* dst = static_cast<float2*>(keep ? keep[k] : w->q);
+      LQ_CUDA(enqueue_resid_df(L, xs[k], shifts[k], nullptr, dst, &w->sd->scal[4 + j % kMaxShifts], nullptr));
+      continue;
+    }
     LQ_CUDA(enqueue_resid64(L, xs[k], b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
     if (keep) {
       keep_residual_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->r64, keep[k], keep_f32);
@@ -837,6 +901,10 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
   LQ_CUDA(cudaEventRecord(w->ev_t0, w->st));
   LQ_CUDA(launch_pack_vector(g, w->b64, LQCD_FP64, reinterpret_cast<const double2*>(b_dev), w->st));
   ctx->launches += 1;
+  if (w->df) {
+    LQ_CUDA(launch_split_df(g, w->b64, w->dfb_h, w->dfb_l, nullptr, w->st, false));
+    ctx->launches += 1;
+  }
 
   int iters = 0, n_ru = 0, st_main = LQCD_OK;
   rc = solve_core(ctx, w->b64, w->xk, shifts, n, tol, maxiter, prec != LQCD_FP64, &iters, &n_ru, &st_main);

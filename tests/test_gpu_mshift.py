@@ -137,6 +137,49 @@ def test_no_graph_path_matches_graph_path():
         assert np.array_equal(a, c)  # deterministic reductions: identical bits
 
 
+@pytest.mark.parametrize("dims,mass,npoles", [((10, 6, 4, 6), 0.05, 12), ((16, 16, 16, 8), 0.05, 14)])
+def test_reported_true_residuals_match_oracle(dims, mass, npoles):
+    # The mixed modes compute reliable updates and true residuals in double-FP32 (~48-bit) instead
+    # of FP64.  The residual norms they report must be the oracle's FP64 residuals of the returned
+    # solutions: at convergence (b - (A + d_k) x_k cancels to 1e-10 of |b|) within 1e-12 + 0.2 %,
+    # and on an unconverged iterate within 1e-7 relative (the residual vector is rounded to FP32
+    # before its norm is taken).
+    import paper_1710_09178_gb300 as lq
+
+    ctx, U, b, c0, res, poles = _problem(dims, mass, npoles, 3, 4)
+    A = lambda v, s: staggered.A_apply(U, v, mass, dims, s)
+    for prec in (FP32, FP16FIX, FP32_L16):
+        rc, st, xs, _ = gpu_mshift(ctx, b, poles, prec=prec)
+        assert rc == 0
+        tr = solvers.true_residuals(A, b, xs, poles)
+        rep = np.array(st["true_residual"][: len(poles)])
+        assert np.all(np.abs(rep - tr) <= 1e-12 + 2e-3 * tr), (rep, tr)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    rc, st, xs, _ = gpu_mshift(ctx, b, poles, maxiter=15, prec=FP32)
+    assert rc == lq.LQCD_ERR_NOT_CONVERGED
+    tr = solvers.true_residuals(A, b, xs, poles)
+    rep = np.array(st["true_residual"][: len(poles)])
+    assert np.all(np.abs(rep - tr) <= 1e-7 * tr), (rep, tr)
+
+
+def test_double_fp32_and_fp64_residual_paths_agree():
+    # the same mixed solve with its residuals in double-FP32 and in FP64: the reliable updates
+    # round differently in the last FP32 bit, so iteration counts may differ by a step or two;
+    # solutions equal to well within the tolerance
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (16, 16, 16, 8), 0.05
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 14, 3, 4)
+    rc1, st1, xs1, _ = gpu_mshift(ctx, b, poles, prec=FP32)
+    ctx.set_option(lq.OPT_DF_RESID, 0)
+    rc2, st2, xs2, _ = gpu_mshift(ctx, b, poles, prec=FP32)
+    assert rc1 == rc2 == 0
+    assert abs(st1["iterations"] - st2["iterations"]) <= 2
+    for x1, x2, s in zip(xs1, xs2, poles):
+        kappa = (16 + 4 * mass ** 2 + s) / (4 * mass ** 2 + s)
+        assert rel_norm(x1, x2) <= kappa * 2e-10
+
+
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_programmatic_dependent_launch_matches_plain_launches(prec):
     # the same graphs captured with and without programmatic dependencies between their kernels,
