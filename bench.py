@@ -573,7 +573,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES,
                    "approximation": "x^-1/2 on [4m^2, 16+4m^2], Zolotarev (n,n)", "tol": TOL,
-                   "precision": "FP32 links+Krylov vectors, FP64 dots/x_k/reliable updates/true residuals",
+                   "precision": "FP32 links+Krylov vectors, FP64 dots and x_k, double-FP32 (FP32 hi/lo) reliable updates and true residuals, 12-real FP32 links in the refinement",
                    "gauge": "exp(i 0.5 H) SU(3), seed 5", "source": "complex Gaussian, seed 6",
                    "l2": "flushed (256 MB written, then another 256 MB read) between timed steps and before every "
                          "Dslash launch",

@@ -226,8 +226,9 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
  *   maxiter    : cap on base iterations (and on each refinement solve)
  *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12, LQCD_FP16FIX, LQCD_FP32_R8
  *                or LQCD_FP32_L16 (FP32 arithmetic with that link copy in the shifted CG,
- *                FP64 dot products, solution accumulation, reliable updates and final
- *                residuals; the refinement solves of R8 and L16 use the FP32 18-real links)
+ *                FP64 dot products and solution accumulation, reliable updates and final
+ *                residuals in double-FP32 (LQCD_OPT_DF_RESID) or FP64; the refinement solves
+ *                of all these modes use the FP32 12-real links)
  *   stats      : host lqcd_solve_stats or NULL
  * Synchronises the context stream before returning.  b = 0 gives x_k = 0, y = 0.
  */

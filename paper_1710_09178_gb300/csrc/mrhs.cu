@@ -22,7 +22,10 @@
 namespace lqcd {
 
 constexpr int kMrhsMax = kMaxShifts;
-constexpr int kMrhsGroup = 8;  // systems per link load in the multi-RHS Dslash
+// systems per link load in the multi-RHS Dslash: 4 accumulators per thread keep the kernel at
+// 8 resident blocks per SM; on GB300 that beats more link reuse (16 systems: +40 % solve time,
+// 8: +9 %, 2: +4 %, 1: +15 % at 32^3 x 8), the links being L2-resident anyway
+constexpr int kMrhsGroup = 4;
 
 struct MrhsDev {
   int m;
@@ -32,6 +35,7 @@ struct MrhsDev {
   int passes, max_passes;
   unsigned ticket[4];
   double a[kMrhsMax];  // 4 m^2 + sigma_j
+  float af[kMrhsMax];  // the same in FP32 (no FP64 conversion inside the FP32 kernels)
   double rr[kMrhsMax], stop2[kMrhsMax], alpha[kMrhsMax], beta[kMrhsMax];
 };
 
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
       T d = 0;
       if (i < vh) {
         const int sj = sys[q];
-        const T a = (T)md->a[sj];
+        const T a = sizeof(T) == 4 ? (T)md->af[sj] : (T)md->a[sj];
         Vec3<T> pv = load_vec(static_cast<const V2*>(vv.p[sj]), i, vh);
         Vec3<T> qv;
 #pragma unroll
@@ -324,6 +328,7 @@ __global__ void __launch_bounds__(128) mrhs_init_kernel(Geom g, MrhsVecs vv, Mrh
       md->rr[sj] = v;
       md->stop2[sj] = in.rel2[sj] * v;
       md->a[sj] = in.a[sj];
+      md->af[sj] = (float)in.a[sj];
       md->alpha[sj] = md->beta[sj] = 0.0;
     }
   }
@@ -420,8 +425,9 @@ template <typename T>
 static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, const Geom& g, int prec, int groups,
                                           cudaStream_t st, int* nl, bool pdl, bool* chained) {
   dim3 grid(mw->nbx, groups);
-  const void* links = prec == LQCD_FP64 ? (const void*)ctx->gauge.u64
-                      : prec == LQCD_FP32_R12 ? (const void*)ctx->gauge.u12 : (const void*)ctx->gauge.u32;
+  // FP32 arithmetic reads the 12-real copy: the kernel is bound by its link loads, and row 3
+  // rebuilt in FP32 is as accurate as the stored FP32 row
+  const void* links = prec == LQCD_FP64 ? (const void*)ctx->gauge.u64 : (const void*)ctx->gauge.u12;
   auto next = [&]() {
     bool r = pdl && *chained;
     *chained = true;
@@ -433,14 +439,10 @@ static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, cons
     e = launch_k(p1, mrhs_dslash_kernel<0, double, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
     if (e == cudaSuccess)
       e = launch_k(p2, mrhs_dslash_kernel<0, double, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
-  } else if (prec == LQCD_FP32_R12) {
+  } else {
     e = launch_k(p1, mrhs_dslash_kernel<2, float, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
     if (e == cudaSuccess)
       e = launch_k(p2, mrhs_dslash_kernel<2, float, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
-  } else {
-    e = launch_k(p1, mrhs_dslash_kernel<1, float, false>, grid, dim3(128), st, g, links, mw->vv, 1, mw->md, mw->partials);
-    if (e == cudaSuccess)
-      e = launch_k(p2, mrhs_dslash_kernel<1, float, true>, grid, dim3(128), st, g, links, mw->vv, 0, mw->md, mw->partials);
   }
   if (e == cudaSuccess) e = launch_k(p3, mrhs_update_kernel<T>, grid, dim3(128), st, g, mw->vv, mw->md, mw->partials);
   dim3 grid3((3 * g.vh + 255) / 256, groups);
