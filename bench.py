@@ -151,6 +151,15 @@ class L2Flusher:
         self.sink.add_(self.r.sum())
 
 
+def solve_algorithmic_bytes(st, vh, fp64):
+    """Minimum traffic of the plain shifted CG's base iterations (every vector and link crossing HBM
+    once): per iteration and site the A-apply (two half-Dslash + the own-site read), the r and p
+    updates, and per active shift the p_k and x_k read-modify-writes."""
+    per_iter = (2 * 1248 + 48 + 144 + 144) if fp64 else (2 * 624 + 24 + 72 + 72)
+    per_shift = (96 + 96) if fp64 else (48 + 96)
+    return vh * (st["iterations"] * per_iter + st.get("shift_iterations", 0) * per_shift)
+
+
 def setup_problem(lq, torch):
     from paper_1710_09178_gb300 import inputs
 
@@ -501,6 +510,8 @@ def main():
                            ("fp32_r8", lq.FP32_R8), ("fp32_l16", lq.FP32_L16)):
             tms, sts = time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
             extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
+                           "algorithmic_GBps": solve_algorithmic_bytes(sts[-1], int(np.prod(DIMS)) // 2,
+                                                                       prec == lq.FP64) / (statistics.mean(tms) * 1e6),
                            "reliable_updates": sts[-1]["reliable_updates"],
                            "refine_iterations": sts[-1]["refine_iterations"],
                            "max_true_residual": max(sts[-1]["true_residual"])}
@@ -578,7 +589,11 @@ def main():
                    "l2": "flushed (256 MB written, then another 256 MB read) between timed steps and before every "
                          "Dslash launch",
                    "parallelism": f"replicas x{world}"},
-        "mixed": {"iterations": last["iterations"], "reliable_updates": last["reliable_updates"],
+        "mixed": {"iterations": last["iterations"], "shift_iterations": last["shift_iterations"],
+                  "algorithmic_GBps": solve_algorithmic_bytes(last, int(np.prod(DIMS)) // 2, False) / (ms_per_solve * 1e6),
+                  "algorithmic_bytes_note": "plain shifted CG base iterations (A-apply, r/p updates, active-shift "
+                                            "p_k/x_k updates) / whole solve time incl. checks and refinement",
+                  "reliable_updates": last["reliable_updates"],
                   "refine_iterations": last["refine_iterations"], "refined_shifts": last["refined_shifts"],
                   "max_true_residual": max(last["true_residual"]), "ms_per_solve_all": times},
         "fp64_vs_mixed": (extra["fp64"]["ms_per_solve"] / ms_per_solve) if "fp64" in extra else None,

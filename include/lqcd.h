@@ -74,6 +74,7 @@ typedef struct {
   int n_shifts;
   double true_residual[LQCD_MAX_SHIFTS]; /* |b - (A + d_k) x_k| / |b| in FP64, per shift */
   double ms;              /* wall time of the call on its stream (CUDA events) */
+  int shift_iterations;   /* sum over base iterations of the shifts still iterating */
 } lqcd_solve_stats;
 
 /*

@@ -69,7 +69,8 @@ def multishift_cg(apply_base, b, shifts, tol=1e-10, maxiter=20000, fixed_iters=N
     loop runs exactly that many iterations with no shift frozen (used to compare
     implementations iteration for iteration).  Returns (xs, info) with xs a list
     of solutions in the order of `shifts` and info a dict holding 'iterations',
-    'zeta' (final per-shift zeta) and 'rr' (final |r|^2).
+    'zeta' (final per-shift zeta), 'rr' (final |r|^2) and 'shift_iterations' (the
+    number of (iteration, shift) pairs in which the shift was still updated).
     """
     shifts = np.asarray(shifts, dtype=np.float64)
     n = shifts.size
@@ -78,7 +79,7 @@ def multishift_cg(apply_base, b, shifts, tol=1e-10, maxiter=20000, fixed_iters=N
     xs = [np.zeros_like(b) for _ in range(n)]
     bb = norm2(b)
     if bb == 0.0:
-        return xs, dict(iterations=0, zeta=np.ones(n), rr=0.0)
+        return xs, dict(iterations=0, zeta=np.ones(n), rr=0.0, shift_iterations=0)
     r = b.copy()
     p = b.copy()
     ps = [b.copy() for _ in range(n)]
@@ -88,12 +89,14 @@ def multishift_cg(apply_base, b, shifts, tol=1e-10, maxiter=20000, fixed_iters=N
     alpha_prev, beta_prev = 1.0, 0.0
     rr = bb
     it = 0
+    shift_iterations = 0
     while True:
         if fixed_iters is not None:
             if it >= fixed_iters:
                 break
         elif not active.any() or it >= maxiter:
             break
+        shift_iterations += int(active.sum())
         q = apply_base(p)
         alpha = rr / float(np.real(vdot(p, q)))
         zeta_new = zeta.copy()  # a stopped shift keeps its last zeta
@@ -121,7 +124,7 @@ def multishift_cg(apply_base, b, shifts, tol=1e-10, maxiter=20000, fixed_iters=N
             for k in range(n):
                 if active[k] and abs(zeta[k]) * np.sqrt(rr) <= tol * np.sqrt(bb):
                     active[k] = False
-    return xs, dict(iterations=it, zeta=zeta.copy(), rr=rr)
+    return xs, dict(iterations=it, zeta=zeta.copy(), rr=rr, shift_iterations=shift_iterations)
 
 
 def true_residuals(apply_shifted, b, xs, shifts):

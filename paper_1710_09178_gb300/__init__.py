@@ -68,6 +68,7 @@ class SolveStats(ctypes.Structure):
         ("n_shifts", ctypes.c_int),
         ("true_residual", ctypes.c_double * MAX_SHIFTS),
         ("ms", ctypes.c_double),
+        ("shift_iterations", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -75,7 +76,8 @@ class SolveStats(ctypes.Structure):
         return dict(iterations=self.iterations, reliable_updates=self.reliable_updates,
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
                     refine_rounds=self.refine_rounds,
-                    kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms)
+                    kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms,
+                    shift_iterations=self.shift_iterations)
 
 
 class BatchProblem(ctypes.Structure):

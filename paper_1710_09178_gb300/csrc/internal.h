@@ -44,6 +44,7 @@ struct SolverDev {
   int ru_skip;
   double ru_delta2;
   double rr_ru_max;
+  int shift_iters;  // sum over iterations of the active shifts (statistics)
   int windows_run;  // windows executed by the graph loop (bounded by max_windows whatever the flags say)
   int max_windows;
   unsigned ticket[4];

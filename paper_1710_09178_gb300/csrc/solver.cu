@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(256) init_kernel(Geom g, const double2* __rest
       sd->ru_delta2 = ip.ru_delta * ip.ru_delta;
       sd->rr_ru_max = bb;
       sd->windows_run = 0;
+      sd->shift_iters = 0;
       sd->max_windows = ip.maxiter / kWindow + 2;
       sd->n_active = trivial ? 0 : ip.n;
       sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
@@ -407,6 +408,7 @@ struct Workspace {
   SolverDev* sd = nullptr;
   int* ru_count = nullptr;
   StatusWords* host_status = nullptr;  // pinned, 2 slots
+  int shift_iters_host = 0;
   double* host_scal = nullptr;         // pinned
   double* partials = nullptr;
   unsigned* tickets = nullptr;
@@ -823,6 +825,7 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   LQ_CUDA(cudaMemcpyAsync(&w->host_status[0], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
   int ru_host = 0;
   LQ_CUDA(cudaMemcpyAsync(&ru_host, w->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+  LQ_CUDA(cudaMemcpyAsync(&w->shift_iters_host, &w->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
   StatusWords last = w->host_status[0];
   ctx->launches += L.nlaunch;
@@ -998,6 +1001,7 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
     stats->refine_rounds = rounds_done;
     stats->kernel_launches = (int)(ctx->launches - launches0);
     stats->n_shifts = n;
+    stats->shift_iterations = w->shift_iters_host;
     for (int k = 0; k < n; ++k) stats->true_residual[k] = tres[k];
     stats->ms = ms;
   }

@@ -122,8 +122,10 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
   }
   // count shifts still active (warp 0 holds all of them, n <= 32)
   const unsigned bal = __ballot_sync(0xffffffffu, still);
+  const unsigned bal_it = __ballot_sync(0xffffffffu, act != 0);
   if (k == 0) {
     const int n_active = __popc(bal);
+    sd->shift_iters += __popc(bal_it);
     const int it = iter + 1;
     const int done = (n_active == 0 || it >= maxiter) ? 1 : 0;
     sd->beta = beta;

@@ -211,6 +211,7 @@ def test_fp64_unrefined_solve_matches_oracle_with_same_stopping_rule(dims, mass,
     oxs, info = solvers.multishift_cg(lambda v: staggered.A_apply(U, v, mass, dims, poles.min()), b, poles,
                                       tol=1e-10)
     assert st["iterations"] == info["iterations"]
+    assert st["shift_iterations"] == info["shift_iterations"]  # every shift stopped in the same iteration
     for x, ox in zip(xs, oxs):
         assert rel_norm(x, ox) < 1e-9
     otr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, oxs, poles)

@@ -72,3 +72,22 @@ def test_rational_apply_matches_dense_matrix_function():
     w, Q = np.linalg.eigh(A)
     exact = Q @ ((w ** -0.5) * (Q.conj().T @ b.reshape(-1)))
     assert np.linalg.norm(y.reshape(-1) - exact) <= 1.5 * err * np.linalg.norm(exact) + 1e-11
+
+
+def test_shift_iteration_count():
+    # with no shift frozen every (iteration, shift) pair counts; with the stopping rule the count is
+    # the sum of each shift's own stopping iteration, which independent single-shift CG runs give
+    dims, mass = (4, 4, 4, 4), 0.1
+    U = inputs.gauge_field(dims, seed=7)
+    b = inputs.gaussian_vector(dims, 8)
+    shifts = np.array([0.0, 0.05, 0.4, 3.0])
+    base = lambda v: staggered.A_apply(U, v, mass, dims, shifts.min())
+    _, info = solvers.multishift_cg(base, b, shifts, fixed_iters=9)
+    assert info["shift_iterations"] == 9 * shifts.size
+    _, info = solvers.multishift_cg(base, b, shifts, tol=1e-10)
+    assert info["shift_iterations"] < shifts.size * info["iterations"]
+    stops = []
+    for sg in shifts:
+        _, it = solvers.cg(lambda v: staggered.A_apply(U, v, mass, dims, sg), b, tol=1e-10)
+        stops.append(it)
+    assert abs(info["shift_iterations"] - sum(stops)) <= shifts.size  # rounding may move a stop by one
