@@ -58,6 +58,8 @@ extern "C" {
 #define LQCD_FP16FIX 3  /* FP32 links; shifted Krylov vectors in 16-bit fixed point + per-site scale */
 #define LQCD_FP32_R8 4  /* FP32 8-real links (a2, a3, b1, arg a1, arg c1; the rest rebuilt), FP32 vectors */
 #define LQCD_FP32_L16 5 /* 16-bit fixed-point links (rows 0-1, q = rint(32767 u); row 2 rebuilt), FP32 vectors */
+#define LQCD_DF64 6     /* double-FP32: links, vectors and arithmetic as FP32 (hi, lo) pairs (~48 bits, FP32 units
+                           only; exact FMA products, TwoSum sums): FP64-class results without FP64 instructions */
 
 #define LQCD_MAX_SHIFTS 32
 
@@ -121,6 +123,8 @@ int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src);
 /*
  * lqcd_vector_bytes - bytes of one internal half-lattice vector of precision prec:
  *   LQCD_FP64                : 48*Vh, [3 colours][Vh] double2 (re, im)
+ *   LQCD_DF64                : 48*Vh, [3 colours][Vh] float2 hi, then [3 colours][Vh] float2 lo;
+ *                              component = hi + lo (hi = fl32(u), lo = fl32(u - hi) on packing)
  *   LQCD_FP32, LQCD_FP32_R12,
  *   LQCD_FP32_R8, LQCD_FP32_L16 : 24*Vh, [3 colours][Vh] float2
  *   LQCD_FP16FIX             : 16*Vh, [Vh] x 16 bytes: six int16 codes q_i then a
@@ -144,8 +148,9 @@ int lqcd_unpack_vector(lqcd_ctx* ctx, double* dst_dev, const void* src_dev, int 
  * dslash_eo - half-lattice hopping operator (Section 3.2; Fig. evenodd).
  *   out_parity = 1: out = D_oe in  (in on even sites, out on odd sites)
  *   out_parity = 0: out = D_eo in  (in on odd sites, out on even sites)
- *   prec       : LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8 or LQCD_FP32_L16 (which
- *                link copy is used); in_dev and out_dev are internal vectors of that precision
+ *   prec       : LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8, LQCD_FP32_L16 or LQCD_DF64
+ *                (which link copy is used; LQCD_DF64 reads the FP32 copy and its rounding errors);
+ *                in_dev and out_dev are internal vectors of that precision
  *                (lqcd_vector_bytes(ctx, prec) bytes each, must not overlap).
  * Requires a gauge field (LQCD_ERR_STATE otherwise).  Asynchronous.
  */
@@ -153,7 +158,7 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
 
 /*
  * lqcd_apply_A - q = (A + sigma) p on even sites, A = 4 m^2 - D_eo D_oe (Section 3.2),
- * internal vectors of precision prec (FP64, FP32, FP32_R12, FP32_R8 or FP32_L16).  If pq_host is not
+ * internal vectors of precision prec (FP64, FP32, FP32_R12, FP32_R8, FP32_L16 or DF64).  If pq_host is not
  * NULL the call synchronises and stores Re<p, q> (FP64 accumulation) there.
  */
 int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
@@ -229,7 +234,9 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
  *                or LQCD_FP32_L16 (FP32 arithmetic with that link copy in the shifted CG,
  *                FP64 dot products and solution accumulation, reliable updates and final
  *                residuals in double-FP32 (LQCD_OPT_DF_RESID) or FP64; the refinement solves
- *                of all these modes use the FP32 12-real links)
+ *                of all these modes use the FP32 12-real links), or LQCD_DF64 (every vector,
+ *                the solutions and the arithmetic in double-FP32: no reliable updates, and the
+ *                final check normally leaves nothing to refine)
  *   stats      : host lqcd_solve_stats or NULL
  * Synchronises the context stream before returning.  b = 0 gives x_k = 0, y = 0.
  */

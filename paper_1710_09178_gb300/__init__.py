@@ -34,8 +34,9 @@ FP32_R12 = 2
 FP16FIX = 3
 FP32_R8 = 4
 FP32_L16 = 5
+DF64 = 6
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_r12": FP32_R12, "fp16fix": FP16FIX, "fp32_r8": FP32_R8,
-              "fp32_l16": FP32_L16}
+              "fp32_l16": FP32_L16, "df64": DF64}
 
 OPT_RELIABLE_INTERVAL = 1
 OPT_REFINE = 2

@@ -36,7 +36,7 @@ int cuda_check(lqcd_ctx* ctx, cudaError_t e, const char* what) {
 }
 
 static bool prec_valid(int prec) {
-  return prec == LQCD_FP64 || vec_fp32(prec) || prec == LQCD_FP16FIX;
+  return prec == LQCD_FP64 || vec_fp32(prec) || prec == LQCD_FP16FIX || prec == LQCD_DF64;
 }
 
 static int ensure_scratch(lqcd_ctx* ctx) {
@@ -154,7 +154,8 @@ int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
 size_t lqcd_vector_bytes(const lqcd_ctx* ctx, int prec) {
   if (!ctx) return 0;
   switch (prec) {
-    case LQCD_FP64: return 48 * (size_t)ctx->Vh;
+    case LQCD_FP64:
+    case LQCD_DF64: return 48 * (size_t)ctx->Vh;
     case LQCD_FP32:
     case LQCD_FP32_R12:
     case LQCD_FP32_R8:
@@ -188,6 +189,19 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
     return fail(ctx, LQCD_ERR_ARG, "dslash_eo: bad argument");
   if (out_dev == in_dev) return fail(ctx, LQCD_ERR_ARG, "dslash_eo: output must not alias the input");
   if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "dslash_eo: no gauge field loaded");
+  if (prec == LQCD_DF64) {
+    const size_t n3 = 3 * (size_t)ctx->Vh;
+    DfArgs d;
+    d.links_hi = ctx->gauge.u32;
+    d.links_lo = ctx->gauge.u32lo;
+    d.in_hi = static_cast<const float2*>(in_dev);
+    d.in_lo = static_cast<const float2*>(in_dev) + n3;
+    d.out_hi = static_cast<float2*>(out_dev);
+    d.out_lo = static_cast<float2*>(out_dev) + n3;
+    d.out_parity = out_parity;
+    ctx->launches += 1;
+    return cuda_check(ctx, launch_df_dslash(make_geom(ctx), d, 0, ctx->stream, false), "dslash_eo");
+  }
   DslashArgs a;
   a.out = out_dev;
   a.in = in_dev;
@@ -208,6 +222,41 @@ int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, in
   int rc = ensure_scratch(ctx);
   if (rc != LQCD_OK) return rc;
   Geom g = make_geom(ctx);
+  if (prec == LQCD_DF64) {
+    const size_t n3 = 3 * (size_t)ctx->Vh;
+    float2* t = static_cast<float2*>(ctx->tmp_odd);
+    DfArgs d;
+    d.links_hi = ctx->gauge.u32;
+    d.links_lo = ctx->gauge.u32lo;
+    d.in_hi = static_cast<const float2*>(p_dev);
+    d.in_lo = static_cast<const float2*>(p_dev) + n3;
+    d.out_hi = t;
+    d.out_lo = t + n3;
+    d.out_parity = 1;
+    cudaError_t e = launch_df_dslash(g, d, 0, ctx->stream, false);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A");
+    DfArgs q = d;
+    q.in_hi = t;
+    q.in_lo = t + n3;
+    q.out_hi = static_cast<float2*>(q_dev);
+    q.out_lo = static_cast<float2*>(q_dev) + n3;
+    q.x_hi = static_cast<const float2*>(p_dev);
+    q.x_lo = static_cast<const float2*>(p_dev) + n3;
+    q.a = 4.0 * ctx->mass * ctx->mass + sigma;
+    q.dot_out = ctx->scalars;
+    q.partials = ctx->partials;
+    q.ticket = ctx->tickets;
+    q.out_parity = 0;
+    e = launch_df_dslash(g, q, 1, ctx->stream, false);
+    ctx->launches += 2;
+    if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A");
+    if (pq_host) {
+      e = cudaMemcpyAsync(pq_host, ctx->scalars, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A readback");
+    }
+    return LQCD_OK;
+  }
   DslashArgs a;
   a.out = ctx->tmp_odd;
   a.in = p_dev;

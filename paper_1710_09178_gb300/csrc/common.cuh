@@ -364,6 +364,19 @@ __device__ __forceinline__ double2 ld_hint(const double2* p, uint64_t pol) {
   return r;
 }
 
+__device__ __forceinline__ float2 ld_hint(const float2* p, uint64_t pol) {
+  float2 r;
+  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(r.x), "=f"(r.y)
+               : "l"(p), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ void st_hint(float2* p, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void st_hint(double2* p, double2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
                : "memory");

@@ -15,8 +15,15 @@
 // The links are the FP32 copy (hi, 1/2 eta bc folded in) plus a copy of the FP32 rounding
 // errors (lo); vectors are split from FP64 once per residual.  The result is rounded to FP32
 // (the reliable update and the refinement both continue in FP32) and |r|^2 is summed in FP64.
+//
+// The same arithmetic also carries a whole shifted-CG solve (precision mode LQCD_DF64): Krylov
+// vectors, shift vectors, the residual window and the solutions x_k are (hi, lo) pairs, stored as
+// [3][Vh] float2 hi followed by [3][Vh] float2 lo (48 bytes per site, as FP64).  The iterated and
+// true residuals then agree to ~2^-48, so the solve needs neither reliable updates nor per-shift
+// refinement, at FP32-unit cost.
 #include "common.cuh"
 #include "internal.h"
+#include "solver_dev.cuh"
 
 namespace lqcd {
 
@@ -49,6 +56,24 @@ __device__ __forceinline__ float2 df_norm(float s, float c) {
   return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
 }
 
+// Sum over the block of per-thread double-FP32 values (s, c): TwoSum shuffles within each warp,
+// then the warps' FP64 values in a fixed order.  Result valid in every thread.
+__device__ __forceinline__ double block_sum_df(float s, float c) {
+  __shared__ double red_df[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    df_add(s, c, s2, c2);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) red_df[warp] = (double)s + (double)c;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red_df[w];
+  __syncthreads();
+  return t;
+}
+
 // x (FP64) -> (hi, lo) FP32 pairs
 __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __restrict__ x, float2* __restrict__ hi,
                                                         float2* __restrict__ lo, const int* done) {
@@ -63,7 +88,9 @@ __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __
   lo[i] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
 }
 
-// EPI 0: out = D in (hi, lo);  EPI 2: r_out = fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
+// EPI 0: out = D in (hi, lo);  EPI 1: out = a x - D in and Re<x, out> (the A-apply of the
+// solve, whose last block runs the alpha step when solver is set);  EPI 2: r_out =
+// fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
 template <int EPI>
 __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
   const int vh = g.vh;
@@ -122,6 +149,34 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
         k.out_lo[(size_t)a * vh + i] = make_float2(re.y, im.y);
       }
     }
+  } else if constexpr (EPI == 1) {
+    // q = a x - D in (x = the own-site vector, p of the solve), Re<x, q> in double-FP32
+    float ds = 0.f, dc = 0.f;
+    if (valid) {
+      const double a64 = k.a_dev ? *k.a_dev : k.a;
+      const float ah = __double2float_rn(a64), al = __double2float_rn(a64 - (double)ah);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const size_t o = (size_t)a * vh + i;
+        const float2 xh = k.x_hi[o], xl = k.x_lo[o];
+        float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+        df_mac(rs, rc, ah, al, xh.x, xl.x);
+        df_mac(is, ic, ah, al, xh.y, xl.y);
+        df_add(rs, rc, -sr[a], -cr[a]);
+        df_add(is, ic, -si[a], -ci[a]);
+        const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+        k.out_hi[o] = make_float2(re.x, im.x);
+        k.out_lo[o] = make_float2(re.y, im.y);
+        df_mac(ds, dc, xh.x, xl.x, re.x, re.y);
+        df_mac(ds, dc, xh.y, xl.y, im.x, im.y);
+      }
+    }
+    const double bs = block_sum_df(ds, dc);
+    if (publish_partial(k.partials, k.ticket, bs)) {
+      const double tot = gather_partials(k.partials, k.ticket);
+      if (k.solver) solver_alpha_step(k.solver, tot);
+      else if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
+    }
   } else {
     float dsite = 0.f;
     if (valid) {
@@ -156,10 +211,230 @@ cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2*
   return launch_k(pdl, split_df_kernel, dim3((n3 + 255) / 256), dim3(256), st, n3, x, hi, lo, done);
 }
 
-cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, bool resid, cudaStream_t st, bool pdl) {
+cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl) {
   const unsigned nb = (unsigned)((g.vh + 127) / 128);
-  if (resid) return launch_k(pdl, df_dslash_kernel<2>, dim3(nb), dim3(128), st, g, a);
+  if (epi == 2) return launch_k(pdl, df_dslash_kernel<2>, dim3(nb), dim3(128), st, g, a);
+  if (epi == 1) return launch_k(pdl, df_dslash_kernel<1>, dim3(nb), dim3(128), st, g, a);
   return launch_k(pdl, df_dslash_kernel<0>, dim3(nb), dim3(128), st, g, a);
+}
+
+// ---------------------------------------------------------------------------------------------
+// The double-FP32 shifted CG (mode LQCD_DF64): the same steps as the FP32/FP64 kernels of the
+// solver, on (hi, lo) vectors.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 split64(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+
+// r = p = b as (hi, lo), |b|^2 in FP64, then the scalar state of a fresh solve
+__global__ void __launch_bounds__(256) df_init_kernel(Geom g, const double2* __restrict__ b64, float2* r, float2* p,
+                                                      SolverDev* sd, InitParams ip, double* partials,
+                                                      unsigned* ticket) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int vh = g.vh;
+  double loc = 0.0;
+  if (i < vh) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * vh + i;
+      const double2 b = b64[o];
+      const float2 re = split64(b.x), im = split64(b.y);
+      const float2 h = make_float2(re.x, im.x), l = make_float2(re.y, im.y);
+      r[o] = h;
+      r[o + 3 * (size_t)vh] = l;
+      p[o] = h;
+      p[o + 3 * (size_t)vh] = l;
+      loc += b.x * b.x + b.y * b.y;
+    }
+  }
+  const double bs = block_sum(loc);
+  if (publish_partial(partials, ticket, bs)) init_scalars(sd, ip, gather_partials(partials, ticket));
+}
+
+// r -= alpha q; R[m] = r; |r|^2 (double-FP32 per warp, FP64 across warps) -> beta step
+__global__ void __launch_bounds__(256) df_r_update_kernel(Geom g, DfUpdArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  SolverDev* sd = a.sd;
+  if (sd->done) return;
+  const int m = sd->m;
+  const int vh = g.vh;
+  const float2 al = split64(sd->alpha);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float ls = 0.f, lc = 0.f;
+  if (i < vh && m < kWindow) {
+    float2* slot = reinterpret_cast<float2*>(static_cast<char*>(a.ring) + m * a.slot_bytes);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
+      const float2 rh = a.r[o], rl = a.r[ol], qh = a.q[o], ql = a.q[ol];
+      float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
+      df_mac(rs, rc, -al.x, -al.y, qh.x, ql.x);
+      df_mac(is, ic, -al.x, -al.y, qh.y, ql.y);
+      const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+      const float2 h = make_float2(re.x, im.x), l = make_float2(re.y, im.y);
+      a.r[o] = h;
+      a.r[ol] = l;
+      slot[o] = h;
+      slot[ol] = l;
+      df_mac(ls, lc, h.x, l.x, h.x, l.x);
+      df_mac(ls, lc, h.y, l.y, h.y, l.y);
+    }
+  }
+  const double bs = block_sum_df(ls, lc);
+  if (publish_partial(a.partials, a.ticket, bs)) solver_beta_step(sd, gather_partials(a.partials, a.ticket));
+}
+
+// p = r + beta p, one thread per complex component
+__global__ void __launch_bounds__(256) df_p_update_kernel(Geom g, const float2* r, float2* p, const SolverDev* sd) {
+  pdl_wait();
+  pdl_trigger();
+  if (sd->done) return;
+  const int n3 = 3 * g.vh;
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n3) return;
+  const float2 be = split64(sd->beta);
+  const float2 rh = r[o], rl = r[o + n3], ph = p[o], pl = p[o + n3];
+  float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
+  df_mac(rs, rc, be.x, be.y, ph.x, pl.x);
+  df_mac(is, ic, be.x, be.y, ph.y, pl.y);
+  const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+  p[o] = make_float2(re.x, im.x);
+  p[o + n3] = make_float2(re.y, im.y);
+}
+
+// The pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i, all in
+// double-FP32 (the window coefficients split from FP64 once per block).  One colour at a time
+// keeps the window's residuals (2 x kWindow float2 pairs) in registers.
+__global__ void __launch_bounds__(128) df_flush_kernel(Geom g, DfFlushArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  SolverDev* sd = a.sd;
+  const int m = sd->m;
+  if (m == 0) return;
+  __shared__ float2 cP[kMaxShifts], cX[kMaxShifts], cpi[kMaxShifts][kWindow], cchi[kMaxShifts][kWindow];
+  __shared__ int act[kMaxShifts];
+  const int n = sd->n;
+  const int first = sd->first;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    cP[t] = split64(sd->P[t]);
+    cX[t] = split64(sd->X[t]);
+    act[t] = sd->wactive[t];
+    for (int q = 0; q < kWindow; ++q) {
+      cpi[t][q] = (q < m) ? split64(sd->pi[t][q]) : make_float2(0.f, 0.f);
+      cchi[t][q] = (q < m) ? split64(sd->chi[t][q]) : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  const int vh = g.vh;
+  const size_t n3 = 3 * (size_t)vh;
+  const uint64_t pol = policy_evict_first();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < vh) {
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * vh + i;
+      float2 Rh[kWindow], Rl[kWindow];
+#pragma unroll
+      for (int q = 0; q < kWindow; ++q) {
+        const float2* slot = reinterpret_cast<const float2*>(static_cast<const char*>(a.ring) + q * a.slot_bytes);
+        Rh[q] = (q < m) ? slot[o] : make_float2(0.f, 0.f);
+        Rl[q] = (q < m) ? slot[o + n3] : make_float2(0.f, 0.f);
+      }
+      float2 bh = make_float2(0.f, 0.f), bl = bh;
+      if (first) {
+        bh = a.b_hi[o];
+        bl = a.b_lo[o];
+      }
+      for (int k = 0; k < n; ++k) {
+        if (!act[k]) continue;
+        float2* pk = a.pk[k];
+        float2* xk = a.xk[k];
+        const float2 p0h = first ? bh : pk[o], p0l = first ? bl : pk[o + n3];
+        // new p_k and the increment of x_k, real and imaginary parts
+        float ps = 0.f, pc = 0.f, qs = 0.f, qc = 0.f, xs = 0.f, xc = 0.f, ys = 0.f, yc = 0.f;
+        df_mac(ps, pc, cP[k].x, cP[k].y, p0h.x, p0l.x);
+        df_mac(qs, qc, cP[k].x, cP[k].y, p0h.y, p0l.y);
+        df_mac(xs, xc, cX[k].x, cX[k].y, p0h.x, p0l.x);
+        df_mac(ys, yc, cX[k].x, cX[k].y, p0h.y, p0l.y);
+#pragma unroll
+        for (int q = 0; q < kWindow; ++q) {
+          if (q >= m) break;
+          const float2 pq = cpi[k][q], cq = cchi[k][q];
+          df_mac(ps, pc, pq.x, pq.y, Rh[q].x, Rl[q].x);
+          df_mac(qs, qc, pq.x, pq.y, Rh[q].y, Rl[q].y);
+          df_mac(xs, xc, cq.x, cq.y, Rh[q].x, Rl[q].x);
+          df_mac(ys, yc, cq.x, cq.y, Rh[q].y, Rl[q].y);
+        }
+        const float2 pre = df_norm(ps, pc), pim = df_norm(qs, qc);
+        pk[o] = make_float2(pre.x, pim.x);
+        pk[o + n3] = make_float2(pre.y, pim.y);
+        // x_k is touched once per window: stream it through L2 without displacing the links
+        float xrs = 0.f, xrc = 0.f, xis = 0.f, xic = 0.f;
+        if (!first) {
+          const float2 xh = ld_hint(xk + o, pol), xl = ld_hint(xk + o + n3, pol);
+          xrs = xh.x;
+          xrc = xl.x;
+          xis = xh.y;
+          xic = xl.y;
+        }
+        df_add(xrs, xrc, xs, xc);
+        df_add(xis, xic, ys, yc);
+        const float2 xre = df_norm(xrs, xrc), xim = df_norm(xis, xic);
+        st_hint(xk + o, make_float2(xre.x, xim.x), pol);
+        st_hint(xk + o + n3, make_float2(xre.y, xim.y), pol);
+      }
+    }
+  }
+  if (publish_partial(a.partials, a.ticket, 0.0)) {
+    __threadfence();
+    const int t = threadIdx.x;
+    if (t == 0) *a.ticket = 0u;
+    if (t < n) {
+      sd->P[t] = 1.0;
+      sd->X[t] = 0.0;
+      sd->wactive[t] = sd->active[t];
+    }
+    if (t == 0) {
+      sd->m = 0;
+      sd->first = 0;
+    }
+  }
+}
+
+// (hi, lo) vectors -> FP64 (x = hi + lo, exact), one thread per complex component
+__global__ void __launch_bounds__(256) df_to_fp64_kernel(int n3, const float2* __restrict__ v, double2* __restrict__ x) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n3) return;
+  const float2 h = v[o], l = v[o + n3];
+  x[o] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+}
+
+cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, SolverDev* sd, const InitParams& ip,
+                           double* partials, unsigned* ticket, cudaStream_t st) {
+  df_init_kernel<<<(g.vh + 255) / 256, 256, 0, st>>>(g, b64, static_cast<float2*>(r), static_cast<float2*>(p), sd, ip,
+                                                     partials, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_r_update_kernel, dim3((g.vh + 255) / 256), dim3(256), st, g, a);
+}
+
+cudaError_t launch_df_p_update(const Geom& g, const void* r, void* p, const SolverDev* sd, cudaStream_t st, bool pdl) {
+  const int n3 = 3 * g.vh;
+  return launch_k(pdl, df_p_update_kernel, dim3((n3 + 255) / 256), dim3(256), st, g, static_cast<const float2*>(r),
+                  static_cast<float2*>(p), sd);
+}
+
+cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_flush_kernel, dim3((g.vh + 127) / 128), dim3(128), st, g, a);
+}
+
+cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st) {
+  const int n3 = 3 * g.vh;
+  df_to_fp64_kernel<<<(n3 + 255) / 256, 256, 0, st>>>(n3, static_cast<const float2*>(v), x);
+  return cudaGetLastError();
 }
 
 }  // namespace lqcd

@@ -156,11 +156,41 @@ struct DfArgs {
   double* partials = nullptr;
   unsigned* ticket = nullptr;
   const int* done = nullptr;        // if non-null and *done, the kernel returns at entry
+  SolverDev* solver = nullptr;      // A-apply inside a solve: the last block runs the alpha step
   int out_parity = 0;
 };
+// double-FP32 vectors of the LQCD_DF64 solve: [3][Vh] float2 hi, then [3][Vh] float2 lo
+struct DfUpdArgs {
+  float2* r;
+  const float2* q;
+  void* ring;  // kWindow slots, slot stride in bytes
+  size_t slot_bytes;
+  SolverDev* sd;
+  double* partials;
+  unsigned* ticket;
+};
+struct DfFlushArgs {
+  const void* ring;
+  size_t slot_bytes;
+  float2* pk[kMaxShifts];
+  float2* xk[kMaxShifts];
+  const float2* b_hi;  // the source as (hi, lo): p_k0 of the first window
+  const float2* b_lo;
+  SolverDev* sd;
+  double* partials;
+  unsigned* ticket;
+};
+struct InitParams;
 cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2* lo, const int* done, cudaStream_t st,
                             bool pdl);
-cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, bool resid, cudaStream_t st, bool pdl);
+// epi: 0 plain, 1 A-apply (q = a x - D in, Re<x, q>), 2 residual
+cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl);
+cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, SolverDev* sd, const InitParams& ip,
+                           double* partials, unsigned* ticket, cudaStream_t st);
+cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl);
+cudaError_t launch_df_p_update(const Geom& g, const void* r, void* p, const SolverDev* sd, cudaStream_t st, bool pdl);
+cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl);
+cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st);
 
 // solver.cu
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,

@@ -117,6 +117,16 @@ __global__ void pack_vector_kernel(Geom g, void* __restrict__ dst, int prec, con
     d[i] = c0;
     d[vh + i] = c1;
     d[2 * vh + i] = c2;
+  } else if (prec == LQCD_DF64) {
+    // (hi, lo) = (fl32(u), fl32(u - hi)) per real component; hi block, then lo block
+    float2* d = static_cast<float2*>(dst);
+    const double2 cs[3] = {c0, c1, c2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float hx = (float)cs[k].x, hy = (float)cs[k].y;
+      d[k * vh + i] = make_float2(hx, hy);
+      d[(3 + k) * vh + i] = make_float2((float)(cs[k].x - (double)hx), (float)(cs[k].y - (double)hy));
+    }
   } else if (vec_fp32(prec)) {
     float2* d = static_cast<float2*>(dst);
     d[i] = make_float2((float)c0.x, (float)c0.y);
@@ -140,6 +150,13 @@ __global__ void unpack_vector_kernel(Geom g, double2* __restrict__ dst, const vo
     const double2* s = static_cast<const double2*>(src);
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] = s[k * vh + i];
+  } else if (prec == LQCD_DF64) {
+    const float2* s = static_cast<const float2*>(src);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 h = s[k * vh + i], l = s[(3 + k) * vh + i];
+      c[k] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
   } else if (vec_fp32(prec)) {
     const float2* s = static_cast<const float2*>(src);
 #pragma unroll

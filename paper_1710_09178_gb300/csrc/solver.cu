@@ -28,7 +28,7 @@
 namespace lqcd {
 
 // storage formats of the shifted Krylov vectors p_k and the residual window R
-enum SFmt { kS64 = 0, kS32 = 1, kS16 = 2 };
+enum SFmt { kS64 = 0, kS32 = 1, kS16 = 2, kSDF = 3 };  // kSDF: (hi, lo) FP32 pairs (LQCD_DF64)
 
 template <typename T>
 __device__ __forceinline__ Vec3<T> to_t(const Vec3<double>& v) {
@@ -78,16 +78,6 @@ __device__ __forceinline__ T site_norm2(const Vec3<T>& v) {
   return s;
 }
 
-struct InitParams {
-  int n;
-  int maxiter;
-  int ru_interval;
-  double ru_delta;
-  double s[kMaxShifts];
-  double a_diag;
-  double tol;
-};
-
 // r = p = b (Krylov precision), |b|^2 in FP64, then the scalar state of a fresh solve.
 template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(Geom g, const double2* __restrict__ b64, void* r, void* p,
@@ -106,41 +96,7 @@ __global__ void __launch_bounds__(256) init_kernel(Geom g, const double2* __rest
   double bs = block_sum(loc);
   if (publish_partial(partials, ticket, bs)) {
     double bb = gather_partials(partials, ticket);
-    int k = threadIdx.x;
-    const int trivial = !(bb > 0.0);  // b = 0 (every x_k = 0) or a non-finite source
-    if (k < ip.n) {
-      sd->s[k] = ip.s[k];
-      sd->zeta[k] = sd->zeta_prev[k] = sd->zeta_new[k] = 1.0;
-      sd->active[k] = sd->wactive[k] = trivial ? 0 : 1;
-      sd->P[k] = 1.0;
-      sd->X[k] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      sd->n = ip.n;
-      sd->a_diag = ip.a_diag;
-      sd->bb = bb;
-      sd->rr = bb;
-      sd->stop2 = ip.tol * ip.tol * bb;
-      sd->alpha = sd->beta = 0.0;
-      sd->alpha_prev = 1.0;
-      sd->beta_prev = 0.0;
-      sd->pq = 0.0;
-      sd->iter = 0;
-      sd->m = 0;
-      sd->first = 1;
-      sd->maxiter = ip.maxiter;
-      sd->ru_interval = ip.ru_interval;
-      sd->iter_ru = 0;
-      sd->ru_skip = 1;
-      sd->ru_delta2 = ip.ru_delta * ip.ru_delta;
-      sd->rr_ru_max = bb;
-      sd->windows_run = 0;
-      sd->shift_iters = 0;
-      sd->max_windows = ip.maxiter / kWindow + 2;
-      sd->n_active = trivial ? 0 : ip.n;
-      sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
-      sd->done = trivial ? 1 : 0;
-    }
+    init_scalars(sd, ip, bb);
   }
 }
 
@@ -401,6 +357,7 @@ struct Workspace {
   void* ring = nullptr;
   void* pk[kMaxShifts] = {};
   double2* xk[kMaxShifts] = {};
+  void* xdf[kMaxShifts] = {};  // LQCD_DF64: the solutions as (hi, lo) pairs during the solve
   double2 *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr, *e64 = nullptr, *rb64 = nullptr;
   // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
   bool df = false;
@@ -418,7 +375,8 @@ struct Workspace {
 
 static size_t vec_bytes(long long vh, int prec) {
   switch (prec) {
-    case LQCD_FP64: return 48 * (size_t)vh;
+    case LQCD_FP64:
+    case LQCD_DF64: return 48 * (size_t)vh;
     case LQCD_FP32:
     case LQCD_FP32_R12:
     case LQCD_FP32_R8:
@@ -443,6 +401,7 @@ void free_workspace(lqcd_ctx* ctx) {
   for (int k = 0; k < kMaxShifts; ++k) {
     if (w->pk[k]) cudaFree(w->pk[k]);
     if (w->xk[k]) cudaFree(w->xk[k]);
+    if (w->xdf[k]) cudaFree(w->xdf[k]);
   }
   if (w->host_status) cudaFreeHost(w->host_status);
   if (w->host_scal) cudaFreeHost(w->host_scal);
@@ -468,11 +427,11 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   ctx->ws = w;
   w->prec = prec;
   w->n_cap = n;
-  w->kprec = (prec == LQCD_FP64) ? LQCD_FP64 : LQCD_FP32;
-  w->sfmt = (prec == LQCD_FP64) ? kS64 : (prec == LQCD_FP16FIX ? kS16 : kS32);
+  w->kprec = (prec == LQCD_FP64 || prec == LQCD_DF64) ? prec : LQCD_FP32;
+  w->sfmt = (prec == LQCD_FP64) ? kS64 : (prec == LQCD_DF64 ? kSDF : (prec == LQCD_FP16FIX ? kS16 : kS32));
   long long vh = ctx->Vh;
   w->kbytes = vec_bytes(vh, w->kprec);
-  w->sbytes = vec_bytes(vh, prec == LQCD_FP64 ? LQCD_FP64 : (prec == LQCD_FP16FIX ? LQCD_FP16FIX : LQCD_FP32));
+  w->sbytes = vec_bytes(vh, (prec == LQCD_FP64 || prec == LQCD_DF64 || prec == LQCD_FP16FIX) ? prec : LQCD_FP32);
   w->dbytes = vec_bytes(vh, LQCD_FP64);
   LQ_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
   LQ_CUDA(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
@@ -489,13 +448,14 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   for (int k = 0; k < n; ++k) {
     LQ_CUDA(cudaMalloc(&w->pk[k], w->sbytes));
     LQ_CUDA(cudaMalloc(&w->xk[k], w->dbytes));
+    if (prec == LQCD_DF64) LQ_CUDA(cudaMalloc(&w->xdf[k], w->dbytes));
   }
   LQ_CUDA(cudaMalloc(&w->b64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->r64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->tmp64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->e64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->rb64, w->dbytes));
-  w->df = prec != LQCD_FP64 && ctx->df_resid;
+  w->df = prec == LQCD_DF64 || (prec != LQCD_FP64 && ctx->df_resid);
   if (w->df) {
     float2** dfb[] = {&w->dfx_h, &w->dfx_l, &w->dft_h, &w->dft_l, &w->dfb_h, &w->dfb_l};
     for (float2** b : dfb) LQ_CUDA(cudaMalloc(b, 24 * (size_t)vh));
@@ -529,11 +489,14 @@ struct Launcher {
 };
 
 // the four kernels of one base iteration
+static cudaError_t enqueue_iteration_df(Launcher& L);
+
 static cudaError_t enqueue_iteration(Launcher& L) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
   cudaStream_t st = w->st;
   const int* done = &w->sd->done;
+  if (w->kprec == LQCD_DF64) return enqueue_iteration_df(L);
   DslashArgs d1;
   d1.out = w->tmp;
   d1.in = w->p;
@@ -583,6 +546,57 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   return e;
 }
 
+// the four kernels of one base iteration of the double-FP32 solve (LQCD_DF64)
+static cudaError_t enqueue_iteration_df(Launcher& L) {
+  Workspace* w = L.w;
+  lqcd_ctx* ctx = L.ctx;
+  cudaStream_t st = w->st;
+  const size_t n3 = 3 * (size_t)L.g.vh;
+  auto hi = [](void* v) { return static_cast<float2*>(v); };
+  auto lo = [n3](void* v) { return static_cast<float2*>(v) + n3; };
+  DfArgs d;
+  d.links_hi = ctx->gauge.u32;
+  d.links_lo = ctx->gauge.u32lo;
+  d.in_hi = hi(w->p);
+  d.in_lo = lo(w->p);
+  d.out_hi = hi(w->tmp);
+  d.out_lo = lo(w->tmp);
+  d.done = &w->sd->done;
+  d.out_parity = 1;
+  cudaError_t e = launch_df_dslash(L.g, d, 0, st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  DfArgs a = d;
+  a.in_hi = hi(w->tmp);
+  a.in_lo = lo(w->tmp);
+  a.out_hi = hi(w->q);
+  a.out_lo = lo(w->q);
+  a.x_hi = hi(w->p);
+  a.x_lo = lo(w->p);
+  a.a_dev = &w->sd->a_diag;
+  a.solver = w->sd;
+  a.partials = w->partials;
+  a.ticket = w->tickets + 0;
+  a.out_parity = 0;
+  e = launch_df_dslash(L.g, a, 1, st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  DfUpdArgs u;
+  u.r = hi(w->r);
+  u.q = hi(w->q);
+  u.ring = w->ring;
+  u.slot_bytes = w->sbytes;
+  u.sd = w->sd;
+  u.partials = w->partials;
+  u.ticket = w->tickets + 1;
+  e = launch_df_r_update(L.g, u, st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  e = launch_df_p_update(L.g, w->r, w->p, w->sd, st, L.next_pdl());
+  L.nlaunch += 1;
+  return e;
+}
+
 static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n) {
   Workspace* w = L.w;
   FlushArgs fa;
@@ -597,6 +611,23 @@ static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2*
   fa.sd = w->sd;
   fa.partials = w->partials;
   fa.ticket = w->tickets + 2;
+  if (w->sfmt == kSDF) {
+    DfFlushArgs df;
+    memset(&df, 0, sizeof(df));
+    df.ring = w->ring;
+    df.slot_bytes = w->sbytes;
+    for (int k = 0; k < n; ++k) {
+      df.pk[k] = static_cast<float2*>(w->pk[k]);
+      df.xk[k] = reinterpret_cast<float2*>(xs[k]);
+    }
+    df.b_hi = w->dfb_h;
+    df.b_lo = w->dfb_l;
+    df.sd = w->sd;
+    df.partials = w->partials;
+    df.ticket = w->tickets + 2;
+    L.nlaunch += 1;
+    return launch_df_flush(L.g, df, w->st, L.next_pdl());
+  }
   int nb = (L.g.vh + 127) / 128;
   const bool pdl = L.next_pdl();
   L.nlaunch += 1;
@@ -653,7 +684,7 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
   d.out_lo = w->dft_l;
   d.done = done;
   d.out_parity = 1;
-  e = launch_df_dslash(L.g, d, false, w->st, L.next_pdl());
+  e = launch_df_dslash(L.g, d, 0, w->st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
   DfArgs r = d;
@@ -671,7 +702,7 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
   r.dot_out = dot;
   r.partials = w->partials;
   r.ticket = w->tickets + 3;
-  e = launch_df_dslash(L.g, r, true, w->st, L.next_pdl());
+  e = launch_df_dslash(L.g, r, 2, w->st, L.next_pdl());
   L.nlaunch += 1;
   return e;
 }
@@ -735,7 +766,9 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   ip.ru_delta = ctx->reliable_delta;
   LQ_CUDA(cudaMemsetAsync(w->ru_count, 0, sizeof(int), w->st));
   int nb = (L.g.vh + 255) / 256;
-  if (w->kprec == LQCD_FP64)
+  if (w->kprec == LQCD_DF64)
+    LQ_CUDA(launch_df_init(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4, w->st));
+  else if (w->kprec == LQCD_FP64)
     init_kernel<double><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
   else
     init_kernel<float><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
@@ -910,8 +943,16 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
   }
 
   int iters = 0, n_ru = 0, st_main = LQCD_OK;
-  rc = solve_core(ctx, w->b64, w->xk, shifts, n, tol, maxiter, prec != LQCD_FP64, &iters, &n_ru, &st_main);
+  // LQCD_DF64 iterates on (hi, lo) solutions and needs no reliable updates; they become FP64 after
+  const bool dfsolve = prec == LQCD_DF64;
+  double2* const* xs_run = dfsolve ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
+  rc = solve_core(ctx, w->b64, xs_run, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, &iters, &n_ru,
+                  &st_main);
   if (rc != LQCD_OK) return rc;
+  if (dfsolve) {
+    for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, w->xdf[k], w->xk[k], w->st));
+    ctx->launches += n;
+  }
   LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
   double bb = w->host_scal[0];

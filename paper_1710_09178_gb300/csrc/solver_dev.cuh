@@ -23,6 +23,57 @@ namespace lqcd {
 // lane are issued before any store (the state lives in global memory and a chain of dependent
 // round trips would cost far more than the arithmetic, most of which is FP64).
 
+// parameters of a fresh solve (host to the init kernel)
+struct InitParams {
+  int n;
+  int maxiter;
+  int ru_interval;
+  double ru_delta;
+  double s[kMaxShifts];
+  double a_diag;
+  double tol;
+};
+
+// Scalar state of a fresh solve; last block of the init kernel, all threads call, bb identical in
+// every thread.
+__device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip, double bb) {
+  int k = threadIdx.x;
+  const int trivial = !(bb > 0.0);  // b = 0 (every x_k = 0) or a non-finite source
+  if (k < ip.n) {
+    sd->s[k] = ip.s[k];
+    sd->zeta[k] = sd->zeta_prev[k] = sd->zeta_new[k] = 1.0;
+    sd->active[k] = sd->wactive[k] = trivial ? 0 : 1;
+    sd->P[k] = 1.0;
+    sd->X[k] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    sd->n = ip.n;
+    sd->a_diag = ip.a_diag;
+    sd->bb = bb;
+    sd->rr = bb;
+    sd->stop2 = ip.tol * ip.tol * bb;
+    sd->alpha = sd->beta = 0.0;
+    sd->alpha_prev = 1.0;
+    sd->beta_prev = 0.0;
+    sd->pq = 0.0;
+    sd->iter = 0;
+    sd->m = 0;
+    sd->first = 1;
+    sd->maxiter = ip.maxiter;
+    sd->ru_interval = ip.ru_interval;
+    sd->iter_ru = 0;
+    sd->ru_skip = 1;
+    sd->ru_delta2 = ip.ru_delta * ip.ru_delta;
+    sd->rr_ru_max = bb;
+    sd->windows_run = 0;
+    sd->shift_iters = 0;
+    sd->max_windows = ip.maxiter / kWindow + 2;
+    sd->n_active = trivial ? 0 : ip.n;
+    sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
+    sd->done = trivial ? 1 : 0;
+  }
+}
+
 // last block, all threads call; pq identical in every thread
 __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
   if (threadIdx.x >= 32) return;

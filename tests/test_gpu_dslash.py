@@ -13,7 +13,7 @@ from paper_1710_09178_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FP64, FP32, FP32_R12, FP16FIX = 0, 1, 2, 3
+FP64, FP32, FP32_R12, FP16FIX, DF64 = 0, 1, 2, 3, 6
 # (10, 6, 4, 6): V/2 = 720 sites is not a multiple of any block, so every launch has a ragged tail
 DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 2, 2), (10, 6, 4, 6), (16, 16, 16, 8)]
 
@@ -81,6 +81,35 @@ def test_apply_A_and_dot(prec, tol):
     assert rel_max(q, ref) < tol
     oref = float(np.real(np.vdot(psi, ref)))
     assert abs(pq - oref) < max(tol, 1e-12) * abs(oref)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_dslash_double_fp32_matches_oracle(dims):
+    # (hi, lo) links and vectors with exact products and compensated sums: ~2^-48 relative
+    ctx, U = make_context(dims, 0.1, gauge_seed=3)
+    psi = inputs.gaussian_vector(dims, 24)
+    for p in (0, 1):
+        ref = staggered.dslash_eo(U, psi, dims, p)
+        assert rel_max(gpu_dslash(ctx, psi, p, DF64), ref) < 1e-13
+
+
+def test_apply_A_double_fp32_and_free_field():
+    dims, m, sigma = (10, 6, 4, 6), 0.05, 0.013
+    ctx, U = make_context(dims, m, gauge_seed=4)
+    psi = inputs.gaussian_vector(dims, 25)
+    q, pq = gpu_apply_A(ctx, psi, sigma, DF64)
+    ref = staggered.A_apply(U, psi, m, dims, sigma)
+    assert rel_max(q, ref) < 1e-13
+    assert abs(pq - float(np.real(np.vdot(psi, ref)))) < 1e-12 * abs(pq)
+    dims, m = (4, 4, 4, 4), 0.1
+    ctx, U = make_context(dims, m, U=inputs.unit_gauge_field(dims))
+    x, y, z, t = lattice.coords(dims)
+    p = [2 * np.pi / 4, 2 * np.pi * 2 / 4, 0.0, 2 * np.pi * 1.5 / 4]
+    full = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))[:, None] * np.array([1.0, -0.5j, 0.25])
+    psi = staggered.restrict(full, dims, 0)
+    q, _ = gpu_apply_A(ctx, psi, 0.0, DF64)
+    lam = 4 * m * m + sum(np.sin(pm) ** 2 for pm in p)
+    assert np.max(np.abs(q - lam * psi)) < 1e-13
 
 
 def test_free_field_on_gpu():
