@@ -57,7 +57,7 @@ __device__ __forceinline__ float2 df_norm(float s, float c) {
 }
 
 // Sum over the block of per-thread double-FP32 values (s, c): TwoSum shuffles within each warp,
-// then the warps' FP64 values in a fixed order.  Result valid in every thread.
+// then the warps' FP64 values in a fixed order.  Result valid in thread 0 (which publishes it).
 __device__ __forceinline__ double block_sum_df(float s, float c) {
   __shared__ double red_df[32];
 #pragma unroll
@@ -69,10 +69,13 @@ __device__ __forceinline__ double block_sum_df(float s, float c) {
   if (lane == 0) red_df[warp] = (double)s + (double)c;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < nw; ++w) t += red_df[w];
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += red_df[w];
   __syncthreads();
   return t;
 }
+
+__device__ __forceinline__ float2 split64(double a) { return split_hi_lo(a); }
 
 // x (FP64) -> (hi, lo) FP32 pairs
 __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __restrict__ x, float2* __restrict__ hi,
@@ -153,8 +156,8 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
     // q = a x - D in (x = the own-site vector, p of the solve), Re<x, q> in double-FP32
     float ds = 0.f, dc = 0.f;
     if (valid) {
-      const double a64 = k.a_dev ? *k.a_dev : k.a;
-      const float ah = __double2float_rn(a64), al = __double2float_rn(a64 - (double)ah);
+      const float2 asp = k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a);
+      const float ah = asp.x, al = asp.y;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const size_t o = (size_t)a * vh + i;
@@ -222,11 +225,6 @@ cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream
 // The double-FP32 shifted CG (mode LQCD_DF64): the same steps as the FP32/FP64 kernels of the
 // solver, on (hi, lo) vectors.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 split64(double a) {
-  const float h = __double2float_rn(a);
-  return make_float2(h, __double2float_rn(a - (double)h));
-}
-
 // r = p = b as (hi, lo), |b|^2 in FP64, then the scalar state of a fresh solve
 __global__ void __launch_bounds__(256) df_init_kernel(Geom g, const double2* __restrict__ b64, float2* r, float2* p,
                                                       SolverDev* sd, InitParams ip, double* partials,
@@ -260,7 +258,7 @@ __global__ void __launch_bounds__(256) df_r_update_kernel(Geom g, DfUpdArgs a) {
   if (sd->done) return;
   const int m = sd->m;
   const int vh = g.vh;
-  const float2 al = split64(sd->alpha);
+  const float2 al = sd->alpha_df;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float ls = 0.f, lc = 0.f;
   if (i < vh && m < kWindow) {
@@ -294,7 +292,7 @@ __global__ void __launch_bounds__(256) df_p_update_kernel(Geom g, const float2* 
   const int n3 = 3 * g.vh;
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n3) return;
-  const float2 be = split64(sd->beta);
+  const float2 be = sd->beta_df;
   const float2 rh = r[o], rl = r[o + n3], ph = p[o], pl = p[o + n3];
   float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
   df_mac(rs, rc, be.x, be.y, ph.x, pl.x);

@@ -26,6 +26,7 @@ struct KArgs {
   const void* bvec;
   double a;
   const double* a_dev;
+  const float* a_devf;
   int out_parity;
   double* dot_out;
   SolverDev* solver;
@@ -178,7 +179,11 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   }
 
   V2* out = static_cast<V2*>(k.out);
-  const T aval = (EPI != (int)Epi::Plain && k.a_dev) ? (T)*k.a_dev : (T)k.a;
+  T aval = (T)k.a;
+  if constexpr (EPI != (int)Epi::Plain) {
+    if (sizeof(T) == 4 && k.a_devf) aval = (T)*k.a_devf;
+    else if (k.a_dev) aval = (T)*k.a_dev;
+  }
   T dsite = 0;  // this lane's share of the site's dot product, summed in T, then added in FP64
   if (valid) {
 #pragma unroll
@@ -261,6 +266,7 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
   k.bvec = a.bvec;
   k.a = a.a;
   k.a_dev = a.a_dev;
+  k.a_devf = a.a_devf;
   k.out_parity = a.out_parity;
   k.dot_out = a.dot_out;
   k.solver = a.solver;

@@ -29,6 +29,10 @@ struct SolverDev {
   double alpha, alpha_prev, beta, beta_prev;
   double pq;
   double a_diag;   // 4 m^2 + sigma_0
+  // FP32 and (hi, lo) copies of alpha, beta and a_diag, written once by the scalar steps so that
+  // the vector kernels convert nothing from FP64 per thread
+  float alpha_f, beta_f, a_diag_f;
+  float2 alpha_df, beta_df, a_diag_df;
   int iter;
   int done;        // 1: every shift stopped (or error); iteration kernels return at entry
   int status;      // LQCD_OK or LQCD_ERR_NONFINITE
@@ -125,6 +129,7 @@ struct DslashArgs {
   Epi epi = Epi::Plain;
   double a = 0;
   const double* a_dev = nullptr; // if set, a is read from device memory (solver state) at run time
+  const float* a_devf = nullptr; // its FP32 copy (read instead by the FP32 kernels)
   const void* aux = nullptr;
   const void* bvec = nullptr;
   double* dot_out = nullptr;     // where the reduced scalar goes (AApply without solver, Resid)
@@ -150,6 +155,7 @@ struct DfArgs {
   const float2* b_hi = nullptr;
   const float2* b_lo = nullptr;
   const double* a_dev = nullptr;    // 4 m^2 + sigma read from device memory, else a
+  const float2* a_devdf = nullptr;  // its (hi, lo) copy, read instead when set
   double a = 0;
   float2* r_out = nullptr;          // residual rounded to FP32
   double* dot_out = nullptr;        // |r|^2

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
   pdl_trigger();
   if (sd->done) return;
   const int m = sd->m;
-  const T alpha = (T)sd->alpha;
+  const T alpha = sizeof(T) == 4 ? (T)sd->alpha_f : (T)sd->alpha;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   T loc = 0;
   if (i < g.vh && m < kWindow) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) p_update_kernel(Geom g, const void* r, vo
   pdl_wait();
   pdl_trigger();
   if (sd->done) return;
-  const T beta = (T)sd->beta;
+  const T beta = sizeof(T) == 4 ? (T)sd->beta_f : (T)sd->beta;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * g.vh) return;
   V2 rv = static_cast<const V2*>(r)[i];
@@ -515,6 +515,7 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   d2.epi = Epi::AApply;
   d2.aux = w->p;
   d2.a_dev = &w->sd->a_diag;  // 4 m^2 + sigma_0 of the running solve
+  d2.a_devf = &w->sd->a_diag_f;
   d2.solver = w->sd;
   d2.partials = w->partials;
   d2.ticket = w->tickets + 0;
@@ -574,6 +575,7 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   a.x_hi = hi(w->p);
   a.x_lo = lo(w->p);
   a.a_dev = &w->sd->a_diag;
+  a.a_devdf = &w->sd->a_diag_df;
   a.solver = w->sd;
   a.partials = w->partials;
   a.ticket = w->tickets + 0;

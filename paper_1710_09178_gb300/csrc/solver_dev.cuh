@@ -19,6 +19,11 @@
 
 namespace lqcd {
 
+__device__ __forceinline__ float2 split_hi_lo(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+
 // The steps run in one warp of the last block; every lane k < n owns shift k.  All loads of a
 // lane are issued before any store (the state lives in global memory and a chain of dependent
 // round trips would cost far more than the arithmetic, most of which is FP64).
@@ -49,6 +54,10 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
   if (threadIdx.x == 0) {
     sd->n = ip.n;
     sd->a_diag = ip.a_diag;
+    sd->a_diag_f = (float)ip.a_diag;
+    sd->a_diag_df = split_hi_lo(ip.a_diag);
+    sd->alpha_f = sd->beta_f = 0.f;
+    sd->alpha_df = sd->beta_df = make_float2(0.f, 0.f);
     sd->bb = bb;
     sd->rr = bb;
     sd->stop2 = ip.tol * ip.tol * bb;
@@ -100,6 +109,8 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
   if (k == 0) {
     sd->pq = pq;
     sd->alpha = alpha;
+    sd->alpha_f = (float)alpha;
+    sd->alpha_df = split_hi_lo(alpha);
     if (!ok) {
       sd->status = LQCD_ERR_NONFINITE;
       sd->done = 1;
@@ -180,6 +191,8 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
     const int it = iter + 1;
     const int done = (n_active == 0 || it >= maxiter) ? 1 : 0;
     sd->beta = beta;
+    sd->beta_f = (float)beta;
+    sd->beta_df = split_hi_lo(beta);
     sd->n_active = n_active;
     sd->m = m + 1;
     sd->rr = rr_new;
