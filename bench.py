@@ -506,12 +506,13 @@ def main():
     extra = {}
     if not args.quick:
         # FP64 solve (the plain method) and the other storage modes
-        for name, prec in (("fp64", lq.FP64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX),
+        for name, prec in (("fp64", lq.FP64), ("df64", lq.DF64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX),
                            ("fp32_r8", lq.FP32_R8), ("fp32_l16", lq.FP32_L16)):
             tms, sts = time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
             extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
                            "algorithmic_GBps": solve_algorithmic_bytes(sts[-1], int(np.prod(DIMS)) // 2,
-                                                                       prec == lq.FP64) / (statistics.mean(tms) * 1e6),
+                                                                       prec in (lq.FP64, lq.DF64))
+                           / (statistics.mean(tms) * 1e6),
                            "reliable_updates": sts[-1]["reliable_updates"],
                            "refine_iterations": sts[-1]["refine_iterations"],
                            "max_true_residual": max(sts[-1]["true_residual"])}
@@ -597,6 +598,7 @@ def main():
                   "refine_iterations": last["refine_iterations"], "refined_shifts": last["refined_shifts"],
                   "max_true_residual": max(last["true_residual"]), "ms_per_solve_all": times},
         "fp64_vs_mixed": (extra["fp64"]["ms_per_solve"] / ms_per_solve) if "fp64" in extra else None,
+        "fp64_vs_df64": (extra["fp64"]["ms_per_solve"] / extra["df64"]["ms_per_solve"]) if "df64" in extra else None,
         "modes": extra,
         "dslash": dsl,
         "roofline": roofline,

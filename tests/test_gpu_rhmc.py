@@ -26,7 +26,8 @@ def _momenta(seed):
     return inputs.counter_normal_pairs(seed, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
 
 
-def test_trajectory_matches_oracle():
+@pytest.mark.parametrize("prec_action", [0, 6])  # heatbath and Hamiltonian solves in FP64 or double-FP32
+def test_trajectory_matches_oracle(prec_action):
     import torch
 
     import paper_1710_09178_gb300 as lq
@@ -41,7 +42,7 @@ def test_trajectory_matches_oracle():
     mom = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
     rc, res = lq.rhmc_trajectory(ctx, Ud, to_dev(p0), to_dev(xi), 0.999999, BETA, TAU, NSTEPS,
                                  (act[0], act[1], act[2]), (heat[0], heat[1], heat[2]), tol=1e-12, prec=FP64,
-                                 prec_action=FP64, mom_out=mom, links_out=links)
+                                 prec_action=prec_action, mom_out=mom, links_out=links)
     assert rc == 0
     Uo, acc, info = rhmc.trajectory(U0, p0, xi, 0.999999, DIMS, MASS, BETA, TAU, NSTEPS, act, heat, tol=1e-12)
     for k in ("kinetic", "gauge", "fermion"):
