@@ -151,6 +151,19 @@ class L2Flusher:
         self.sink.add_(self.r.sum())
 
 
+def replica_aggregate(total_ms, steps, world, dist, device):
+    """N independent replicas (one lattice solve per rank, no data-path collective): the timed
+    region is the slowest rank's, and the whole job completes steps x world solves in it.
+    Returns (max timed ms, ms per solve of one replica, whole-job ms per solve)."""
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / steps, total_ms / (steps * world)
+
+
 def solve_algorithmic_bytes(st, vh, fp64):
     """Minimum traffic of the plain shifted CG's base iterations (every vector and link crossing HBM
     once): per iteration and site the A-apply (two half-Dslash + the own-site read), the r and p
@@ -495,13 +508,7 @@ def main():
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     launches_timed = sum(s["kernel_launches"] for s in stats)
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_solve = total_ms / args.steps
-    value = total_ms / (args.steps * world)  # whole-job time per solve over all replicas
+    total_ms, ms_per_solve, value = replica_aggregate(sum(times), args.steps, world, dist, "cuda")
 
     extra = {}
     if not args.quick:
