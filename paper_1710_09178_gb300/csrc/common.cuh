@@ -587,8 +587,8 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // Sum over the block of per-thread values of type T: within each warp in T (FP32 keeps the
-// FP64 pipe, 1/64 of the FP32 rate on GB300, out of the per-thread path), across warps in FP64.
-// Result valid in every thread.
+// FP64 pipe, 1/64 of the FP32 rate on GB300, out of the per-thread path), across warps in FP64
+// by warp 0 alone.  Result valid in warp 0 (every caller publishes it from thread 0).
 template <typename T>
 __device__ __forceinline__ double block_sum_mixed(T v) {
   __shared__ double red_smem2[32];
@@ -598,9 +598,32 @@ __device__ __forceinline__ double block_sum_mixed(T v) {
   __syncthreads();
   if (l == 0) red_smem2[w] = (double)v;
   __syncthreads();
+  if (w != 0) return 0.0;
   int nw = blockDim.x >> 5;
   double t = (l < nw) ? red_smem2[l] : 0.0;
   return warp_sum(t);
+}
+
+// G sums at once (one per system of a multi-RHS kernel): FP32 within each warp, FP64 across the
+// warps in a fixed order.  out[q] valid in thread q < G; two barriers for all G.
+template <typename T, int G>
+__device__ __forceinline__ void block_sum_multi(const T (&v)[G], double (&out)[G]) {
+  __shared__ double red_multi[32][G];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    T x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (l == 0) red_multi[w][q] = (double)x;
+  }
+  __syncthreads();
+  if (threadIdx.x < G) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += red_multi[k][threadIdx.x];
+    out[threadIdx.x % G] = t;
+  }
+  __syncthreads();
 }
 
 // Publish this block's partial; returns true in the one block that finishes last.

@@ -36,6 +36,7 @@ struct MrhsDev {
   unsigned ticket[4];
   double a[kMrhsMax];  // 4 m^2 + sigma_j
   float af[kMrhsMax];  // the same in FP32 (no FP64 conversion inside the FP32 kernels)
+  float alpha_f[kMrhsMax], beta_f[kMrhsMax];  // FP32 copies written by the scalar steps
   double rr[kMrhsMax], stop2[kMrhsMax], alpha[kMrhsMax], beta[kMrhsMax];
 };
 
@@ -131,10 +132,11 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
         if (q < ng) store_vec(static_cast<V2*>(vv.tmp[sys[q]]), i, vh, acc[q]);
     }
   } else {
+    T d[kMrhsGroup];
+#pragma unroll
     for (int q = 0; q < kMrhsGroup; ++q) {
-      if (q >= ng) break;  // uniform
-      T d = 0;
-      if (i < vh) {
+      d[q] = 0;
+      if (q < ng && i < vh) {
         const int sj = sys[q];
         const T a = sizeof(T) == 4 ? (T)md->af[sj] : (T)md->a[sj];
         Vec3<T> pv = load_vec(static_cast<const V2*>(vv.p[sj]), i, vh);
@@ -143,13 +145,14 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
         for (int c = 0; c < 3; ++c) {
           qv.c[c].re = a * pv.c[c].re - acc[q].c[c].re;
           qv.c[c].im = a * pv.c[c].im - acc[q].c[c].im;
-          d += pv.c[c].re * qv.c[c].re + pv.c[c].im * qv.c[c].im;
+          d[q] += pv.c[c].re * qv.c[c].re + pv.c[c].im * qv.c[c].im;
         }
         store_vec(static_cast<V2*>(vv.q[sj]), i, vh, qv);
       }
-      double bsum = block_sum_mixed(d);
-      if (threadIdx.x == 0) partials[(size_t)(g0 + q) * gridDim.x + blockIdx.x] = bsum;
     }
+    double bsum[kMrhsGroup];
+    block_sum_multi(d, bsum);
+    if (threadIdx.x < ng) partials[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = bsum[threadIdx.x];
     // last block over the whole grid (all groups): alpha_j = (r_j, r_j) / (p_j, q_j)
     __shared__ bool last;
     __syncthreads();
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
             md->done = 1;
           }
           md->alpha[sj] = alpha;
+          md->alpha_f[sj] = (float)alpha;
         }
       }
       if (threadIdx.x == 0) md->ticket[0] = 0u;
@@ -195,10 +199,13 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
   const int ng = min(kMrhsGroup, n_act - g0);
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int q = 0; q < ng; ++q) {
+  T d[kMrhsGroup];
+#pragma unroll
+  for (int q = 0; q < kMrhsGroup; ++q) {
+    d[q] = 0;
+    if (q >= ng) continue;
     const int sj = md->list[g0 + q];
-    const T alpha = (T)md->alpha[sj];
-    T d = 0;
+    const T alpha = sizeof(T) == 4 ? (T)md->alpha_f[sj] : (T)md->alpha[sj];
     if (i < vh) {
       Vec3<T> pv = load_vec(static_cast<const V2*>(vv.p[sj]), i, vh);
       Vec3<T> qv = load_vec(static_cast<const V2*>(vv.q[sj]), i, vh);
@@ -210,13 +217,16 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
         ev.c[c].im = fma(alpha, pv.c[c].im, ev.c[c].im);
         rv.c[c].re = fma(-alpha, qv.c[c].re, rv.c[c].re);
         rv.c[c].im = fma(-alpha, qv.c[c].im, rv.c[c].im);
-        d += rv.c[c].re * rv.c[c].re + rv.c[c].im * rv.c[c].im;
+        d[q] += rv.c[c].re * rv.c[c].re + rv.c[c].im * rv.c[c].im;
       }
       store_vec(static_cast<V2*>(vv.e[sj]), i, vh, ev);
       store_vec(static_cast<V2*>(vv.r[sj]), i, vh, rv);
     }
-    double bsum = block_sum_mixed(d);
-    if (threadIdx.x == 0) partials[(size_t)(g0 + q) * gridDim.x + blockIdx.x] = bsum;
+  }
+  {
+    double bsum[kMrhsGroup];
+    block_sum_multi(d, bsum);
+    if (threadIdx.x < ng) partials[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = bsum[threadIdx.x];
   }
   __shared__ bool last;
   __syncthreads();
@@ -242,6 +252,7 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
         md->done = 1;
       }
       md->beta[sj] = beta;
+      md->beta_f[sj] = (float)beta;
       md->rr[sj] = v;
       keep[pos] = !(v <= md->stop2[sj]);
     }
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(256) mrhs_pupdate_kernel(Geom g, MrhsVecs vv, 
   if (k >= 3 * g.vh) return;
   for (int q = 0; q < ng; ++q) {
     const int sj = md->list[g0 + q];
-    const T beta = (T)md->beta[sj];
+    const T beta = sizeof(T) == 4 ? (T)md->beta_f[sj] : (T)md->beta[sj];
     V2 rv = static_cast<const V2*>(vv.r[sj])[k];
     V2 pv = static_cast<V2*>(vv.p[sj])[k];
     pv.x = fma(beta, pv.x, rv.x);
@@ -330,6 +341,7 @@ __global__ void __launch_bounds__(128) mrhs_init_kernel(Geom g, MrhsVecs vv, Mrh
       md->a[sj] = in.a[sj];
       md->af[sj] = (float)in.a[sj];
       md->alpha[sj] = md->beta[sj] = 0.0;
+      md->alpha_f[sj] = md->beta_f[sj] = 0.f;
     }
   }
   __syncthreads();
