@@ -562,6 +562,39 @@ __device__ __forceinline__ Mat3<float> load_link16(const char* __restrict__ U, i
 }
 
 // ---------------------------------------------------------------------------
+// Double-FP32 ("df") arithmetic: an FP64-class number as an FP32 pair (hi, lo), operated on
+// with FP32 instructions only (exact FMA products, Knuth's TwoSum).
+// ---------------------------------------------------------------------------
+// s + c += (ah + al)(bh + bl), dropping al bl.  The _rn intrinsics are never contracted into
+// fused multiply-adds, which TwoSum's exactness requires.
+__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// s + c += (bh + bl)
+__device__ __forceinline__ void df_add(float& s, float& c, float bh, float bl) {
+  const float t = __fadd_rn(s, bh);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(bh, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, bl));
+}
+
+// (hi, lo) with hi = fl32(s + c) (Fast2Sum: |s| >= |c| for an accumulated correction)
+__device__ __forceinline__ float2 df_norm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic reductions.  Each block reduces in a fixed tree and writes one
 // partial; the last block to finish (atomic ticket) adds the partials in index
 // order, so the result does not depend on block scheduling.

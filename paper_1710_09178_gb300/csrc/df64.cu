@@ -27,35 +27,6 @@
 
 namespace lqcd {
 
-// s + c += (ah + al)(bh + bl), dropping al bl.  The _rn intrinsics are never contracted into
-// fused multiply-adds, which TwoSum's exactness requires.
-__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  const float t = __fadd_rn(s, p);
-  const float z = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, e));
-}
-
-// s + c += (bh + bl)
-__device__ __forceinline__ void df_add(float& s, float& c, float bh, float bl) {
-  const float t = __fadd_rn(s, bh);
-  const float z = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(bh, z));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, bl));
-}
-
-// (hi, lo) with hi = fl32(s + c) (Fast2Sum: |s| >= |c| for an accumulated correction)
-__device__ __forceinline__ float2 df_norm(float s, float c) {
-  const float h = __fadd_rn(s, c);
-  return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
-}
-
 // Sum over the block of per-thread double-FP32 values (s, c): TwoSum shuffles within each warp,
 // then the warps' FP64 values in a fixed order.  Result valid in thread 0 (which publishes it).
 __device__ __forceinline__ double block_sum_df(float s, float c) {

@@ -171,7 +171,7 @@ struct FlushArgs {
 
 // Apply the pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i.
 // At the first window of a solve p_k0 = b and x_k0 = 0 (nothing is read).
-template <typename T, int SF>
+template <typename T, int SF, bool XDF>
 __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
   SolverDev* sd = a.sd;
   pdl_wait();
@@ -225,13 +225,34 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
       }
       store_s<SF, T>(a.pk[k], i, vh, np);
       // x_k is touched once per window: stream it through L2 without displacing the links
+      if constexpr (XDF) {
+        // (hi, lo) FP32 pairs: the window's increment added with TwoSum, no FP64 instruction
+        float2* xh = reinterpret_cast<float2*>(a.xk[k]);
+        const size_t n3 = 3 * (size_t)vh;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        double2* xp = a.xk[k] + (size_t)c * vh + i;
-        double2 x = first ? make_double2(0.0, 0.0) : ld_hint(xp, pol);
-        x.x += (double)dx.c[c].re;
-        x.y += (double)dx.c[c].im;
-        st_hint(xp, x, pol);
+        for (int c = 0; c < 3; ++c) {
+          const size_t o = (size_t)c * vh + i;
+          float2 h = make_float2(0.f, 0.f), l = h;
+          if (!first) {
+            h = ld_hint(xh + o, pol);
+            l = ld_hint(xh + o + n3, pol);
+          }
+          float rs = h.x, rc = l.x, is = h.y, ic = l.y;
+          df_add(rs, rc, (float)dx.c[c].re, 0.f);
+          df_add(is, ic, (float)dx.c[c].im, 0.f);
+          const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+          st_hint(xh + o, make_float2(re.x, im.x), pol);
+          st_hint(xh + o + n3, make_float2(re.y, im.y), pol);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double2* xp = a.xk[k] + (size_t)c * vh + i;
+          double2 x = first ? make_double2(0.0, 0.0) : ld_hint(xp, pol);
+          x.x += (double)dx.c[c].re;
+          x.y += (double)dx.c[c].im;
+          st_hint(xp, x, pol);
+        }
       }
     }
   }
@@ -357,7 +378,8 @@ struct Workspace {
   void* ring = nullptr;
   void* pk[kMaxShifts] = {};
   double2* xk[kMaxShifts] = {};
-  void* xdf[kMaxShifts] = {};  // LQCD_DF64: the solutions as (hi, lo) pairs during the solve
+  void* xdf[kMaxShifts] = {};  // the solutions as (hi, lo) FP32 pairs during the solve (xdfmode)
+  bool xdfmode = false;        // every mode but LQCD_FP64 (with double-FP32 residuals)
   double2 *b64 = nullptr, *r64 = nullptr, *tmp64 = nullptr, *e64 = nullptr, *rb64 = nullptr;
   // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
   bool df = false;
@@ -448,7 +470,7 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   for (int k = 0; k < n; ++k) {
     LQ_CUDA(cudaMalloc(&w->pk[k], w->sbytes));
     LQ_CUDA(cudaMalloc(&w->xk[k], w->dbytes));
-    if (prec == LQCD_DF64) LQ_CUDA(cudaMalloc(&w->xdf[k], w->dbytes));
+    if (prec == LQCD_DF64 || (prec != LQCD_FP64 && ctx->df_resid)) LQ_CUDA(cudaMalloc(&w->xdf[k], w->dbytes));
   }
   LQ_CUDA(cudaMalloc(&w->b64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->r64, w->dbytes));
@@ -456,6 +478,7 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   LQ_CUDA(cudaMalloc(&w->e64, w->dbytes));
   LQ_CUDA(cudaMalloc(&w->rb64, w->dbytes));
   w->df = prec == LQCD_DF64 || (prec != LQCD_FP64 && ctx->df_resid);
+  w->xdfmode = w->df;
   if (w->df) {
     float2** dfb[] = {&w->dfx_h, &w->dfx_l, &w->dft_h, &w->dft_l, &w->dfb_h, &w->dfb_l};
     for (float2** b : dfb) LQ_CUDA(cudaMalloc(b, 24 * (size_t)vh));
@@ -633,9 +656,13 @@ static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2*
   int nb = (L.g.vh + 127) / 128;
   const bool pdl = L.next_pdl();
   L.nlaunch += 1;
-  if (w->sfmt == kS64) return launch_k(pdl, flush_kernel<double, kS64>, dim3(nb), dim3(128), w->st, L.g, fa);
-  if (w->sfmt == kS16) return launch_k(pdl, flush_kernel<float, kS16>, dim3(nb), dim3(128), w->st, L.g, fa);
-  return launch_k(pdl, flush_kernel<float, kS32>, dim3(nb), dim3(128), w->st, L.g, fa);
+  if (w->sfmt == kS64) return launch_k(pdl, flush_kernel<double, kS64, false>, dim3(nb), dim3(128), w->st, L.g, fa);
+  if (w->sfmt == kS16) {
+    if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS16, true>, dim3(nb), dim3(128), w->st, L.g, fa);
+    return launch_k(pdl, flush_kernel<float, kS16, false>, dim3(nb), dim3(128), w->st, L.g, fa);
+  }
+  if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS32, true>, dim3(nb), dim3(128), w->st, L.g, fa);
+  return launch_k(pdl, flush_kernel<float, kS32, false>, dim3(nb), dim3(128), w->st, L.g, fa);
 }
 
 // FP64 residual r64 = bvec - (A + sigma) x into r64, |r64|^2 into *dot (device)
@@ -674,14 +701,23 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
                                     double* dot, const int* done) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
-  cudaError_t e = launch_split_df(L.g, x, w->dfx_h, w->dfx_l, done, w->st, L.next_pdl());
-  L.nlaunch += 1;
-  if (e != cudaSuccess) return e;
+  const float2* xh = w->dfx_h;
+  const float2* xl = w->dfx_l;
+  cudaError_t e = cudaSuccess;
+  if (w->xdfmode) {
+    // the solutions are already (hi, lo) pairs
+    xh = reinterpret_cast<const float2*>(x);
+    xl = xh + 3 * (size_t)L.g.vh;
+  } else {
+    e = launch_split_df(L.g, x, w->dfx_h, w->dfx_l, done, w->st, L.next_pdl());
+    L.nlaunch += 1;
+    if (e != cudaSuccess) return e;
+  }
   DfArgs d;
   d.links_hi = ctx->gauge.u32;
   d.links_lo = ctx->gauge.u32lo;
-  d.in_hi = w->dfx_h;
-  d.in_lo = w->dfx_l;
+  d.in_hi = xh;
+  d.in_lo = xl;
   d.out_hi = w->dft_h;
   d.out_lo = w->dft_l;
   d.done = done;
@@ -694,8 +730,8 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
   r.in_lo = w->dft_l;
   r.out_hi = r.out_lo = nullptr;
   r.out_parity = 0;
-  r.x_hi = w->dfx_h;
-  r.x_lo = w->dfx_l;
+  r.x_hi = xh;
+  r.x_lo = xl;
   r.b_hi = w->dfb_h;
   r.b_lo = w->dfb_l;
   r.a = 4.0 * ctx->mass * ctx->mass + sigma;
@@ -881,6 +917,19 @@ __global__ void keep_residual_kernel(int n3, const double2* __restrict__ r64, vo
   else static_cast<double2*>(dst)[i] = v;
 }
 
+// x ((hi, lo) FP32 pairs) += e (FP32)
+__global__ void add_correction_df_kernel(int n3, float2* __restrict__ x, const float2* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const float2 h = x[i], l = x[i + n3], ev = e[i];
+  float rs = h.x, rc = l.x, is = h.y, ic = l.y;
+  df_add(rs, rc, ev.x, 0.f);
+  df_add(is, ic, ev.y, 0.f);
+  const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+  x[i] = make_float2(re.x, im.x);
+  x[i + n3] = make_float2(re.y, im.y);
+}
+
 // x (FP64) += e (FP32 or FP64)
 __global__ void add_correction_kernel(int n3, double2* __restrict__ x, const void* __restrict__ e, int from_f32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -945,16 +994,13 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
   }
 
   int iters = 0, n_ru = 0, st_main = LQCD_OK;
-  // LQCD_DF64 iterates on (hi, lo) solutions and needs no reliable updates; they become FP64 after
+  // The solutions live as (hi, lo) FP32 pairs through the solve, the checks and the refinement
+  // (every mode but LQCD_FP64) and become FP64 at the end; LQCD_DF64 needs no reliable updates.
   const bool dfsolve = prec == LQCD_DF64;
-  double2* const* xs_run = dfsolve ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
+  double2* const* xs_run = w->xdfmode ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
   rc = solve_core(ctx, w->b64, xs_run, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, &iters, &n_ru,
                   &st_main);
   if (rc != LQCD_OK) return rc;
-  if (dfsolve) {
-    for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, w->xdf[k], w->xk[k], w->st));
-    ctx->launches += n;
-  }
   LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
   double bb = w->host_scal[0];
@@ -972,7 +1018,7 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
       rc = mrhs_prepare(ctx, prec, n, &rhs);
       if (rc != LQCD_OK) return rc;
     }
-    rc = true_residuals(ctx, w->b64, w->xk, shifts, all, bb, tres, rhs, f32);
+    rc = true_residuals(ctx, w->b64, xs_run, shifts, all, bb, tres, rhs, f32);
     if (rc != LQCD_OK) return rc;
     // Per-shift refinement, all shifts at once: (A + d_k) e_k = b - (A + d_k) x_k for every shift whose
     // true residual is above tol, each reduced by 0.75 tol / residual (a 25 % margin for the FP32
@@ -996,19 +1042,27 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
       void* const* es = mrhs_solutions(ctx);
       const int n3 = 3 * g.vh;
       for (int k : todo) {
-        add_correction_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->xk[k], es[k], f32);
+        if (w->xdfmode)
+          add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(w->xdf[k]),
+                                                                         static_cast<const float2*>(es[k]));
+        else
+          add_correction_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->xk[k], es[k], f32);
         ctx->launches += 1;
       }
       LQ_CUDA(cudaGetLastError());
       if (round == 0) refined = (int)todo.size();
       rounds_done = round + 1;
-      rc = true_residuals(ctx, w->b64, w->xk, shifts, todo, bb, tres, rhs, f32);
+      rc = true_residuals(ctx, w->b64, xs_run, shifts, todo, bb, tres, rhs, f32);
       if (rc != LQCD_OK) return rc;
       if (st2 == LQCD_ERR_NONFINITE) break;
     }
     if (status == LQCD_OK)
       for (int k = 0; k < n; ++k)
         if (!(tres[k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
+  }
+  if (w->xdfmode && bb != 0.0) {
+    for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, w->xdf[k], w->xk[k], w->st));
+    ctx->launches += n;
   }
   if (bb == 0.0) {
     for (int k = 0; k < n; ++k) {
