@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
     // q = a x - D in (x = the own-site vector, p of the solve), Re<x, q> in double-FP32
     float ds = 0.f, dc = 0.f;
     if (valid) {
-      const float2 asp = k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a);
+      const float2 asp = k.a_split ? make_float2(k.a_hi, k.a_lo)
+                                   : (k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a));
       const float ah = asp.x, al = asp.y;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -154,8 +155,9 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
   } else {
     float dsite = 0.f;
     if (valid) {
-      const double a64 = k.a_dev ? *k.a_dev : k.a;
-      const float ah = __double2float_rn(a64), al = __double2float_rn(a64 - (double)ah);
+      const float2 asp = k.a_split ? make_float2(k.a_hi, k.a_lo)
+                                   : (k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a));
+      const float ah = asp.x, al = asp.y;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const size_t o = (size_t)a * vh + i;

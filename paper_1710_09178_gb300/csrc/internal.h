@@ -156,6 +156,8 @@ struct DfArgs {
   const float2* b_lo = nullptr;
   const double* a_dev = nullptr;    // 4 m^2 + sigma read from device memory, else a
   const float2* a_devdf = nullptr;  // its (hi, lo) copy, read instead when set
+  float a_hi = 0.f, a_lo = 0.f;     // a split on the host, used when a_split is set
+  int a_split = 0;
   double a = 0;
   float2* r_out = nullptr;          // residual rounded to FP32
   double* dot_out = nullptr;        // |r|^2

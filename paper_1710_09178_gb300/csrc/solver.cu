@@ -736,6 +736,14 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
   r.b_lo = w->dfb_l;
   r.a = 4.0 * ctx->mass * ctx->mass + sigma;
   r.a_dev = a_dev;
+  if (a_dev == &w->sd->a_diag) {
+    r.a_devdf = &w->sd->a_diag_df;  // the reliable update's 4m^2 + sigma_0
+  } else if (!a_dev) {
+    const float ah = (float)r.a;
+    r.a_hi = ah;
+    r.a_lo = (float)(r.a - (double)ah);
+    r.a_split = 1;
+  }
   r.r_out = r_out;
   r.dot_out = dot;
   r.partials = w->partials;
