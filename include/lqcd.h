@@ -198,7 +198,7 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
  * 10-iteration window once one is due: after LQCD_OPT_RELIABLE_INTERVAL iterations, or earlier when
  * the iterated residual fell by LQCD_OPT_RELIABLE_DELTA (so that the FP32 drift stays small
  * against the residual it replaces). */
-#define LQCD_OPT_RELIABLE_INTERVAL 1 /* most iterations between FP64 reliable updates (mixed modes; default 100) */
+#define LQCD_OPT_RELIABLE_INTERVAL 1 /* most iterations between reliable updates (mixed modes; default 100) */
 #define LQCD_OPT_REFINE 2            /* 1 = refine every shift to the true residual (default), 0 = off */
 #define LQCD_OPT_BATCH 3             /* iterations per host-polled batch when graphs are off (default 20) */
 #define LQCD_OPT_USE_GRAPH 4         /* 1 = one CUDA graph per solve whose conditional while-node repeats a
@@ -212,7 +212,8 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
                                         back to 0 by itself where the driver refuses it), 0 = off */
 #define LQCD_OPT_DF_RESID 8          /* mixed modes: 1 = reliable updates and true-residual checks in
                                         double-FP32 arithmetic (FP32 hi/lo pairs, exact products, TwoSum
-                                        accumulation; ~48-bit, FP32 units only) (default), 0 = FP64 */
+                                        accumulation; ~48-bit, FP32 units only) and the solutions kept as
+                                        double-FP32 pairs during the solve (default), 0 = FP64 */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*
@@ -228,12 +229,15 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
  *                or NULL (then only y is produced); entries may not be NULL
  *   y_dev      : device complex128 [Vh][3] output or NULL
  *   tol        : requested relative residual; the call returns LQCD_OK only when
- *                the FP64 true residual |b - (A+d_k)x_k|/|b| <= tol for every k
+ *                the true residual |b - (A+d_k)x_k|/|b| <= tol for every k (computed in FP64
+ *                for LQCD_FP64, in double-FP32 (~48-bit; within ~1e-12 of the FP64 value at
+ *                1e-10) for the other modes unless LQCD_OPT_DF_RESID is 0)
  *   maxiter    : cap on base iterations (and on each refinement solve)
  *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12, LQCD_FP16FIX, LQCD_FP32_R8
  *                or LQCD_FP32_L16 (FP32 arithmetic with that link copy in the shifted CG,
- *                FP64 dot products and solution accumulation, reliable updates and final
- *                residuals in double-FP32 (LQCD_OPT_DF_RESID) or FP64; the refinement solves
+ *                FP64 dot products, solutions accumulated as double-FP32 pairs, reliable
+ *                updates and final residuals in double-FP32 (LQCD_OPT_DF_RESID) or FP64, the
+ *                solutions then in FP64 throughout; the refinement solves
  *                of all these modes use the FP32 12-real links), or LQCD_DF64 (every vector,
  *                the solutions and the arithmetic in double-FP32: no reliable updates, and the
  *                final check normally leaves nothing to refine)

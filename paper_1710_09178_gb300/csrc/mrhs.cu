@@ -1,6 +1,6 @@
 // mrhs.cu - many independent shifted CG solves sharing one operator:
 //     (A + sigma_j) e_j = r_j,   j = 1..m,   A = 4m^2 - D_eo D_oe,
-// used for the per-shift refinement of the shifted CG (each shift's FP64 true residual is the
+// used for the per-shift refinement of the shifted CG (each shift's true residual is the
 // right-hand side of its correction equation).  The systems advance in lock step; the
 // Dslash kernels load every link once per group of G systems and apply it to each of them
 // (multi-right-hand-side Dslash), so link traffic per system drops by G.  Every system has

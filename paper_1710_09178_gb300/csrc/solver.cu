@@ -1,5 +1,5 @@
 // solver.cu - shifted conjugate gradient on the GPU (Section 4, ref. [mcg]) with
-// mixed-precision storage, FP64 reliable updates and per-shift refinement.
+// mixed-precision storage, reliable updates and per-shift refinement.
 //
 // One base iteration is four kernels, all enqueued without host round trips:
 //   1. tmp = D_oe p                                          (dslash.cu)
@@ -955,8 +955,9 @@ __global__ void add_correction_kernel(int n3, double2* __restrict__ x, const voi
   x[i] = a;
 }
 
-// FP64 true residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts; when keep is not
-// null each residual is also stored in keep[k] (refinement precision) as a right-hand side.
+// True residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts (double-FP32 in the modes
+// that keep x_k as (hi, lo) pairs, FP64 otherwise); when keep is not null each residual is also
+// stored in keep[k] (refinement precision) as a right-hand side.
 static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts,
                           const std::vector<int>& ks, double bnorm2, double* out, void* const* keep, int keep_f32) {
   Workspace* w = ctx->ws;
