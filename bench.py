@@ -572,7 +572,10 @@ def main():
         t = tr[-1]
         traj = {"workload": "24^3x6, beta 5.4, m 0.025, 16 poles, Omelyan tau 1, 25 steps",
                 "ms_per_trajectory": t["event_ms"], "dH": t["dH"], "accepted": t["accepted"],
-                "solves": t["solves"], "iterations": t["iterations"]}
+                "solves": t["solves"], "iterations": t["iterations"],
+                "start": "the synthetic exp(i 0.5 H) field, far rougher than an equilibrium ensemble at beta 5.4: "
+                         "the MD energy error is large from it (it falls as step^2; acceptance over thermalised "
+                         "chains is tested on 4^4)"}
 
     # ---- CPU baseline: the oracle, bounded sample, scaled by the FP64 iteration count -------
     cpu = None
