@@ -106,6 +106,61 @@ __device__ __forceinline__ bool lane_writes(int sub, int c) {
   return c == sub;
 }
 
+// Output stage shared by the Dslash kernels: d = (D in)(x) of site i, written as the plain
+// output, the A-apply a * aux - d with Re<aux, out>, or the residual bvec - (a * aux - d) with
+// |out|^2; the sums are reduced over the grid by the last block (every thread of the block calls).
+template <typename T, typename V2, int TPS, int EPI>
+__device__ __forceinline__ void dslash_epilogue(const KArgs& k, const Vec3<T>& d, int i, int sub, bool valid,
+                                                int vh) {
+  V2* out = static_cast<V2*>(k.out);
+  T aval = (T)k.a;
+  if constexpr (EPI != (int)Epi::Plain) {
+    if (sizeof(T) == 4 && k.a_devf) aval = (T)*k.a_devf;
+    else if (k.a_dev) aval = (T)*k.a_dev;
+  }
+  T dsite = 0;  // this lane's share of the site's dot product, summed in T, then added in FP64
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!lane_writes<TPS>(sub, c)) continue;
+      size_t o = (size_t)c * vh + i;
+      if constexpr (EPI == (int)Epi::Plain) {
+        V2 w;
+        w.x = d.c[c].re;
+        w.y = d.c[c].im;
+        out[o] = w;
+      } else {
+        V2 ps = static_cast<const V2*>(k.aux)[o];
+        T qre = aval * ps.x - d.c[c].re;
+        T qim = aval * ps.y - d.c[c].im;
+        if constexpr (EPI == (int)Epi::AApply) {
+          dsite += ps.x * qre + ps.y * qim;
+        } else {
+          V2 bv = static_cast<const V2*>(k.bvec)[o];
+          qre = bv.x - qre;
+          qim = bv.y - qim;
+          dsite += qre * qre + qim * qim;
+        }
+        V2 w;
+        w.x = qre;
+        w.y = qim;
+        out[o] = w;
+      }
+    }
+  }
+  if constexpr (EPI != (int)Epi::Plain) {
+    double bs = block_sum_mixed(dsite);
+    if (publish_partial(k.partials, k.ticket, bs)) {
+      double tot = gather_partials(k.partials, k.ticket);
+      if (k.solver && EPI == (int)Epi::AApply) {
+        solver_alpha_step(k.solver, tot);
+      } else if (threadIdx.x == 0 && k.dot_out) {
+        *k.dot_out = tot;
+      }
+    }
+  }
+}
+
 template <int LF, int TPS, int EPI>
 __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   typedef typename LinkTraits<LF>::T T;
@@ -178,53 +233,7 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
     d.c[c] = cmake(re, im);
   }
 
-  V2* out = static_cast<V2*>(k.out);
-  T aval = (T)k.a;
-  if constexpr (EPI != (int)Epi::Plain) {
-    if (sizeof(T) == 4 && k.a_devf) aval = (T)*k.a_devf;
-    else if (k.a_dev) aval = (T)*k.a_dev;
-  }
-  T dsite = 0;  // this lane's share of the site's dot product, summed in T, then added in FP64
-  if (valid) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (!lane_writes<TPS>(sub, c)) continue;
-      size_t o = (size_t)c * vh + i;
-      if constexpr (EPI == (int)Epi::Plain) {
-        V2 w;
-        w.x = d.c[c].re;
-        w.y = d.c[c].im;
-        out[o] = w;
-      } else {
-        V2 ps = static_cast<const V2*>(k.aux)[o];
-        T qre = aval * ps.x - d.c[c].re;
-        T qim = aval * ps.y - d.c[c].im;
-        if constexpr (EPI == (int)Epi::AApply) {
-          dsite += ps.x * qre + ps.y * qim;
-        } else {
-          V2 bv = static_cast<const V2*>(k.bvec)[o];
-          qre = bv.x - qre;
-          qim = bv.y - qim;
-          dsite += qre * qre + qim * qim;
-        }
-        V2 w;
-        w.x = qre;
-        w.y = qim;
-        out[o] = w;
-      }
-    }
-  }
-  if constexpr (EPI != (int)Epi::Plain) {
-    double bs = block_sum_mixed(dsite);
-    if (publish_partial(k.partials, k.ticket, bs)) {
-      double tot = gather_partials(k.partials, k.ticket);
-      if (k.solver && EPI == (int)Epi::AApply) {
-        solver_alpha_step(k.solver, tot);
-      } else if (threadIdx.x == 0 && k.dot_out) {
-        *k.dot_out = tot;
-      }
-    }
-  }
+  dslash_epilogue<T, V2, TPS, EPI>(k, d, i, sub, valid, vh);
 }
 
 template <int LF, int TPS>
