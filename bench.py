@@ -11,10 +11,11 @@ the rational application.
 
 Printed JSON line (rank 0): value = ms per solve (mixed), plus the FP64 solve,
 the 12-real and 16-bit variants, the Dslash roofline (algorithmic bytes per
-launch over the CUDA-event time of back-to-back launches that rotate over eight
-gauge fields, so that every launch reads from HBM; the isolated launch after an
-L2 flush is reported beside it), the end-to-end number through the C ABI with
-host buffers, and the oracle timed on the host cores (cpu_baseline).
+launch over the CUDA-event time per launch of a CUDA graph of launches that
+rotate over eight gauge fields, so that every launch reads from HBM; the same
+launches from the host stream and the isolated launch after an L2 flush are
+reported beside it), the end-to-end number through the C ABI with host buffers,
+and the oracle timed on the host cores (cpu_baseline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -229,12 +230,12 @@ def time_dslash(lq, torch, ctx, prec_name, prec, reps, flush_buf):
 STREAM_FIELDS = 8  # 8 x 75.5 MB of FP32 links: each field is ~528 MB of traffic old when it is read again
 
 
-def make_stream_contexts(lq, torch, Ud, n):
+def make_stream_contexts(lq, torch, Ud, n, stream=None):
     """n contexts holding their own copies of the same gauge field (distinct buffers, so distinct
-    L2 lines), with one input and one output vector each."""
+    L2 lines), with one input and one output vector each, launching on `stream` (default: current)."""
     out = []
     for _ in range(n):
-        c = lq.Context(DIMS, MASS)
+        c = lq.Context(DIMS, MASS, stream=None if stream is None else stream.cuda_stream)
         c.set_gauge(Ud)
         vin, vout = c.new_vector(lq.FP32), c.new_vector(lq.FP32)
         vin.view(torch.float32).normal_()
@@ -245,8 +246,9 @@ def make_stream_contexts(lq, torch, Ud, n):
 def time_dslash_stream(lq, torch, sctx, prec, reps):
     """Average duration of back-to-back Dslash launches that rotate over the gauge fields of sctx.
     Between two reads of one field the other fields move 7 x 75.5 MB through L2 (129 MB), so every
-    launch streams its links and vectors from HBM, as the isolated launches after an L2 flush do,
-    but the launch latency and the ramp-up of one launch overlap the drain of the previous one."""
+    launch streams its links and vectors from HBM, as the isolated launches after an L2 flush do.
+    Each launch is one call through the C ABI from Python, so the host's per-call time shows up as
+    gaps between the kernels."""
     stream = torch.cuda.current_stream()
     n = len(sctx)
 
@@ -265,6 +267,45 @@ def time_dslash_stream(lq, torch, sctx, prec, reps):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def time_dslash_graph(lq, torch, Ud, prec, reps, n_fields=STREAM_FIELDS):
+    """As time_dslash_stream, with the reps launches captured in one CUDA graph (the way the
+    solver runs them): the host launch gaps between the kernels are gone and what is left is the
+    kernel's own duration from HBM.  Returns ms per launch (median of 5 replays), or None where
+    the capture is refused."""
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    sctx = make_stream_contexts(lq, torch, Ud, n_fields, stream=s)
+    n = len(sctx)
+    try:
+        with torch.cuda.stream(s):
+            for i in range(2 * n):
+                c, vin, vout = sctx[i % n]
+                lq.dslash_eo(c, vout, vin, (i // n) & 1, prec)
+            s.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+                for i in range(reps):
+                    c, vin, vout = sctx[i % n]
+                    lq.dslash_eo(c, vout, vin, (i // n) & 1, prec)
+            graph.replay()
+            ms = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                graph.replay()
+                e1.record(s)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1) / reps)
+        return statistics.median(ms)
+    except (RuntimeError, lq.LqcdError):
+        return None
+    finally:
+        torch.cuda.synchronize()
+        for c, _, _ in sctx:
+            c.close()
 
 
 def cpu_baseline_oracle(U, b, coeffs, iters_per_solve, sample_iters):
@@ -421,7 +462,8 @@ def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True
 
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
-    `dslash_stream` = the roofline's back-to-back launches over 8 gauge fields (4 rotations),
+    `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
+    then 6 replays of the graph: 592 launches),
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch."""
     import torch
 
@@ -434,13 +476,9 @@ def run_profile_target(kind, prec_name):
     prec = lq.PRECISIONS[prec_name]
     ctx = lq.Context(DIMS, MASS)
     ctx.set_gauge(torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda())
-    if kind == "dslash_stream":
-        sctx = make_stream_contexts(lq, torch, torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda(),
-                                    STREAM_FIELDS)
-        time_dslash_stream(lq, torch, sctx, prec, 2 * STREAM_FIELDS)
-        torch.cuda.synchronize()
-        for c, _, _ in sctx:
-            c.close()
+    if kind == "dslash_graph":
+        ms = time_dslash_graph(lq, torch, torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda(), prec, 96)
+        print(json.dumps({"profile": "dslash_graph", "ms_per_launch": ms}))
     elif kind == "dslash":
         vin = ctx.new_vector(prec)
         vout = ctx.new_vector(prec)
@@ -468,7 +506,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
-    ap.add_argument("--profile", choices=["dslash", "dslash_stream", "solve"], help="run a small fixed workload for ncu and exit")
+    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve"], help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
@@ -593,18 +631,25 @@ def main():
     for c, _, _ in sctx:
         c.close()
     del sctx
-    s_gbs = DSLASH_BYTES_PER_SITE["fp32"] * vh / (s_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": s_gbs, "peak": peak, "unit": "GB/s",
-                "frac": s_gbs / peak, "traffic": traffic, "kernel": "dslash_kernel<L32> (FP32)",
+    g_ms = time_dslash_graph(lq, torch, Ud, lq.FP32, 96)
+    bpl = DSLASH_BYTES_PER_SITE["fp32"] * vh
+    streamed = {"ms": s_ms, "achieved": bpl / (s_ms * 1e-3) / 1e9, "frac": bpl / (s_ms * 1e-3) / 1e9 / peak,
+                "timing": f"96 back-to-back stream launches rotating over {STREAM_FIELDS} gauge fields "
+                          f"({STREAM_FIELDS} x 75.5 MB > L2: every launch reads from HBM), median of 5"}
+    isolated = {"ms": d32["ms"], "achieved": d32["algorithmic_GBps"], "frac": d32["algorithmic_GBps"] / peak,
+                "timing": "one launch after an L2 flush, launch latency included, mean of 40"}
+    if g_ms is not None:
+        r_ms, r_timing = g_ms, (f"the same 96 launches over {STREAM_FIELDS} gauge fields captured in one CUDA "
+                                f"graph (as in the solver), median of 5 replays")
+    else:
+        r_ms, r_timing = s_ms, streamed["timing"]
+    r_gbs = bpl / (r_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": r_gbs, "peak": peak, "unit": "GB/s",
+                "frac": r_gbs / peak, "traffic": traffic, "kernel": "dslash_kernel<L32> (FP32)",
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "bytes_per_launch": DSLASH_BYTES_PER_SITE["fp32"] * vh,
-                "ms_per_launch": s_ms,
-                "timing": f"96 back-to-back launches rotating over {STREAM_FIELDS} gauge fields "
-                          f"({STREAM_FIELDS} x 75.5 MB > L2, every launch reads from HBM), median of 5",
-                "isolated_launch": {"ms": d32["ms"], "achieved": d32["algorithmic_GBps"],
-                                    "frac": d32["algorithmic_GBps"] / peak,
-                                    "timing": "one launch after an L2 flush, launch latency included, mean of 40"}}
+                "bytes_per_launch": bpl, "ms_per_launch": r_ms, "timing": r_timing,
+                "stream_launches": streamed, "isolated_launch": isolated}
 
     # ---- end to end through the C ABI with host buffers ------------------------------------
     c0, res, poles, _ = coeffs
@@ -660,7 +705,7 @@ def main():
                    "precision": "FP32 links+Krylov vectors, FP64 dots and x_k, double-FP32 (FP32 hi/lo) reliable updates and true residuals, 12-real FP32 links in the refinement",
                    "gauge": "exp(i 0.5 H) SU(3), seed 5", "source": "complex Gaussian, seed 6",
                    "l2": "flushed (256 MB written, then another 256 MB read) between timed steps and before every "
-                         "isolated Dslash launch; the back-to-back Dslash launches of the roofline rotate over "
+                         "isolated Dslash launch; the graph-launched Dslash of the roofline rotates over "
                          "8 gauge fields (604 MB of links > L2)",
                    "parallelism": f"replicas x{world}"},
         "mixed": {"iterations": last["iterations"], "shift_iterations": last["shift_iterations"],
