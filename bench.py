@@ -321,6 +321,25 @@ def cpu_baseline_oracle(U, b, coeffs, iters_per_solve, sample_iters):
     return per_iter_ms * iters_per_solve, per_iter_ms, dt
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def oracle_iterations():
     p = os.path.join(ROOT, "tests", "golden", "oracle_iterations_32c8.json")
     if os.path.exists(p):
@@ -359,7 +378,7 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES, "tol": TOL,
                    "precision": "fp64 oracle (numpy)"},
-        "cpu_baseline": {"value": value, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "ms/solve", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"{sample} shifted-CG iterations per step at 32^3x8, 16 shifts, scaled by the "
                                    f"{iters} iterations the oracle needs for a full solve (tests/golden)"},
         "e2e": {"value": value, "unit": "ms/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -611,6 +630,16 @@ def main():
                            "reliable_updates": sts[-1]["reliable_updates"],
                            "refine_iterations": sts[-1]["refine_iterations"],
                            "max_true_residual": max(sts[-1]["true_residual"])}
+        # the heatbath's x^{1/4} (residues c_k < 0, c0 > 0) on the same interval, mixed and FP64
+        lo, hi = 4 * MASS * MASS, 16 + 4 * MASS * MASS
+        q_coeffs = lq.rational_coeffs(0.25, lo, hi, NPOLES)
+        for name, prec in (("fp32_x^1/4", lq.FP32), ("fp64_x^1/4", lq.FP64)):
+            tms, sts = time_solves(lq, torch, ctx, bd, xs, y, q_coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
+            extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
+                           "reliable_updates": sts[-1]["reliable_updates"],
+                           "refine_iterations": sts[-1]["refine_iterations"],
+                           "max_true_residual": max(sts[-1]["true_residual"]),
+                           "approximation_error": q_coeffs[3]}
 
     # ---- Dslash roofline (the kernel that dominates the solve) ------------------------------
     peak, peak_kind = read_peaks()
@@ -690,7 +719,7 @@ def main():
         iters_fp64 = extra.get("fp64", {}).get("iterations") or oracle_iterations() or stats[-1]["iterations"]
         sample = env_int("LQCD_CPU_SAMPLE_ITERS", 12)
         val, per_iter, dt = cpu_baseline_oracle(U, b, coeffs, iters_fp64, sample)
-        cpu = {"value": val, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+        cpu = {"value": val, "unit": "ms/solve", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{sample} iterations of the oracle's shifted CG at 32^3x8 with 16 shifts ({dt:.1f} s, "
                          f"{per_iter:.0f} ms/iteration, numpy single thread), scaled by {iters_fp64} iterations "
                          f"per FP64 solve"}
