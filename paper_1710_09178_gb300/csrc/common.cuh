@@ -588,6 +588,12 @@ __device__ __forceinline__ void df_add(float& s, float& c, float bh, float bl) {
   c = __fadd_rn(c, __fadd_rn(err, bl));
 }
 
+// FP64 -> (hi, lo) FP32 pair: hi = fl32(a), lo = fl32(a - hi)
+__device__ __forceinline__ float2 split_hi_lo(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+
 // (hi, lo) with hi = fl32(s + c) (Fast2Sum: |s| >= |c| for an accumulated correction)
 __device__ __forceinline__ float2 df_norm(float s, float c) {
   const float h = __fadd_rn(s, c);
@@ -670,6 +676,52 @@ __device__ __forceinline__ bool publish_partial(double* partials, unsigned* tick
   }
   __syncthreads();
   return last;
+}
+
+// One warp: the sum of n double-FP32 partials p[0..n) in a fixed order (each lane accumulates
+// p[lane], p[lane + 32], ... with TwoSum, then a shuffle tree), on the FP32 pipes.  The value is
+// that of lane 0; the other lanes may differ in the last bits.
+__device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f, c = 0.f;
+  for (int b = lane; b < n; b += 32) {
+    const float2 x = __ldcg(p + b);
+    df_add(s, c, x.x, x.y);
+  }
+  float2 v = df_norm(s, c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v.x, o), ol = __shfl_xor_sync(0xffffffffu, v.y, o);
+    float s2 = v.x, c2 = v.y;
+    df_add(s2, c2, oh, ol);
+    v = df_norm(s2, c2);
+  }
+  return (double)v.x + (double)v.y;
+}
+
+// Every block of the kernel that follows the one that wrote the n partials (one per block, no
+// ticket): warp 0 sums them in a fixed order, and thread 0 forms *x / sum (SUM_OVER_X false) or
+// sum / *x (true).  The pair (sum, ratio) reaches every thread through shared memory, the same
+// bits in every block.  The FP64 work stays in one warp per block (GB300's FP64 pipe is 1/64 of
+// the FP32 rate).
+// DF: the partials are double-FP32 pairs (hi, lo) in the 8 bytes of each entry, added on the
+// FP32 pipes (warp_sum_df; the FP32 solves), else FP64 values added in FP64.
+template <bool SUM_OVER_X, bool DF>
+__device__ __forceinline__ double2 partials_ratio(const double* partials, int n, const double* x) {
+  __shared__ double2 res;
+  if (threadIdx.x < 32) {
+    double v;
+    if constexpr (DF) {
+      v = warp_sum_df(reinterpret_cast<const float2*>(partials), n);
+    } else {
+      v = 0.0;
+      for (int b = threadIdx.x; b < n; b += 32) v += __ldcg(partials + b);
+      v = warp_sum(v);
+    }
+    if (threadIdx.x == 0) res = make_double2(v, SUM_OVER_X ? v / *x : *x / v);
+  }
+  __syncthreads();
+  return res;
 }
 
 // In the last block: the sum of all partials in index order (identical in every thread).

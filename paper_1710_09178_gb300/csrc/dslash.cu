@@ -1,7 +1,8 @@
 // dslash.cu - the half-lattice staggered hopping operator (Section 3.2):
 //   out(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) in(x+mu) - U_mu(x-mu)^dagger in(x-mu)]
 // for every x of the output parity, with optional fused epilogues:
-//   AApply : out = a * aux - D in, and the FP64 sum Re<aux, out>   (one half of A = 4m^2 - D_eo D_oe)
+//   AApply : out = a * aux - D in, and the FP64 sum Re<aux, out>   (one half of A = 4m^2 - D_eo D_oe);
+//            without a ticket the sum stays as per-block partials for the next kernel
 //   Resid  : out = bvec - (a * aux - D in), and the FP64 sum |out|^2 (true residual)
 //
 // Bandwidth-bound gather kernel: each output site reads 8 links (all links once
@@ -13,7 +14,6 @@
 
 #include "common.cuh"
 #include "internal.h"
-#include "solver_dev.cuh"
 
 namespace lqcd {
 
@@ -29,7 +29,6 @@ struct KArgs {
   const float* a_devf;
   int out_parity;
   double* dot_out;
-  SolverDev* solver;
   const int* done;
   double* partials;
   unsigned* ticket;
@@ -150,13 +149,16 @@ __device__ __forceinline__ void dslash_epilogue(const KArgs& k, const Vec3<T>& d
   }
   if constexpr (EPI != (int)Epi::Plain) {
     double bs = block_sum_mixed(dsite);
+    if (!k.ticket) {  // the next kernel sums the per-block partials itself (FP32: as (hi, lo) pairs)
+      if (threadIdx.x == 0) {
+        if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(k.partials)[blockIdx.x] = split_hi_lo(bs);
+        else k.partials[blockIdx.x] = bs;
+      }
+      return;
+    }
     if (publish_partial(k.partials, k.ticket, bs)) {
       double tot = gather_partials(k.partials, k.ticket);
-      if (k.solver && EPI == (int)Epi::AApply) {
-        solver_alpha_step(k.solver, tot);
-      } else if (threadIdx.x == 0 && k.dot_out) {
-        *k.dot_out = tot;
-      }
+      if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
     }
   }
 }
@@ -261,8 +263,9 @@ static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cu
 
 static int default_tps(int) { return 1; }  // fastest on GB300 at 16^3x8 and 32^3x8 (sweep over 1, 2, 4, 8)
 
+// blocks of one Dslash launch (= partials it writes): the FP64 kernel always runs 1 thread per site
 int dslash_grid_blocks(const Geom& g, int prec, int tps) {
-  if (tps <= 0) tps = default_tps(prec);
+  if (tps <= 0 || prec == LQCD_FP64) tps = default_tps(prec);
   long long threads = (long long)g.vh * tps;
   return (int)((threads + 127) / 128);
 }
@@ -278,7 +281,6 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
   k.a_devf = a.a_devf;
   k.out_parity = a.out_parity;
   k.dot_out = a.dot_out;
-  k.solver = a.solver;
   k.done = a.done;
   k.partials = a.partials;
   k.ticket = a.ticket;

@@ -24,6 +24,8 @@ constexpr int kWindow = 10;  // iterations folded into one update of x_k, p_k
 
 struct SolverDev {
   double rr;       // |r|^2 of the current base residual
+  double rr_b;     // copy of rr taken by the alpha step: the p-update kernel forms beta from it while
+                   // its scalar block overwrites rr
   double bb;       // |b|^2
   double stop2;    // tol^2 |b|^2: shift k stops when zeta_k^2 |r|^2 <= stop2
   double alpha, alpha_prev, beta, beta_prev;
@@ -133,10 +135,9 @@ struct DslashArgs {
   const void* aux = nullptr;
   const void* bvec = nullptr;
   double* dot_out = nullptr;     // where the reduced scalar goes (AApply without solver, Resid)
-  SolverDev* solver = nullptr;   // AApply inside a solve: last block runs the alpha step
   const int* done = nullptr;     // if non-null and *done, the kernel returns at entry
-  double* partials = nullptr;
-  unsigned* ticket = nullptr;
+  double* partials = nullptr;     // one per block
+  unsigned* ticket = nullptr;     // null: the sum is left as per-block partials (the solver's A-apply)
   bool pdl = false;              // programmatic dependent launch (inside captured solve graphs)
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);

@@ -59,6 +59,25 @@ struct V2Of<double> {
   typedef double2 type;
 };
 
+// Per-block partials of the FP32 solves are stored as double-FP32 pairs in the 8 bytes of
+// partials[idx]: the last block then adds up to 16 x 1024 of them per kernel on the FP32 pipes
+// (warp_sum_df), which in FP64 took microseconds on GB300's narrow FP64 units.  The FP64 solves
+// keep FP64 partials and sums.
+template <typename T>
+__device__ __forceinline__ void store_partial_m(double* partials, size_t idx, double v) {
+  if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(partials)[idx] = split_hi_lo(v);
+  else partials[idx] = v;
+}
+
+// One warp: the sum of partials[off .. off + n) in a fixed order (value of lane 0)
+template <typename T>
+__device__ __forceinline__ double warp_sum_partials(const double* partials, size_t off, int n) {
+  if constexpr (sizeof(T) == 4) return warp_sum_df(reinterpret_cast<const float2*>(partials) + off, n);
+  double v = 0.0;
+  for (int b = threadIdx.x & 31; b < n; b += 32) v += __ldcg(partials + off + b);
+  return warp_sum(v);
+}
+
 // acc -= M^dagger v
 template <typename T>
 __device__ __forceinline__ void mdv_sub(Vec3<T>& out, const Mat3<T>& M, const Vec3<T>& v) {
@@ -152,7 +171,7 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
     }
     double bsum[kMrhsGroup];
     block_sum_multi(d, bsum);
-    if (threadIdx.x < ng) partials[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = bsum[threadIdx.x];
+    if (threadIdx.x < ng) store_partial_m<T>(partials, (size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x, bsum[threadIdx.x]);
     // last block over the whole grid (all groups): alpha_j = (r_j, r_j) / (p_j, q_j)
     __shared__ bool last;
     __syncthreads();
@@ -167,9 +186,7 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
       // one warp per system: strided partial sums in a fixed order, then a fixed shuffle tree
       const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
       for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
-        double v = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
-        v = warp_sum(v);
+        const double v = warp_sum_partials<T>(partials, (size_t)pos * gridDim.x, gridDim.x);
         if (lane == 0) {
           int sj = md->list[pos];
           double alpha = md->rr[sj] / v;
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
   {
     double bsum[kMrhsGroup];
     block_sum_multi(d, bsum);
-    if (threadIdx.x < ng) partials[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = bsum[threadIdx.x];
+    if (threadIdx.x < ng) store_partial_m<T>(partials, (size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x, bsum[threadIdx.x]);
   }
   __shared__ bool last;
   __syncthreads();
@@ -241,9 +258,7 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
   __shared__ int keep[kMrhsMax];
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
-    double v = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(partials + (size_t)pos * gridDim.x + b);
-    v = warp_sum(v);
+    const double v = warp_sum_partials<T>(partials, (size_t)pos * gridDim.x, gridDim.x);
     if (lane == 0) {
       int sj = md->list[pos];
       double beta = v / md->rr[sj];

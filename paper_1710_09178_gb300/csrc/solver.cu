@@ -3,9 +3,11 @@
 //
 // One base iteration is four kernels, all enqueued without host round trips:
 //   1. tmp = D_oe p                                          (dslash.cu)
-//   2. q = (4m^2 + sigma_0) p - D_eo tmp, (p, q) -> alpha step (dslash.cu epilogue + solver_dev.cuh)
-//   3. r -= alpha q, R[m] = r, (r, r) -> beta step           (r_update_kernel)
-//   4. p = r + beta p                                        (p_update_kernel)
+//   2. q = (4m^2 + sigma_0) p - D_eo tmp, per-block partials of (p, q)   (dslash.cu epilogue)
+//   3. alpha from those partials, r -= alpha q, R[m] = r, partials of (r, r);
+//      an extra block runs the alpha step (solver_dev.cuh)               (r_update_kernel)
+//   4. beta from those partials, p = r + beta p; an extra block runs the
+//      beta step                                                        (p_update_kernel)
 // Every kWindow iterations the window kernel applies the pending x_k / p_k
 // updates of all shifts at once (flush_kernel): each shift vector is read and
 // written once per window instead of once per iteration, which is what makes
@@ -106,25 +108,47 @@ struct RUpdArgs {
   void* ring;  // kWindow slots, slot stride in bytes
   size_t slot_bytes;
   SolverDev* sd;
-  double* partials;
-  unsigned* ticket;
+  const double* pq_partials;  // per-block partials of Re<p, q> left by the A-apply
+  int n_pq;
+  double* rr_partials;  // this kernel's per-block partials of |r|^2
 };
 
-// r -= alpha q; R[m] = r; |r|^2 -> beta step
+// The scalar steps run in one extra block appended to the update kernels (blockIdx.x == nb): it
+// sums the previous kernel's partials like every other block and runs the step while the other
+// blocks stream their sites, so neither the A-apply nor the r update ends with a last-block tail.
+// Every block derives alpha (beta) from the same partials in the same order, so all blocks use
+// the bits the step stores.
+__device__ __forceinline__ bool done_now(const SolverDev* sd) {
+  // the scalar block of the running kernel may set the flag concurrently; either value is fine
+  return *reinterpret_cast<const volatile int*>(&sd->done) != 0;
+}
+
+// r -= alpha q; R[m] = r; |r|^2 partials.  Scalar block: the alpha step.
 template <typename T, int SF>
-__global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
+__global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, RUpdArgs a) {
   typedef typename KTraits<T>::V2 V2;
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
-  if (sd->done) return;
+  if (done_now(sd)) return;
   const int m = sd->m;
-  const T alpha = sizeof(T) == 4 ? (T)sd->alpha_f : (T)sd->alpha;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool scalar_block = blockIdx.x == gridDim.x - 1;
+  const bool mine = !scalar_block && i < g.vh && m < kWindow;
+  Vec3<T> r, q;
+  if (mine) {  // issued before the partials are summed: they do not depend on alpha
+    r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
+    q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
+  }
+  // (Re<p, q>, |r|^2 / Re<p, q>)
+  const double2 pq_alpha = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, &sd->rr);
+  if (scalar_block) {
+    solver_alpha_step(sd, pq_alpha.x);
+    return;
+  }
+  const T alpha = sizeof(T) == 4 ? (T)(float)pq_alpha.y : (T)pq_alpha.y;
   T loc = 0;
-  if (i < g.vh && m < kWindow) {
-    Vec3<T> r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
-    Vec3<T> q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
+  if (mine) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       r.c[c].re = fma(-alpha, q.c[c].re, r.c[c].re);
@@ -134,28 +158,52 @@ __global__ void __launch_bounds__(256) r_update_kernel(Geom g, RUpdArgs a) {
     store_s<SF, T>(static_cast<char*>(a.ring) + m * a.slot_bytes, i, g.vh, r);
     loc = site_norm2(r);
   }
-  double bs = block_sum_mixed(loc);
-  if (publish_partial(a.partials, a.ticket, bs)) {
-    double rr = gather_partials(a.partials, a.ticket);
-    solver_beta_step(sd, rr);
+  const double bs = block_sum_mixed(loc);
+  if (threadIdx.x == 0) {
+    if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(a.rr_partials)[blockIdx.x] = split_hi_lo(bs);
+    else a.rr_partials[blockIdx.x] = bs;
   }
 }
 
-// p = r + beta p
+struct PUpdArgs {
+  const void* r;
+  void* p;
+  SolverDev* sd;
+  const double* rr_partials;  // per-block partials of |r|^2 left by the r update
+  int n_rr;
+};
+
+// p = r + beta p, one site per thread.  Scalar block: the beta step (stopping tests, window
+// coefficients, reliable-update decision, done flag).
 template <typename T>
-__global__ void __launch_bounds__(256) p_update_kernel(Geom g, const void* r, void* p, const SolverDev* sd) {
+__global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, PUpdArgs a) {
   typedef typename KTraits<T>::V2 V2;
+  SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
-  if (sd->done) return;
-  const T beta = sizeof(T) == 4 ? (T)sd->beta_f : (T)sd->beta;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * g.vh) return;
-  V2 rv = static_cast<const V2*>(r)[i];
-  V2 pv = static_cast<V2*>(p)[i];
-  pv.x = fma(beta, pv.x, rv.x);
-  pv.y = fma(beta, pv.y, rv.y);
-  static_cast<V2*>(p)[i] = pv;
+  if (done_now(sd)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool scalar_block = blockIdx.x == gridDim.x - 1;
+  const bool mine = !scalar_block && i < g.vh;
+  Vec3<T> r, p;
+  if (mine) {
+    r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
+    p = load_vec(static_cast<const V2*>(a.p), i, g.vh);
+  }
+  // (|r_new|^2, |r_new|^2 / |r|^2)
+  const double2 rr_beta = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, &sd->rr_b);
+  if (scalar_block) {
+    solver_beta_step(sd, rr_beta.x);
+    return;
+  }
+  if (!mine) return;
+  const T beta = sizeof(T) == 4 ? (T)(float)rr_beta.y : (T)rr_beta.y;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    p.c[c].re = fma(beta, p.c[c].re, r.c[c].re);
+    p.c[c].im = fma(beta, p.c[c].im, r.c[c].im);
+  }
+  store_vec(static_cast<V2*>(a.p), i, g.vh, p);
 }
 
 struct FlushArgs {
@@ -390,6 +438,7 @@ struct Workspace {
   int shift_iters_host = 0;
   double* host_scal = nullptr;         // pinned
   double* partials = nullptr;
+  double* partials_b = nullptr;  // second half of the partials allocation (r update -> p update)
   unsigned* tickets = nullptr;
   std::map<std::tuple<const void*, const void*, int, int>, cudaGraphExec_t> graphs;
   std::map<std::tuple<const void*, const void*, int, int>, int> graph_nodes;
@@ -488,7 +537,8 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   LQ_CUDA(cudaMalloc(&w->ru_count, sizeof(int)));
   // one partial per block of the widest reduction kernel
   int nparts = std::max(dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8), (int)((vh + 127) / 128)) + 64;
-  LQ_CUDA(cudaMalloc(&w->partials, sizeof(double) * nparts));
+  LQ_CUDA(cudaMalloc(&w->partials, 2 * sizeof(double) * nparts));
+  w->partials_b = w->partials + nparts;
   LQ_CUDA(cudaMalloc(&w->tickets, sizeof(unsigned) * 16));
   LQ_CUDA(cudaMemsetAsync(w->tickets, 0, sizeof(unsigned) * 16, w->st));
   LQ_CUDA(cudaMallocHost(&w->host_status, sizeof(StatusWords) * 2));
@@ -539,32 +589,35 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   d2.aux = w->p;
   d2.a_dev = &w->sd->a_diag;  // 4 m^2 + sigma_0 of the running solve
   d2.a_devf = &w->sd->a_diag_f;
-  d2.solver = w->sd;
-  d2.partials = w->partials;
-  d2.ticket = w->tickets + 0;
+  d2.partials = w->partials;  // no ticket: the r update sums the partials and runs the alpha step
   e = launch_dslash(L.g, ctx->gauge, d2, st, &L.nlaunch);
   if (e != cudaSuccess) return e;
+  const int nb = (L.g.vh + 255) / 256;  // streaming blocks; one more runs the scalar step
   RUpdArgs ra;
   ra.r = w->r;
   ra.q = w->q;
   ra.ring = w->ring;
   ra.slot_bytes = w->sbytes;
   ra.sd = w->sd;
-  ra.partials = w->partials;
-  ra.ticket = w->tickets + 1;
-  int nb = (L.g.vh + 255) / 256;
-  int nb3 = (3 * L.g.vh + 255) / 256;
+  ra.pq_partials = w->partials;
+  ra.n_pq = dslash_grid_blocks(L.g, d2.prec, d2.tps);
+  ra.rr_partials = w->partials_b;
+  PUpdArgs pa;
+  pa.r = w->r;
+  pa.p = w->p;
+  pa.sd = w->sd;
+  pa.rr_partials = w->partials_b;
+  pa.n_rr = nb;
   const bool pr = L.next_pdl(), pp = L.next_pdl();
-  const void* rc = w->r;
   if (w->kprec == LQCD_FP64) {
-    e = launch_k(pr, r_update_kernel<double, kS64>, dim3(nb), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
+    e = launch_k(pr, r_update_kernel<double, kS64>, dim3(nb + 1), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, dim3(nb + 1), dim3(256), st, L.g, pa);
   } else if (w->sfmt == kS16) {
-    e = launch_k(pr, r_update_kernel<float, kS16>, dim3(nb), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
+    e = launch_k(pr, r_update_kernel<float, kS16>, dim3(nb + 1), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb + 1), dim3(256), st, L.g, pa);
   } else {
-    e = launch_k(pr, r_update_kernel<float, kS32>, dim3(nb), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb3), dim3(256), st, L.g, rc, w->p, (const SolverDev*)w->sd);
+    e = launch_k(pr, r_update_kernel<float, kS32>, dim3(nb + 1), dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb + 1), dim3(256), st, L.g, pa);
   }
   L.nlaunch += 2;
   return e;

@@ -15,14 +15,10 @@
 // residuals of the window; the window kernel applies them every kWindow iterations.
 #pragma once
 
+#include "common.cuh"
 #include "internal.h"
 
 namespace lqcd {
-
-__device__ __forceinline__ float2 split_hi_lo(double a) {
-  const float h = __double2float_rn(a);
-  return make_float2(h, __double2float_rn(a - (double)h));
-}
 
 // The steps run in one warp of the last block; every lane k < n owns shift k.  All loads of a
 // lane are issued before any store (the state lives in global memory and a chain of dependent
@@ -108,6 +104,7 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
   const bool ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
   if (k == 0) {
     sd->pq = pq;
+    sd->rr_b = rr;
     sd->alpha = alpha;
     sd->alpha_f = (float)alpha;
     sd->alpha_df = split_hi_lo(alpha);
