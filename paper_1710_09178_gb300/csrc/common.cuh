@@ -700,15 +700,21 @@ __device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
 }
 
 // Every block of the kernel that follows the one that wrote the n partials (one per block, no
-// ticket): warp 0 sums them in a fixed order, and thread 0 forms *x / sum (SUM_OVER_X false) or
-// sum / *x (true).  The pair (sum, ratio) reaches every thread through shared memory, the same
-// bits in every block.  The FP64 work stays in one warp per block (GB300's FP64 pipe is 1/64 of
-// the FP32 rate).
-// DF: the partials are double-FP32 pairs (hi, lo) in the 8 bytes of each entry, added on the
-// FP32 pipes (warp_sum_df; the FP32 solves), else FP64 values added in FP64.
+// ticket): warp 0 sums them in a fixed order, and thread 0 forms ratio = *x / sum (SUM_OVER_X
+// false) or sum / *x (true) with its FP32 and (hi, lo) copies.  The result reaches every thread
+// through shared memory, the same bits in every block; the FP64 work stays in one warp per block
+// (GB300's FP64 pipe is 1/64 of the FP32 rate).  DF: the partials are double-FP32 pairs (hi, lo)
+// in the 8 bytes of each entry, added on the FP32 pipes (warp_sum_df; the FP32 and double-FP32
+// solves), else FP64 values added in FP64.
+struct PartialsRatio {
+  double sum, ratio;
+  float ratio_f;
+  float2 ratio_df;
+};
+
 template <bool SUM_OVER_X, bool DF>
-__device__ __forceinline__ double2 partials_ratio(const double* partials, int n, const double* x) {
-  __shared__ double2 res;
+__device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, int n, const double* x) {
+  __shared__ PartialsRatio res;
   if (threadIdx.x < 32) {
     double v;
     if constexpr (DF) {
@@ -718,10 +724,23 @@ __device__ __forceinline__ double2 partials_ratio(const double* partials, int n,
       for (int b = threadIdx.x; b < n; b += 32) v += __ldcg(partials + b);
       v = warp_sum(v);
     }
-    if (threadIdx.x == 0) res = make_double2(v, SUM_OVER_X ? v / *x : *x / v);
+    if (threadIdx.x == 0) {
+      const double q = SUM_OVER_X ? v / *x : *x / v;
+      res.sum = v;
+      res.ratio = q;
+      res.ratio_df = split_hi_lo(q);
+      res.ratio_f = res.ratio_df.x;
+    }
   }
   __syncthreads();
   return res;
+}
+
+// A block's FP64 sum v as partial idx: a double-FP32 pair in the entry's 8 bytes (DF) or FP64
+template <bool DF>
+__device__ __forceinline__ void store_partial(double* partials, size_t idx, double v) {
+  if constexpr (DF) reinterpret_cast<float2*>(partials)[idx] = split_hi_lo(v);
+  else partials[idx] = v;
 }
 
 // In the last block: the sum of all partials in index order (identical in every thread).

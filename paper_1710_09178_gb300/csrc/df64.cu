@@ -147,10 +147,13 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
       }
     }
     const double bs = block_sum_df(ds, dc);
+    if (!k.ticket) {  // inside the solve: the r update sums the (hi, lo) partials itself
+      if (threadIdx.x == 0) store_partial<true>(k.partials, blockIdx.x, bs);
+      return;
+    }
     if (publish_partial(k.partials, k.ticket, bs)) {
       const double tot = gather_partials(k.partials, k.ticket);
-      if (k.solver) solver_alpha_step(k.solver, tot);
-      else if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
+      if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
     }
   } else {
     float dsite = 0.f;
@@ -187,8 +190,10 @@ cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2*
   return launch_k(pdl, split_df_kernel, dim3((n3 + 255) / 256), dim3(256), st, n3, x, hi, lo, done);
 }
 
+int df_dslash_grid_blocks(const Geom& g) { return (g.vh + 127) / 128; }
+
 cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl) {
-  const unsigned nb = (unsigned)((g.vh + 127) / 128);
+  const unsigned nb = (unsigned)df_dslash_grid_blocks(g);
   if (epi == 2) return launch_k(pdl, df_dslash_kernel<2>, dim3(nb), dim3(128), st, g, a);
   if (epi == 1) return launch_k(pdl, df_dslash_kernel<1>, dim3(nb), dim3(128), st, g, a);
   return launch_k(pdl, df_dslash_kernel<0>, dim3(nb), dim3(128), st, g, a);
@@ -223,18 +228,26 @@ __global__ void __launch_bounds__(256) df_init_kernel(Geom g, const double2* __r
   if (publish_partial(partials, ticket, bs)) init_scalars(sd, ip, gather_partials(partials, ticket));
 }
 
-// r -= alpha q; R[m] = r; |r|^2 (double-FP32 per warp, FP64 across warps) -> beta step
-__global__ void __launch_bounds__(256) df_r_update_kernel(Geom g, DfUpdArgs a) {
+// r -= alpha q; R[m] = r; (hi, lo) partials of |r|^2.  alpha comes from the A-apply's partials
+// (every block, the same bits); one extra block runs the alpha step.
+__global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, DfUpdArgs a) {
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
-  if (sd->done) return;
+  if (*reinterpret_cast<const volatile int*>(&sd->done)) return;  // the scalar block may set it meanwhile
   const int m = sd->m;
   const int vh = g.vh;
-  const float2 al = sd->alpha_df;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool scalar_block = blockIdx.x == gridDim.x - 1;
+  const bool mine = !scalar_block && i < vh && m < kWindow;
+  const PartialsRatio pa = partials_ratio<false, true>(a.pq_partials, a.n_pq, &sd->rr);
+  if (scalar_block) {
+    solver_alpha_step(sd, pa.sum);
+    return;
+  }
+  const float2 al = pa.ratio_df;
   float ls = 0.f, lc = 0.f;
-  if (i < vh && m < kWindow) {
+  if (mine) {
     float2* slot = reinterpret_cast<float2*>(static_cast<char*>(a.ring) + m * a.slot_bytes);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -254,25 +267,37 @@ __global__ void __launch_bounds__(256) df_r_update_kernel(Geom g, DfUpdArgs a) {
     }
   }
   const double bs = block_sum_df(ls, lc);
-  if (publish_partial(a.partials, a.ticket, bs)) solver_beta_step(sd, gather_partials(a.partials, a.ticket));
+  if (threadIdx.x == 0) store_partial<true>(a.rr_partials, blockIdx.x, bs);
 }
 
-// p = r + beta p, one thread per complex component
-__global__ void __launch_bounds__(256) df_p_update_kernel(Geom g, const float2* r, float2* p, const SolverDev* sd) {
+// p = r + beta p, one site per thread; beta from the r update's partials; one extra block runs
+// the beta step.
+__global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, DfUpdArgs a) {
   pdl_wait();
   pdl_trigger();
-  if (sd->done) return;
-  const int n3 = 3 * g.vh;
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n3) return;
-  const float2 be = sd->beta_df;
-  const float2 rh = r[o], rl = r[o + n3], ph = p[o], pl = p[o + n3];
-  float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
-  df_mac(rs, rc, be.x, be.y, ph.x, pl.x);
-  df_mac(is, ic, be.x, be.y, ph.y, pl.y);
-  const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
-  p[o] = make_float2(re.x, im.x);
-  p[o + n3] = make_float2(re.y, im.y);
+  SolverDev* sd = a.sd;
+  if (*reinterpret_cast<const volatile int*>(&sd->done)) return;
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool scalar_block = blockIdx.x == gridDim.x - 1;
+  const PartialsRatio pb = partials_ratio<true, true>(a.rr_partials, (int)gridDim.x - 1, &sd->rr_b);
+  if (scalar_block) {
+    solver_beta_step(sd, pb.sum);
+    return;
+  }
+  if (i >= vh) return;
+  const float2 be = pb.ratio_df;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
+    const float2 rh = a.r[o], rl = a.r[ol], ph = a.p[o], pl = a.p[ol];
+    float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
+    df_mac(rs, rc, be.x, be.y, ph.x, pl.x);
+    df_mac(is, ic, be.x, be.y, ph.y, pl.y);
+    const float2 re = df_norm(rs, rc), im = df_norm(is, ic);
+    a.p[o] = make_float2(re.x, im.x);
+    a.p[ol] = make_float2(re.y, im.y);
+  }
 }
 
 // The pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i, all in
@@ -388,14 +413,13 @@ cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, 
   return cudaGetLastError();
 }
 
+// the update kernels: one block per 256 sites plus the scalar block
 cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(pdl, df_r_update_kernel, dim3((g.vh + 255) / 256), dim3(256), st, g, a);
+  return launch_k(pdl, df_r_update_kernel, dim3((g.vh + 255) / 256 + 1), dim3(256), st, g, a);
 }
 
-cudaError_t launch_df_p_update(const Geom& g, const void* r, void* p, const SolverDev* sd, cudaStream_t st, bool pdl) {
-  const int n3 = 3 * g.vh;
-  return launch_k(pdl, df_p_update_kernel, dim3((n3 + 255) / 256), dim3(256), st, g, static_cast<const float2*>(r),
-                  static_cast<float2*>(p), sd);
+cudaError_t launch_df_p_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_p_update_kernel, dim3((g.vh + 255) / 256 + 1), dim3(256), st, g, a);
 }
 
 cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl) {

@@ -162,21 +162,22 @@ struct DfArgs {
   double a = 0;
   float2* r_out = nullptr;          // residual rounded to FP32
   double* dot_out = nullptr;        // |r|^2
-  double* partials = nullptr;
-  unsigned* ticket = nullptr;
+  double* partials = nullptr;       // one per block
+  unsigned* ticket = nullptr;       // null: the A-apply's sum stays as (hi, lo) partials (inside the solve)
   const int* done = nullptr;        // if non-null and *done, the kernel returns at entry
-  SolverDev* solver = nullptr;      // A-apply inside a solve: the last block runs the alpha step
   int out_parity = 0;
 };
 // double-FP32 vectors of the LQCD_DF64 solve: [3][Vh] float2 hi, then [3][Vh] float2 lo
 struct DfUpdArgs {
-  float2* r;
+  float2* r;  // (hi, lo) vectors: hi [3][vh] then lo [3][vh]
   const float2* q;
+  float2* p;
   void* ring;  // kWindow slots, slot stride in bytes
   size_t slot_bytes;
   SolverDev* sd;
-  double* partials;
-  unsigned* ticket;
+  const double* pq_partials;  // (hi, lo) partials of Re<p, q> left by the A-apply
+  int n_pq;
+  double* rr_partials;  // (hi, lo) partials of |r|^2: written by the r update, read by the p update
 };
 struct DfFlushArgs {
   const void* ring;
@@ -197,7 +198,8 @@ cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream
 cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, SolverDev* sd, const InitParams& ip,
                            double* partials, unsigned* ticket, cudaStream_t st);
 cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl);
-cudaError_t launch_df_p_update(const Geom& g, const void* r, void* p, const SolverDev* sd, cudaStream_t st, bool pdl);
+cudaError_t launch_df_p_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl);
+int df_dslash_grid_blocks(const Geom& g);  // blocks (= partials) of one double-FP32 Dslash launch
 cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st);
 

@@ -140,13 +140,13 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, RUpdArgs a) {
     r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
     q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
   }
-  // (Re<p, q>, |r|^2 / Re<p, q>)
-  const double2 pq_alpha = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, &sd->rr);
+  // Re<p, q> and alpha = |r|^2 / Re<p, q>
+  const PartialsRatio pa = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, &sd->rr);
   if (scalar_block) {
-    solver_alpha_step(sd, pq_alpha.x);
+    solver_alpha_step(sd, pa.sum);
     return;
   }
-  const T alpha = sizeof(T) == 4 ? (T)(float)pq_alpha.y : (T)pq_alpha.y;
+  const T alpha = sizeof(T) == 4 ? (T)pa.ratio_f : (T)pa.ratio;
   T loc = 0;
   if (mine) {
 #pragma unroll
@@ -159,10 +159,7 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, RUpdArgs a) {
     loc = site_norm2(r);
   }
   const double bs = block_sum_mixed(loc);
-  if (threadIdx.x == 0) {
-    if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(a.rr_partials)[blockIdx.x] = split_hi_lo(bs);
-    else a.rr_partials[blockIdx.x] = bs;
-  }
+  if (threadIdx.x == 0) store_partial<sizeof(T) == 4>(a.rr_partials, blockIdx.x, bs);
 }
 
 struct PUpdArgs {
@@ -190,14 +187,14 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, PUpdArgs a) {
     r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
     p = load_vec(static_cast<const V2*>(a.p), i, g.vh);
   }
-  // (|r_new|^2, |r_new|^2 / |r|^2)
-  const double2 rr_beta = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, &sd->rr_b);
+  // |r_new|^2 and beta = |r_new|^2 / |r|^2
+  const PartialsRatio pb = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, &sd->rr_b);
   if (scalar_block) {
-    solver_beta_step(sd, rr_beta.x);
+    solver_beta_step(sd, pb.sum);
     return;
   }
   if (!mine) return;
-  const T beta = sizeof(T) == 4 ? (T)(float)rr_beta.y : (T)rr_beta.y;
+  const T beta = sizeof(T) == 4 ? (T)pb.ratio_f : (T)pb.ratio;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     p.c[c].re = fma(beta, p.c[c].re, r.c[c].re);
@@ -652,9 +649,7 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   a.x_lo = lo(w->p);
   a.a_dev = &w->sd->a_diag;
   a.a_devdf = &w->sd->a_diag_df;
-  a.solver = w->sd;
-  a.partials = w->partials;
-  a.ticket = w->tickets + 0;
+  a.partials = w->partials;  // no ticket: the r update sums the partials and runs the alpha step
   a.out_parity = 0;
   e = launch_df_dslash(L.g, a, 1, st, L.next_pdl());
   L.nlaunch += 1;
@@ -662,15 +657,17 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   DfUpdArgs u;
   u.r = hi(w->r);
   u.q = hi(w->q);
+  u.p = hi(w->p);
   u.ring = w->ring;
   u.slot_bytes = w->sbytes;
   u.sd = w->sd;
-  u.partials = w->partials;
-  u.ticket = w->tickets + 1;
+  u.pq_partials = w->partials;
+  u.n_pq = df_dslash_grid_blocks(L.g);
+  u.rr_partials = w->partials_b;
   e = launch_df_r_update(L.g, u, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  e = launch_df_p_update(L.g, w->r, w->p, w->sd, st, L.next_pdl());
+  e = launch_df_p_update(L.g, u, st, L.next_pdl());
   L.nlaunch += 1;
   return e;
 }
