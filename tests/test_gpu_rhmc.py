@@ -121,3 +121,48 @@ def test_chain_satisfies_exp_minus_dH_identity():
     assert abs(np.mean(w) - 1.0) <= 4 * err, (np.mean(w), err, np.mean(dH))
     assert np.mean(dH) >= -4 * np.std(dH, ddof=1) / np.sqrt(n_meas)
     assert 0.3 < np.mean(acc) <= 1.0
+
+
+def test_chain_resumes_from_checkpoint(tmp_path):
+    # three trajectories in one run, and the same chain stopped after the first, written to a
+    # checkpoint, read back into a fresh context and continued: the same links, bit for bit, and
+    # the same energies (the random numbers are drawn from streams keyed by the step)
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+    from paper_1710_09178_gb300 import checkpoint
+
+    act, heat = _coeffs()
+    seed = 61
+
+    def run(ctx, Ud, steps):
+        out = []
+        for t in steps:
+            p = _momenta(seed * 1000 + t)
+            xi = inputs.gaussian_vector(DIMS, seed * 1000 + 500 + t)
+            u = float(inputs.counter_uniform(seed, np.array([t], dtype=np.uint64), 0)[0])
+            rc, res = lq.rhmc_trajectory(ctx, Ud, to_dev(p), to_dev(xi), u, BETA, TAU, NSTEPS, act, heat,
+                                         tol=1e-10, md_tol=1e-9, prec=lq.FP32, prec_action=FP64)
+            assert rc == 0
+            out.append((res["dH"], res["accepted"]))
+        torch.cuda.synchronize()
+        return out
+
+    ctx, U0 = make_context(DIMS, MASS, gauge_seed=62)
+    Ua = to_dev(U0)
+    full = run(ctx, Ua, range(3))
+    ctx.close()
+
+    ctx1, _ = make_context(DIMS, MASS, U=U0)
+    Ub = to_dev(U0)
+    first = run(ctx1, Ub, range(1))
+    ctx1.close()
+    path = str(tmp_path / "chain")
+    checkpoint.save(path, Ub, DIMS, step=1, seed=seed)
+    U1, h = checkpoint.load(path, DIMS)
+    ctx2, _ = make_context(DIMS, MASS, U=U1)
+    Uc = to_dev(U1)
+    rest = run(ctx2, Uc, range(h["step"], 3))
+    ctx2.close()
+    assert first + rest == full
+    assert np.array_equal(Uc.cpu().numpy().view(np.uint64), Ua.cpu().numpy().view(np.uint64))
