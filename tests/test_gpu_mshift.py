@@ -221,3 +221,23 @@ def test_fp64_unrefined_solve_matches_oracle_with_same_stopping_rule(dims, mass,
         assert rel_norm(x, ox) < 1e-9
     otr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, oxs, poles)
     assert np.allclose(st["true_residual"], otr, rtol=0.1, atol=1e-12)  # near tol the residuals differ at rounding level
+
+
+@pytest.mark.parametrize("prec", [FP32, DF64])
+def test_full_size_32c8_solve_certified_by_oracle(prec):
+    # the benchmark's workload and launch configuration (32^3 x 8, m 0.02, 16-pole x^{-1/2} on
+    # [4m^2, 16 + 4m^2], gauge seed 5, source seed 6, default options): the oracle's FP64 true
+    # residual of every returned x_k is at most tol and equals the one the solve reports, and the
+    # returned y is the oracle's c0 b + sum_k c_k x_k of the returned x_k
+    dims, mass = (32, 32, 32, 8), 0.02
+    ctx, U = make_context(dims, mass, gauge_seed=5)
+    b = inputs.gaussian_vector(dims, 6)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(16, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    rc, st, xs, y = gpu_mshift(ctx, b, poles, res, c0, prec=prec, want_y=True)
+    assert rc == 0
+    tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, poles)
+    assert np.all(tr <= 1e-10), tr
+    rep = np.array(st["true_residual"][: len(poles)])
+    assert np.all(np.abs(rep - tr) <= 1e-12 + 2e-3 * tr), (rep, tr)
+    yo = solvers.rational_apply(b, xs, c0, res)
+    assert rel_norm(y, yo) < 1e-13
