@@ -1,4 +1,6 @@
 """Helpers for the GPU parity tests: move seeded inputs to the device and run the library."""
+import functools
+
 import numpy as np
 
 from paper_1710_09178_gb300 import inputs
@@ -12,7 +14,19 @@ def torch_mod():
 
 def to_dev(a):
     torch = torch_mod()
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a = np.ascontiguousarray(a)
+    if not a.flags.writeable:  # the shared seeded fields
+        a = a.copy()
+    return torch.from_numpy(a).cuda()
+
+
+@functools.lru_cache(maxsize=4)
+def seeded_gauge(dims, seed):
+    """inputs.gauge_field, generated once per (dims, seed) in a test session and read-only (the
+    large lattices take seconds to generate); callers that modify links take a copy."""
+    U = inputs.gauge_field(tuple(dims), seed=seed)
+    U.flags.writeable = False
+    return U
 
 
 def make_context(dims, mass, U=None, gauge_seed=1):
@@ -20,7 +34,7 @@ def make_context(dims, mass, U=None, gauge_seed=1):
 
     ctx = lq.Context(dims, mass)
     if U is None:
-        U = inputs.gauge_field(dims, seed=gauge_seed)
+        U = seeded_gauge(tuple(dims), gauge_seed)
     ctx.set_gauge(to_dev(U))
     return ctx, U
 

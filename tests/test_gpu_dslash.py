@@ -71,6 +71,19 @@ def test_dslash_full_size_32c8_fp32_and_r12():
     assert rel_max(gpu_dslash(ctx, psi, 1, FP64), ref) < 1e-12
 
 
+def test_dslash_beyond_l2_40c8():
+    # 40^3 x 8: FP32 links of 147 MB, more than L2 holds; every format against the oracle
+    dims = (40, 40, 40, 8)
+    ctx, U = make_context(dims, 0.05, gauge_seed=71)
+    psi = inputs.gaussian_vector(dims, 73)
+    for p in (0, 1):
+        ref = staggered.dslash_eo(U, psi, dims, p)
+        assert rel_max(gpu_dslash(ctx, psi, p, FP64), ref) < 1e-12
+        assert rel_max(gpu_dslash(ctx, psi, p, FP32), ref) < 2e-6
+        assert rel_max(gpu_dslash(ctx, psi, p, FP32_R12), ref) < 2e-6
+        assert rel_max(gpu_dslash(ctx, psi, p, DF64), ref) < 1e-13
+
+
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 2e-6), (FP32_R12, 2e-6)])
 def test_apply_A_and_dot(prec, tol):
     dims, m, sigma = (10, 6, 4, 6), 0.05, 0.013

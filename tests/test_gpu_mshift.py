@@ -223,16 +223,20 @@ def test_fp64_unrefined_solve_matches_oracle_with_same_stopping_rule(dims, mass,
     assert np.allclose(st["true_residual"], otr, rtol=0.1, atol=1e-12)  # near tol the residuals differ at rounding level
 
 
-@pytest.mark.parametrize("prec", [FP32, DF64])
-def test_full_size_32c8_solve_certified_by_oracle(prec):
+@pytest.mark.parametrize("prec,power", [(FP32, -0.5), (DF64, -0.5), (FP32, 0.25)])
+def test_full_size_32c8_solve_certified_by_oracle(prec, power):
     # the benchmark's workload and launch configuration (32^3 x 8, m 0.02, 16-pole x^{-1/2} on
-    # [4m^2, 16 + 4m^2], gauge seed 5, source seed 6, default options): the oracle's FP64 true
-    # residual of every returned x_k is at most tol and equals the one the solve reports, and the
-    # returned y is the oracle's c0 b + sum_k c_k x_k of the returned x_k
+    # [4m^2, 16 + 4m^2], gauge seed 5, source seed 6, default options; and the heatbath's x^{1/4}):
+    # the oracle's FP64 true residual of every returned x_k is at most tol and equals the one the
+    # solve reports, and the returned y is the oracle's c0 b + sum_k c_k x_k of the returned x_k
     dims, mass = (32, 32, 32, 8), 0.02
     ctx, U = make_context(dims, mass, gauge_seed=5)
     b = inputs.gaussian_vector(dims, 6)
-    c0, res, poles, _ = rational.zolotarev_inv_sqrt(16, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
+    if power == -0.5:
+        c0, res, poles, _ = rational.zolotarev_inv_sqrt(16, lo, hi)
+    else:
+        c0, res, poles, _ = rational.remez_power(power, lo, hi, 16)
     rc, st, xs, y = gpu_mshift(ctx, b, poles, res, c0, prec=prec, want_y=True)
     assert rc == 0
     tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, poles)
@@ -241,3 +245,17 @@ def test_full_size_32c8_solve_certified_by_oracle(prec):
     assert np.all(np.abs(rep - tr) <= 1e-12 + 2e-3 * tr), (rep, tr)
     yo = solvers.rational_apply(b, xs, c0, res)
     assert rel_norm(y, yo) < 1e-13
+
+
+def test_lattice_beyond_l2_40c8():
+    # 40^3 x 8: the FP32 links (147 MB) no longer fit in the 126 MB L2, so the solve streams them
+    # from HBM every half-Dslash.  8-pole x^{-1/2}, mixed precision; every shift certified by the
+    # oracle's FP64 true residual
+    dims, mass = (40, 40, 40, 8), 0.05
+    ctx, U = make_context(dims, mass, gauge_seed=71)
+    b = inputs.gaussian_vector(dims, 72)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(8, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    rc, st, xs, _ = gpu_mshift(ctx, b, poles, res, c0, prec=FP32)
+    assert rc == 0
+    tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, poles)
+    assert np.all(tr <= 1e-10), tr
