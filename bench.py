@@ -476,7 +476,70 @@ def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True
         p["ctx"].close()
     for o in owners:
         o.close()
+    out["dslash_batch"] = run_batch_dslash(lq, torch, picks)
     return out
+
+
+def run_batch_dslash(lq, torch, picks, reps=20):
+    """The half-Dslash of every lattice of the batch workload (FP32 links, both parities in turn):
+    one persistent dslash_eo_batch launch over all lattices vs one dslash_eo launch per lattice
+    (each with its autotuned threads per site), each variant captured reps times in a CUDA graph.
+    Returns per-sweep times and algorithmic GB/s."""
+    from paper_1710_09178_gb300 import inputs
+
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    ctxs, ins, outs = [], [], []
+    for l, (dims, mass) in enumerate(picks):
+        c = lq.Context(dims, mass, stream=s.cuda_stream)
+        c.set_gauge(torch.from_numpy(inputs.gauge_field(dims, seed=7000 + l)).cuda())
+        c.autotune(lq.FP32)  # the per-lattice launches use their best threads per site
+        vin, vout = c.new_vector(lq.FP32), c.new_vector(lq.FP32)
+        vin.view(torch.float32).normal_()
+        ctxs.append(c)
+        ins.append(vin)
+        outs.append(vout)
+    torch.cuda.synchronize()
+    n = len(ctxs)
+    bytes_sweep = sum(DSLASH_BYTES_PER_SITE["fp32"] * (int(np.prod(d)) // 2) for d, _ in picks)
+
+    def batched(r):
+        lq.dslash_eo_batch(ctxs, outs, ins, [r & 1] * n, lq.FP32)
+
+    def single(r):
+        for c, vi, vo in zip(ctxs, ins, outs):
+            lq.dslash_eo(c, vo, vi, r & 1, lq.FP32)
+
+    res = {}
+    with torch.cuda.stream(s):
+        for name, fn in (("persistent_batch", batched), ("one_launch_per_lattice", single)):
+            fn(0)
+            fn(1)
+            s.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+                for r in range(reps):
+                    fn(r)
+            graph.replay()
+            ms = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                graph.replay()
+                e1.record(s)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1) / reps)
+            m = statistics.median(ms)
+            res[name] = {"us_per_sweep": m * 1e3, "algorithmic_GBps": bytes_sweep / (m * 1e-3) / 1e9,
+                         "launches_per_sweep": 1 if name == "persistent_batch" else n}
+    res["speedup"] = res["one_launch_per_lattice"]["us_per_sweep"] / res["persistent_batch"]["us_per_sweep"]
+    res["lattices"] = n
+    res["bytes_per_sweep"] = bytes_sweep
+    res["timing"] = f"{reps} sweeps per CUDA graph, median of 5 replays"
+    for c in ctxs:
+        c.close()
+    return res
 
 
 def run_profile_target(kind, prec_name):

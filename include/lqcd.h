@@ -157,6 +157,25 @@ int lqcd_unpack_vector(lqcd_ctx* ctx, double* dst_dev, const void* src_dev, int 
 int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, int prec);
 
 /*
+ * dslash_eo_batch - dslash_eo on n lattices at once, each with its own context (any sizes and
+ * masses), in one persistent launch: the output sites of all lattices are cut into chunks of
+ * 128 and the GPU's blocks take chunks from a shared counter until none are left, so lattices
+ * too small to fill the GPU run together (batching of many independent lattices; the paper
+ * treats one lattice at a time).
+ *   ctxs[l], out_devs[l], in_devs[l], out_parities[l] : as ctx, out_dev, in_dev, out_parity of
+ *                dslash_eo for lattice l, l = 0 .. n-1; 1 <= n <= LQCD_MAX_BATCH
+ *   prec       : LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8 or LQCD_FP32_L16 (not LQCD_DF64)
+ * The outputs equal those of n dslash_eo calls bit for bit.  Enqueued on ctxs[0]'s stream; work
+ * enqueued on the other contexts' streams must be ordered before the call (contexts created on
+ * the same stream are).  Host arrays are read before the call returns.  LQCD_ERR_ARG for null
+ * pointers, n out of range, an unsupported prec, a bad parity or out aliasing in;
+ * LQCD_ERR_STATE if a context has no gauge field.  Asynchronous.
+ */
+#define LQCD_MAX_BATCH 128
+int dslash_eo_batch(lqcd_ctx* const* ctxs, void* const* out_devs, const void* const* in_devs,
+                    const int* out_parities, int n, int prec);
+
+/*
  * lqcd_apply_A - q = (A + sigma) p on even sites, A = 4 m^2 - D_eo D_oe (Section 3.2),
  * internal vectors of precision prec (FP64, FP32, FP32_R12, FP32_R8, FP32_L16 or DF64).  If pq_host is not
  * NULL the call synchronises and stores Re<p, q> (FP64 accumulation) there.

@@ -48,13 +48,14 @@ OPT_PDL = 7
 OPT_DF_RESID = 8
 
 MAX_SHIFTS = 32
+MAX_BATCH = 128
 
 EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
     "fermion_force", "rhmc_trajectory", "mshift_cg_batch", "lqcd_autotune",
-    "lqcd_share_gauge",
+    "lqcd_share_gauge", "dslash_eo_batch",
 ]
 
 
@@ -159,6 +160,7 @@ def load_library(path: str = LIB_PATH):
         "mshift_cg_batch": (i, [ctypes.POINTER(BatchProblem), i, i]),
         "lqcd_autotune": (i, [vp, i, ctypes.POINTER(ctypes.c_int)]),
         "lqcd_share_gauge": (i, [vp, vp]),
+        "dslash_eo_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +278,19 @@ class Context:
 def dslash_eo(ctx: Context, out, in_, out_parity: int, prec: int):
     """out = D_oe in (out_parity=1) or D_eo in (out_parity=0); internal vectors of precision prec."""
     return ctx.check(load_library().dslash_eo(ctx.handle, _ptr(out), _ptr(in_), int(out_parity), int(prec)))
+
+
+def dslash_eo_batch(ctxs, outs, ins, out_parities, prec: int):
+    """dslash_eo on several lattices in one persistent launch (dslash_eo_batch); the lists are
+    indexed alike; launched on ctxs[0]'s stream."""
+    n = len(ctxs)
+    if not (len(outs) == len(ins) == len(out_parities) == n):
+        raise ValueError("dslash_eo_batch: lists of different lengths")
+    H = ctypes.c_void_p * n
+    rc = load_library().dslash_eo_batch(H(*[c.handle.value for c in ctxs]), H(*[_ptr(o) for o in outs]),
+                                        H(*[_ptr(x) for x in ins]),
+                                        (ctypes.c_int * n)(*[int(p) for p in out_parities]), n, int(prec))
+    return ctxs[0].check(rc)
 
 
 def mshift_cg(ctx: Context, shifts, residues, c0, b, xs=None, y=None, tol=1e-10, maxiter=20000, prec=FP32,

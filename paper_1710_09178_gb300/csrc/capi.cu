@@ -3,6 +3,7 @@
 // kernels.  Errors come back as status codes with a message in the context.
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -212,6 +213,59 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
   cudaError_t e = launch_dslash(make_geom(ctx), ctx->gauge, a, ctx->stream, &nl);
   ctx->launches += nl;
   return cuda_check(ctx, e, "dslash_eo");
+}
+
+static const void* link_copy(const GaugeCopies& gc, int prec) {
+  switch (prec) {
+    case LQCD_FP64: return gc.u64;
+    case LQCD_FP32_R12: return gc.u12;
+    case LQCD_FP32_R8: return gc.u8;
+    case LQCD_FP32_L16: return gc.u16;
+    default: return gc.u32;
+  }
+}
+
+int dslash_eo_batch(lqcd_ctx* const* ctxs, void* const* out_devs, const void* const* in_devs,
+                    const int* out_parities, int n, int prec) {
+  static_assert(kMaxBatch == LQCD_MAX_BATCH, "batch limit");
+  if (!ctxs || !ctxs[0]) return LQCD_ERR_ARG;
+  lqcd_ctx* c0 = ctxs[0];
+  if (!out_devs || !in_devs || !out_parities || n < 1 || n > LQCD_MAX_BATCH)
+    return fail(c0, LQCD_ERR_ARG, "dslash_eo_batch: bad argument");
+  if (!prec_valid(prec) || prec == LQCD_FP16FIX || prec == LQCD_DF64)
+    return fail(c0, LQCD_ERR_ARG, "dslash_eo_batch: unsupported precision");
+  for (int l = 0; l < n; ++l) {
+    lqcd_ctx* c = ctxs[l];
+    if (!c || !out_devs[l] || !in_devs[l] || (out_parities[l] != 0 && out_parities[l] != 1) ||
+        out_devs[l] == in_devs[l])
+      return fail(c0, LQCD_ERR_ARG, "dslash_eo_batch: bad argument");
+    if (!c->gauge.loaded) return fail(c0, LQCD_ERR_STATE, "dslash_eo_batch: no gauge field loaded");
+  }
+  // the work counter lives in ctxs[0]'s scratch (allocated on first use)
+  int rc = ensure_scratch(c0);
+  if (rc != LQCD_OK) return rc;
+  int dev = 0, n_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // kBatchPerLaunch lattices per persistent launch, consecutive launches on ctxs[0]'s stream
+  for (int l0 = 0; l0 < n && e == cudaSuccess; l0 += kBatchPerLaunch) {
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = std::min(kBatchPerLaunch, n - l0);
+    for (int j = 0; j < a.n; ++j) {
+      const lqcd_ctx* c = ctxs[l0 + j];
+      a.lat[j].g = make_geom(c);
+      a.lat[j].links = link_copy(c->gauge, prec);
+      a.lat[j].in = in_devs[l0 + j];
+      a.lat[j].out = out_devs[l0 + j];
+      a.lat[j].out_parity = out_parities[l0 + j];
+      a.chunk_end[j + 1] = a.chunk_end[j] + batch_items(c->Vh);
+    }
+    for (int j = a.n; j < kBatchPerLaunch; ++j) a.chunk_end[j + 1] = a.chunk_end[a.n];
+    e = launch_dslash_batch(a, prec, c0->tickets + 7, n_sm, c0->stream);
+    c0->launches += 1;
+  }
+  return cuda_check(c0, e, "dslash_eo_batch");
 }
 
 int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host) {

@@ -10,6 +10,7 @@
 // TPS threads cooperate on one site, each taking 8/TPS of the hops, and combine
 // their partial sums with warp shuffles; more threads per site means more
 // independent loads in flight per SM.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -163,29 +164,27 @@ __device__ __forceinline__ void dslash_epilogue(const KArgs& k, const Vec3<T>& d
   }
 }
 
-template <int LF, int TPS, int EPI>
-__global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
+// The hops of lane `sub` of output site i (TPS lanes per site): h = sub, sub + TPS, ...; h even
+// is the forward hop along mu = h / 2 (U_mu(x) in(x + mu)), h odd the backward one
+// (U_mu(x - mu)^dagger in(x - mu), the link stored at x - mu in the other parity's block).
+// start() computes the neighbours and signs and issues the first link's loads; apply() runs the
+// two-stage software pipeline (the loads of hop q + 1 in flight while hop q is computed) and
+// returns the lane's share of (D in)(x).  Shared by the single-lattice and the batched kernels.
+template <int LF, int TPS>
+struct SiteHops {
   typedef typename LinkTraits<LF>::T T;
   typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
-  const int vh = g.vh;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = gt / TPS;
-  const int sub = gt % TPS;
-  const bool valid = i < vh;
-  const int p = k.out_parity;
-  const V2* in = static_cast<const V2*>(k.in);
-
-  // hops of this lane: h = sub, sub + TPS, ...; h even = forward, odd = backward along mu = h / 2
-  constexpr int NH = 8 / TPS;
-  int nb[NH] = {}, sg[NH] = {};
-  // FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
-  const uint64_t pol = (LF == kL64) ? policy_evict_first() : policy_evict_last();
-  auto link_of = [&](int q) {
-    const int h = sub + q * TPS;
-    return (h & 1) ? load_raw<LF>(k.links, 1 - p, h >> 1, nb[q], vh, pol) : load_raw<LF>(k.links, p, h >> 1, i, vh, pol);
-  };
+  static constexpr int NH = 8 / TPS;
+  int nb[NH], sg[NH];
   RawLink<LF> Wn;
-  if (valid) {
+
+  __device__ __forceinline__ RawLink<LF> link(const void* links, int p, int i, int sub, int q, int vh,
+                                              uint64_t pol) const {
+    const int h = sub + q * TPS;
+    return (h & 1) ? load_raw<LF>(links, 1 - p, h >> 1, nb[q], vh, pol) : load_raw<LF>(links, p, h >> 1, i, vh, pol);
+  }
+
+  __device__ __forceinline__ void start(const Geom& g, const void* links, int p, int i, int sub, uint64_t pol) {
     Site s = site_of(g, p, i);
 #pragma unroll
     for (int q = 0; q < NH; ++q) {
@@ -199,34 +198,64 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
         sg[q] = (LF >= kL12) ? link_sign_bwd(g, s, mu) : 1;
       }
     }
-    Wn = link_of(0);  // links are never written by the kernels of a solve: fetched before the wait
+    Wn = link(links, p, i, sub, 0, g.vh, pol);
   }
-  pdl_wait();
-  pdl_trigger();
-  if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
 
-  Vec3<T> accf = vzero<T>(), accb = vzero<T>();
-  if (valid) {
-    // two-stage software pipeline: the loads of hop q+1 are in flight while hop q is computed
+  __device__ __forceinline__ Vec3<T> apply(const void* links, const V2* in, int p, int i, int sub, int vh,
+                                           uint64_t pol) {
+    Vec3<T> accf = vzero<T>(), accb = vzero<T>();
     Vec3<T> vn = ldg_vec(in, nb[0], vh);
 #pragma unroll
     for (int q = 0; q < NH; ++q) {
       const Mat3<T> W = decode<LF>(Wn, sg[q]);
       Vec3<T> v = vn;
       if (q + 1 < NH) {
-        Wn = link_of(q + 1);
+        Wn = link(links, p, i, sub, q + 1, vh, pol);
         vn = ldg_vec(in, nb[q + 1], vh);
       }
       if (((sub + q * TPS) & 1) == 0) mv_acc(accf, W, v);
       else mdv_acc(accb, W, v);
     }
+    Vec3<T> d;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.c[c] = cmake(accf.c[c].re - accb.c[c].re, accf.c[c].im - accb.c[c].im);
+    return d;
   }
+};
+
+// FP32 links stay in L2 between launches; the FP64 copy (reliable updates) must not displace them
+template <int LF>
+__device__ __forceinline__ uint64_t link_policy() {
+  return (LF == kL64) ? policy_evict_first() : policy_evict_last();
+}
+
+template <int LF, int TPS, int EPI>
+__global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
+  typedef typename LinkTraits<LF>::T T;
+  typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
+  const int vh = g.vh;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / TPS;
+  const int sub = gt % TPS;
+  const bool valid = i < vh;
+  const int p = k.out_parity;
+  const V2* in = static_cast<const V2*>(k.in);
+  const uint64_t pol = link_policy<LF>();
+  SiteHops<LF, TPS> hops;
+  // links are never written by the kernels of a solve: the first one is fetched before the wait
+  if (valid) hops.start(g, k.links, p, i, sub, pol);
+  pdl_wait();
+  pdl_trigger();
+  if (k.done && *k.done) return;  // uniform: the flag only changes between kernels
+
+  Vec3<T> part = vzero<T>();
+  if (valid) part = hops.apply(k.links, in, p, i, sub, vh, pol);
   // D in = fwd - bwd, summed over the TPS lanes of the site
   Vec3<T> d;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    T re = accf.c[c].re - accb.c[c].re;
-    T im = accf.c[c].im - accb.c[c].im;
+    T re = part.c[c].re;
+    T im = part.c[c].im;
 #pragma unroll
     for (int o = 1; o < TPS; o <<= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -236,6 +265,91 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   }
 
   dslash_epilogue<T, V2, TPS, EPI>(k, d, i, sub, valid, vh);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched half-Dslash over many lattices of different sizes in one persistent launch.  The work
+// is split into items of kBatchChunk output sites of one lattice (chunk_end holds the prefix
+// sums of the lattices' item counts); every block takes items from a global counter until none
+// are left, so uneven lattices load-balance over the SMs and small lattices that could not fill
+// the GPU on their own share it.  One thread per site, the same per-site arithmetic as
+// dslash_kernel (bit-identical outputs).  No block waits on another: the counter only hands out
+// items.  The descriptors are copied from the parameter block to shared memory with constant
+// offsets once per block, and every index taken from them is checked before use.
+// ---------------------------------------------------------------------------------------------
+constexpr int kBatchChunk = 128;
+static_assert(sizeof(BatchArgs) <= 4000, "the batch descriptors travel as the kernel's parameter block");
+static_assert(kBatchPerLaunch <= kBatchChunk, "one thread per descriptor");
+
+template <int LF>
+__global__ void __launch_bounds__(kBatchChunk, 7) dslash_batch_kernel(BatchArgs a, unsigned* head) {
+  typedef typename LinkTraits<LF>::T T;
+  typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
+  __shared__ BatchLattice lat[kBatchPerLaunch];
+  __shared__ int chunk_end[kBatchPerLaunch + 1];
+  __shared__ int item_s;
+#pragma unroll
+  for (int j = 0; j < kBatchPerLaunch; ++j)
+    if (threadIdx.x == j) lat[j] = a.lat[j];
+#pragma unroll
+  for (int j = 0; j <= kBatchPerLaunch; ++j)
+    if (threadIdx.x == j) chunk_end[j] = a.chunk_end[j];
+  const int n = a.n;
+  if (n < 1 || n > kBatchPerLaunch) return;  // uniform; the host never passes such a block
+  __syncthreads();
+  const int n_items = chunk_end[n];
+  const uint64_t pol = link_policy<LF>();
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();  // item_s is written again at the top of the next round
+    if (it >= n_items) break;
+    int l = 0;  // the lattice of item it: chunk_end[l] <= it < chunk_end[l + 1] (binary search)
+    for (int lo = 0, hi = n - 1; lo <= hi;) {
+      const int mid = (lo + hi) >> 1;
+      if (chunk_end[mid + 1] <= it) {
+        lo = mid + 1;
+        l = lo;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    if (l >= n) continue;
+    const BatchLattice& L = lat[l];
+    const int i = (it - chunk_end[l]) * kBatchChunk + threadIdx.x;
+    if (i >= 0 && i < L.g.vh) {
+      SiteHops<LF, 1> hops;
+      hops.start(L.g, L.links, L.out_parity, i, 0, pol);
+      const Vec3<T> d = hops.apply(L.links, static_cast<const V2*>(L.in), L.out_parity, i, 0, L.g.vh, pol);
+      V2* out = static_cast<V2*>(L.out);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        V2 w;
+        w.x = d.c[c].re;
+        w.y = d.c[c].im;
+        out[(size_t)c * L.g.vh + i] = w;
+      }
+    }
+  }
+}
+
+int batch_items(int vh) { return (vh + kBatchChunk - 1) / kBatchChunk; }
+
+cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, int n_sm, cudaStream_t st) {
+  const int items = a.chunk_end[a.n];
+  if (items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min(items, 7 * n_sm);  // one resident wave of persistent blocks
+  switch (prec) {
+    case LQCD_FP64: dslash_batch_kernel<kL64><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+    case LQCD_FP32_R12: dslash_batch_kernel<kL12><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+    case LQCD_FP32_R8: dslash_batch_kernel<kL8><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+    case LQCD_FP32_L16: dslash_batch_kernel<kL16><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+    default: dslash_batch_kernel<kL32><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+  }
+  return cudaGetLastError();
 }
 
 template <int LF, int TPS>

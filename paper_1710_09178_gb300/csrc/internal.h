@@ -6,11 +6,10 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "lqcd.h"
 
 namespace lqcd {
-
-struct Geom;
 
 // Device-resident state of one shifted-CG solve (scalars, per-shift recurrences
 // and the coefficients of the pending window of shift-vector updates).
@@ -141,6 +140,26 @@ struct DslashArgs {
   bool pdl = false;              // programmatic dependent launch (inside captured solve graphs)
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
+
+// dslash.cu: the batched half-Dslash (dslash_eo_batch).  One launch takes up to kBatchPerLaunch
+// lattices, whose descriptors travel in the kernel's parameter block (under 4 KB); larger
+// batches are split into consecutive launches.
+constexpr int kMaxBatch = 128;
+constexpr int kBatchPerLaunch = 32;
+struct BatchLattice {
+  Geom g;
+  const void* links;  // the link copy of the batch's precision
+  const void* in;
+  void* out;
+  int out_parity;
+};
+struct BatchArgs {
+  int n;
+  int chunk_end[kBatchPerLaunch + 1];  // prefix sums of the lattices' item counts
+  BatchLattice lat[kBatchPerLaunch];
+};
+int batch_items(int vh);
+cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, int n_sm, cudaStream_t st);
 int dslash_grid_blocks(const Geom& g, int prec, int tps);
 
 // df64.cu: residuals b - (A + sigma) x in double-FP32 arithmetic

@@ -76,3 +76,58 @@ def test_autotune_keeps_parity(dims):
     psi = inputs.gaussian_vector(dims, 71)
     for p in (0, 1):
         assert rel_max(gpu_dslash(ctx, psi, p, lq.FP32), staggered.dslash_eo(U, psi, dims, p)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 4, 5])  # FP64, FP32, 12-real, 8-real, 16-bit links
+def test_dslash_batch_equals_single_launches_and_oracle(prec):
+    # five lattices of different sizes (one with a ragged last chunk: V/2 = 720), both parities:
+    # the persistent batched launch gives the bits of one dslash_eo per lattice, and those match
+    # the oracle (16-bit links: on the oracle-decoded links)
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+    from oracle import linkcomp
+
+    lattices = [(4, 4, 4, 4), (10, 6, 4, 6), (8, 8, 8, 8), (16, 16, 16, 4), (2, 2, 2, 2)]
+    ctxs, ins, outs, refs, pars = [], [], [], [], []
+    for li, dims in enumerate(lattices):
+        ctx, U = make_context(dims, 0.05, gauge_seed=80 + li)
+        psi = inputs.gaussian_vector(dims, 90 + li)
+        p = li & 1
+        vin = ctx.new_vector(prec)
+        ctx.pack(vin, prec, to_dev(psi))
+        ctxs.append(ctx)
+        ins.append(vin)
+        outs.append(ctx.new_vector(prec))
+        pars.append(p)
+        Ur = linkcomp.decode_l16(linkcomp.encode_l16(U.reshape(-1, 3, 3))).reshape(U.shape) if prec == 5 else U
+        refs.append(staggered.dslash_eo(Ur, psi, dims, p))
+    lq.dslash_eo_batch(ctxs, outs, ins, pars, prec)
+    torch.cuda.synchronize()
+    for ctx, vin, vout, p, ref in zip(ctxs, ins, outs, pars, refs):
+        single = ctx.new_vector(prec)
+        lq.dslash_eo(ctx, single, vin, p, prec)
+        torch.cuda.synchronize()
+        assert torch.equal(single, vout)
+        got = torch.empty(ctx.Vh, 3, dtype=torch.complex128, device="cuda")
+        ctx.unpack(got, vout, prec)
+        got = got.cpu().numpy()
+        tol = 1e-12 if prec == 0 else (1e-4 if prec == 4 else 2e-6)
+        assert rel_max(got, ref) < tol
+
+
+def test_dslash_batch_rejects_bad_arguments():
+    import paper_1710_09178_gb300 as lq
+
+    ctx, _ = make_context((4, 4, 4, 4), 0.1)
+    v, w = ctx.new_vector(lq.FP32), ctx.new_vector(lq.FP32)
+    for args in (([ctx], [v], [v], [0], lq.FP32), ([ctx], [w], [v], [2], lq.FP32), ([ctx], [w], [v], [0], lq.DF64),
+                 ([ctx], [w], [v], [0], lq.FP16FIX)):
+        with pytest.raises(lq.LqcdError):
+            lq.dslash_eo_batch(*args)
+    bare = lq.Context((4, 4, 4, 4), 0.1)
+    with pytest.raises(lq.LqcdError):
+        lq.dslash_eo_batch([ctx, bare], [w, v], [v, w], [0, 1], lq.FP32)
+    with pytest.raises(lq.LqcdError):
+        lq.dslash_eo_batch([ctx] * (lq.MAX_BATCH + 1), [w] * (lq.MAX_BATCH + 1), [v] * (lq.MAX_BATCH + 1),
+                           [0] * (lq.MAX_BATCH + 1), lq.FP32)
