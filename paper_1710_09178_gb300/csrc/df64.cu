@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __
   lo[i] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
 }
 
-// EPI 0: out = D in (hi, lo);  EPI 1: out = a x - D in and Re<x, out> (the A-apply of the
-// solve, whose last block runs the alpha step when solver is set);  EPI 2: r_out =
-// fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
+// EPI 0: out = D in (hi, lo);  EPI 1: out = a x - D in and Re<x, out> (the A-apply; inside the
+// solve, without a ticket, the sum stays as per-block (hi, lo) partials for the r update);
+// EPI 2: r_out = fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
 template <int EPI>
 __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
   const int vh = g.vh;

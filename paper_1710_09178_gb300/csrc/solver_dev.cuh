@@ -1,5 +1,6 @@
-// solver_dev.cuh - the scalar steps of the shifted CG, run by the last block of a
-// reduction kernel right after the global sum it needs is known.
+// solver_dev.cuh - the scalar steps of the shifted CG, run by one block right after the global
+// sum it needs is known: the extra block of the r and p update kernels in the base iteration,
+// the last block of a reduction kernel elsewhere.
 //
 // Shifted CG (Section 4; ref. [mcg]): base system A + sigma_0 with sigma_0 the
 // smallest shift, s_k = sigma_k - sigma_0, residual collinearity r_k = zeta_k r.
@@ -20,7 +21,7 @@
 
 namespace lqcd {
 
-// The steps run in one warp of the last block; every lane k < n owns shift k.  All loads of a
+// The steps run in one warp of that block; every lane k < n owns shift k.  All loads of a
 // lane are issued before any store (the state lives in global memory and a chain of dependent
 // round trips would cost far more than the arithmetic, most of which is FP64).
 
@@ -79,7 +80,7 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
   }
 }
 
-// last block, all threads call; pq identical in every thread
+// the block that runs the step; all its threads call, pq identical in every thread
 __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
     if (i < m) sd->chi[k][i] = chi[i] + ak * pi[i];
 }
 
-// last block, all threads call; rr_new identical in every thread
+// the block that runs the step; all its threads call, rr_new identical in every thread
 __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
