@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, DfUpdArgs a
   const bool mine = !scalar_block && i < vh && m < kWindow;
   const PartialsRatio pa = partials_ratio<false, true>(a.pq_partials, a.n_pq, &sd->rr);
   if (scalar_block) {
-    solver_alpha_step(sd, pa.sum);
+    solver_alpha_step(sd, pa);
     return;
   }
   const float2 al = pa.ratio_df;
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, DfUpdArgs a
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
   const PartialsRatio pb = partials_ratio<true, true>(a.rr_partials, (int)gridDim.x - 1, &sd->rr_b);
   if (scalar_block) {
-    solver_beta_step(sd, pb.sum);
+    solver_beta_step(sd, pb);
     return;
   }
   if (i >= vh) return;

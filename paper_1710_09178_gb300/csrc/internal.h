@@ -55,6 +55,7 @@ struct SolverDev {
   unsigned ticket[4];
   double s[kMaxShifts];  // sigma_k - sigma_0
   double zeta[kMaxShifts], zeta_prev[kMaxShifts], zeta_new[kMaxShifts];
+  double zratio[kMaxShifts];  // zeta_new / zeta of the running iteration (alpha step -> beta step)
   int active[kMaxShifts];   // shift still iterating
   int wactive[kMaxShifts];  // shift takes part in the pending window
   // pending window: p_k = P p_k0 + sum_i pi_i R_i,  x_k = x_k0 + X p_k0 + sum_i chi_i R_i

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, RUpdArgs a) {
   // Re<p, q> and alpha = |r|^2 / Re<p, q>
   const PartialsRatio pa = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, &sd->rr);
   if (scalar_block) {
-    solver_alpha_step(sd, pa.sum);
+    solver_alpha_step(sd, pa);
     return;
   }
   const T alpha = sizeof(T) == 4 ? (T)pa.ratio_f : (T)pa.ratio;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, PUpdArgs a) {
   // |r_new|^2 and beta = |r_new|^2 / |r|^2
   const PartialsRatio pb = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, &sd->rr_b);
   if (scalar_block) {
-    solver_beta_step(sd, pb.sum);
+    solver_beta_step(sd, pb);
     return;
   }
   if (!mine) return;

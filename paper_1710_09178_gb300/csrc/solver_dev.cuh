@@ -80,8 +80,10 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
   }
 }
 
-// the block that runs the step; all its threads call, pq identical in every thread
-__device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
+// the block that runs the step; all its threads call.  pa = (Re<p, q>, alpha = |r|^2 / Re<p, q>
+// with its FP32 and (hi, lo) copies), formed once by thread 0 (every FP64 division costs tens of
+// cycles per warp on GB300's narrow FP64 pipe, and the step is on the iteration's critical path).
+__device__ __forceinline__ void solver_alpha_step(SolverDev* sd, const PartialsRatio& pa) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
   const double rr = sd->rr, alpha_prev = sd->alpha_prev, beta_prev = sd->beta_prev;
@@ -101,14 +103,14 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
       chi[i] = (i < m) ? sd->chi[k][i] : 0.0;
     }
   }
-  const double alpha = rr / pq;
+  const double pq = pa.sum, alpha = pa.ratio;
   const bool ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
   if (k == 0) {
     sd->pq = pq;
     sd->rr_b = rr;
     sd->alpha = alpha;
-    sd->alpha_f = (float)alpha;
-    sd->alpha_df = split_hi_lo(alpha);
+    sd->alpha_f = pa.ratio_f;
+    sd->alpha_df = pa.ratio_df;
     if (!ok) {
       sd->status = LQCD_ERR_NONFINITE;
       sd->done = 1;
@@ -116,17 +118,22 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, double pq) {
   }
   if (!ok || !act) return;
   const double den = alpha * beta_prev * (zp - z) + zp * alpha_prev * (1.0 + sk * alpha);
-  const double zn = z * zp * alpha_prev / den;
-  const double ak = alpha * zn / z;
+  // zeta_k' = zeta_k zeta_k^old alpha_old / den, formed as zeta_k q with q = zeta_k'/zeta_k (one
+  // FP64 division instead of two; q is reused by the beta step)
+  const double q = zp * alpha_prev / den;
+  const double zn = z * q;
+  const double ak = alpha * q;
   sd->zeta_new[k] = zn;
+  sd->zratio[k] = q;
   sd->X[k] = X + ak * P;
 #pragma unroll
   for (int i = 0; i < kWindow; ++i)
     if (i < m) sd->chi[k][i] = chi[i] + ak * pi[i];
 }
 
-// the block that runs the step; all its threads call, rr_new identical in every thread
-__device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
+// the block that runs the step; all its threads call.  pb = (|r_new|^2, beta = |r_new|^2 / |r|^2
+// with its FP32 and (hi, lo) copies), formed once by thread 0.
+__device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRatio& pb) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
   const double rr = sd->rr, stop2 = sd->stop2, alpha = sd->alpha;
@@ -135,15 +142,16 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
   const double ru_delta2 = sd->ru_delta2, rr_ru_max = sd->rr_ru_max;
   const bool mine = k < n;
   const int act = mine ? sd->active[k] : 0;
-  double z = 1.0, zn = 1.0, P = 0.0, pi[kWindow];
+  double z = 1.0, zn = 1.0, zr = 1.0, P = 0.0, pi[kWindow];
   if (act) {
     z = sd->zeta[k];
     zn = sd->zeta_new[k];
+    zr = sd->zratio[k];
     P = sd->P[k];
 #pragma unroll
     for (int i = 0; i < kWindow; ++i) pi[i] = (i < m) ? sd->pi[k][i] : 0.0;
   }
-  const double beta = rr_new / rr;
+  const double rr_new = pb.sum, beta = pb.ratio;
   const bool ok = isfinite(rr_new) && isfinite(beta);
   if (!ok) {
     if (k == 0) {
@@ -163,8 +171,7 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
   }
   int still = 0;
   if (act) {
-    const double ratio = zn / z;
-    const double bk = beta * ratio * ratio;
+    const double bk = beta * zr * zr;  // zr = zn / z, formed by the alpha step
     sd->P[k] = P * bk;
     const bool stop = zn * zn * rr_new <= stop2;
 #pragma unroll
@@ -189,8 +196,8 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, double rr_new) {
     const int it = iter + 1;
     const int done = (n_active == 0 || it >= maxiter) ? 1 : 0;
     sd->beta = beta;
-    sd->beta_f = (float)beta;
-    sd->beta_df = split_hi_lo(beta);
+    sd->beta_f = pb.ratio_f;
+    sd->beta_df = pb.ratio_df;
     sd->n_active = n_active;
     sd->m = m + 1;
     sd->rr = rr_new;
