@@ -183,20 +183,25 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
     __syncthreads();
     if (last) {
       __threadfence();
-      // one warp per system: strided partial sums in a fixed order, then a fixed shuffle tree
+      // one warp per system: strided partial sums in a fixed order, then a fixed shuffle tree;
+      // then one lane per system divides (all systems' FP64 divisions in one pass of warp 0)
+      __shared__ double pq_s[kMrhsMax];
       const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
       for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
         const double v = warp_sum_partials<T>(partials, (size_t)pos * gridDim.x, gridDim.x);
-        if (lane == 0) {
-          int sj = md->list[pos];
-          double alpha = md->rr[sj] / v;
-          if (!(v > 0.0) || !isfinite(alpha)) {
-            md->status = LQCD_ERR_NONFINITE;
-            md->done = 1;
-          }
-          md->alpha[sj] = alpha;
-          md->alpha_f[sj] = (float)alpha;
+        if (lane == 0) pq_s[pos] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < n_act) {
+        const int pos = threadIdx.x, sj = md->list[pos];
+        const double v = pq_s[pos];
+        const double alpha = md->rr[sj] / v;
+        if (!(v > 0.0) || !isfinite(alpha)) {
+          md->status = LQCD_ERR_NONFINITE;
+          md->done = 1;
         }
+        md->alpha[sj] = alpha;
+        md->alpha_f[sj] = (float)alpha;
       }
       if (threadIdx.x == 0) md->ticket[0] = 0u;
     }
@@ -256,21 +261,25 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
   if (!last) return;
   __threadfence();
   __shared__ int keep[kMrhsMax];
+  __shared__ double rr_s[kMrhsMax];
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int pos = threadIdx.x >> 5; pos < n_act; pos += nw) {
     const double v = warp_sum_partials<T>(partials, (size_t)pos * gridDim.x, gridDim.x);
-    if (lane == 0) {
-      int sj = md->list[pos];
-      double beta = v / md->rr[sj];
-      if (!isfinite(v)) {
-        md->status = LQCD_ERR_NONFINITE;
-        md->done = 1;
-      }
-      md->beta[sj] = beta;
-      md->beta_f[sj] = (float)beta;
-      md->rr[sj] = v;
-      keep[pos] = !(v <= md->stop2[sj]);
+    if (lane == 0) rr_s[pos] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < n_act) {  // one lane per system
+    const int pos = threadIdx.x, sj = md->list[pos];
+    const double v = rr_s[pos];
+    const double beta = v / md->rr[sj];
+    if (!isfinite(v)) {
+      md->status = LQCD_ERR_NONFINITE;
+      md->done = 1;
     }
+    md->beta[sj] = beta;
+    md->beta_f[sj] = (float)beta;
+    md->rr[sj] = v;
+    keep[pos] = !(v <= md->stop2[sj]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
