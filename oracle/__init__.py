@@ -19,7 +19,8 @@ paper (Gupta & Majumdar, arXiv:1710.09178) line by line rather than to be fast:
   linkcomp.py  8-real and 16-bit compressed SU(3) link storage   (Section 5 outlook)
 
 Each function names the passage it follows.  Where the paper is silent or
-ambiguous the oracle takes one stated reading (listed in the design doc).
+ambiguous the oracle takes one stated reading, given in the docstring of the
+module or function that depends on it.
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 against closed forms, invariants, dense linear algebra or brute force.
 """

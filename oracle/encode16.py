@@ -3,9 +3,9 @@
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Section 5 mentions single and half precision storage (and notes that the paper
-itself stays in double precision).  The compact form used for Krylov vectors in
-this build stores one site's 3 complex numbers as six int16 codes and one float32
-scale (16 bytes per site).  Definition (reading; the paper gives none), with
+itself stays in double precision).  The compact form used here for Krylov vectors
+stores one site's 3 complex numbers as six int16 codes and one float32 scale
+(16 bytes per site).  Definition (reading; the paper gives none), with
 every floating-point step in IEEE float32, round to nearest even:
 
     n   = max_i |v_i|                 over the six real components v_i (float32)

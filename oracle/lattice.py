@@ -15,7 +15,7 @@ lexicographic order; the position of a site in that ordered list is its
 half-lattice index.
 
 Staggered phases (absorbed into the links in Section 3.2; explicit in the
-operator fixed for this build): eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y),
+operator used here): eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y),
 eta_t = (-1)^(x+y+z); boundary conditions periodic in x, y, z and antiperiodic
 in t (a hop across the t boundary carries an extra factor -1).
 """

@@ -7,8 +7,8 @@ Section 3.2 writes the staggered matrix as M = 2m + sum_mu (U_mu(x) delta_{x+mu,
 into the blocks [[m_oo, D_oe], [D_eo, m_ee]] after grouping odd and even sites;
 the half-lattice operator (M^dagger M)_ee = m_ee^2 + D_eo^dagger D_oe.
 
-Normalisation fixed for this build (it differs from Section 3.2 only by rescaling
-the hopping term): the hopping operator carries a factor 1/2 and explicit phases,
+Normalisation used throughout (it differs from Section 3.2 only by rescaling the
+hopping term): the hopping operator carries a factor 1/2 and explicit phases,
 
     (D psi)(x) = 1/2 sum_mu eta_mu(x) [ U_mu(x) psi(x+mu) - U_mu(x-mu)^dagger psi(x-mu) ],
 

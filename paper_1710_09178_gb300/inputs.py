@@ -11,7 +11,7 @@ generators", OOPSLA 2014): a value is a pure function of (seed, stream,
 counter), so any site's numbers can be regenerated independently.  Uniforms
 are turned into normal deviates with the Box-Muller transform.
 
-Gauge links follow the synthetic recipe stated for this build: for every link
+Gauge links are synthetic: for every link
 (site l, direction mu) draw eight N(0,1) numbers h_a, form the traceless
 Hermitian H = sum_a h_a lambda_a / 2 (Gell-Mann matrices), take
 U = exp(i * 0.5 * H) by scaling-and-squaring of the Taylor series, and project
