@@ -121,3 +121,18 @@ def test_rational_coeffs_appendix_case(lib):
 
     c0, res, poles, err = rational_coeffs(0.25, 5e-5, 34.0, 24)
     assert rational.max_relative_error(c0, res, poles, 0.25, 5e-5, 34.0) < 1e-12
+
+
+def test_binding_constants_mirror_the_header():
+    # every status code, precision mode, option key and limit of include/lqcd.h has the same value
+    # in the Python binding (LQCD_X -> X, or LQCD_X for the status codes)
+    import paper_1710_09178_gb300 as pkg
+
+    src = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    defs = dict(re.findall(r"^#define\s+(LQCD_[A-Z0-9_]+)\s+(-?\d+)\b", src, flags=re.M))
+    assert len(defs) >= 20
+    for name, value in defs.items():
+        short = name[len("LQCD_"):]
+        py = getattr(pkg, name, getattr(pkg, short, None))
+        assert py is not None, name
+        assert py == int(value), (name, py, value)
