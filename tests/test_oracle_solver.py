@@ -1,4 +1,4 @@
-"""Pins for oracle/solvers.py (Section 4, shifted CG): dense LU solves, independent CG solves, b = 0."""
+"""Pins for oracle/solvers.py (Section 4, shifted CG): dense LU solves, independent CG solves, residual collinearity, b = 0."""
 import numpy as np
 import pytest
 
@@ -91,3 +91,23 @@ def test_shift_iteration_count():
         _, it = solvers.cg(lambda v: staggered.A_apply(U, v, mass, dims, sg), b, tol=1e-10)
         stops.append(it)
     assert abs(info["shift_iterations"] - sum(stops)) <= shifts.size  # rounding may move a stop by one
+
+
+@pytest.mark.parametrize("iters", [1, 2, 5, 12])
+def test_shifted_residuals_are_collinear_with_the_base_residual(iters):
+    # Section 4, ref. [mcg]: the shifted CG keeps every shifted residual b - (A + sigma_k) x_k equal
+    # to zeta_k times the base residual b - (A + sigma_0) x_0; a wrong sign or index anywhere in the
+    # zeta recurrence or the x_k / p_k updates breaks this at the first iterations
+    dims, mass = (4, 4, 2, 2), 0.1
+    U, b = _setup(dims, mass, gseed=5, vseed=6)
+    shifts = np.array([0.003, 0.04, 0.5, 2.0, 11.0])
+    A = lambda v, s: staggered.A_apply(U, v, mass, dims, s)
+    xs, info = solvers.multishift_cg(lambda v: A(v, shifts.min()), b, shifts, fixed_iters=iters)
+    k0 = int(np.argmin(shifts))
+    r0 = b - A(xs[k0], shifts[k0])
+    assert np.isclose(np.vdot(r0, r0).real, info["rr"], rtol=1e-10)
+    nb = np.linalg.norm(b)
+    for k, s in enumerate(shifts):
+        rk = b - A(xs[k], s)
+        assert np.linalg.norm(rk - info["zeta"][k] * r0) <= 1e-12 * nb, (k, s)
+    assert info["zeta"][k0] == 1.0
