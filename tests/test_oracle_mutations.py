@@ -1,10 +1,15 @@
-"""The oracle's pins catch plausible mistakes (Section 3.2 operator, Section 4 shifted CG).
+"""The oracle's pins catch plausible mistakes (Section 3.2 operator, Section 4 shifted CG,
+Section 3.1 fermion force, gauge force and molecular dynamics).
 
 Each case plants one mistake in an in-memory copy of an oracle module: a wrong staggered phase,
 a periodic instead of antiperiodic t boundary, a dropped 1/2, a missing dagger or conjugation,
-a wrong sign between the hops or in A, a wrong sign, power or ratio in the shifted-CG
-recurrences.  The compact pins below must all hold for the real oracle and at least one must
-fail for every mutant.  The files under oracle/ are never modified.
+a wrong sign between the hops or in A; a wrong sign, power or ratio in the shifted-CG
+recurrences; a dropped sign, phase or factor, the wrong Hermitian part or a transposed outer
+product in the fermion force; a wrong normalisation or staple in the gauge force; a wrong kick
+or drift in the Omelyan integrator.  The compact pins below (free field, anti-hermiticity,
+hermiticity, gauge covariance; residual collinearity; central finite differences of S_f and
+S_g; reversibility and the second-order energy error) must all hold for the real oracle, and
+at least one must fail for every mutant.  The files under oracle/ are never modified.
 """
 import inspect
 import itertools
@@ -132,3 +137,167 @@ def test_collinearity_catches_planted_mistake(name):
     assert a in src
     mutant = _module("solvers_copy", src.replace(a, b, 1))
     assert _collinearity_error(mutant) > 1e-6
+
+
+# ---- fermion force (Section 3.1 MD equations): central finite differences of S_f ----------
+def _force_copy(edit=None):
+    from oracle import force
+
+    src = inspect.getsource(force)
+    if edit:
+        assert edit[0] in src
+        src = src.replace(edit[0], edit[1], 1)
+    src = src.replace("from . import lattice, staggered, solvers\n", "")
+    return _module("force_copy", src, lattice=lattice, staggered=staggered, solvers=solvers)
+
+
+def _force_fd_error(fmod):
+    from scipy.linalg import expm
+
+    from oracle import rational
+
+    dims, mass = (4, 2, 2, 4), 0.1
+    U = inputs.gauge_field(dims, seed=3)
+    phi = inputs.gaussian_vector(dims, 4)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(6, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    Fa = fmod.force_components(fmod.fermion_force(U, phi, mass, dims, c0, res, poles))
+    lam = fmod.gell_mann()
+    rng = np.random.default_rng(11)
+    V = int(np.prod(dims))
+    worst, eps = 0.0, 1e-5
+    for _ in range(8):
+        l, mu, a = int(rng.integers(V)), int(rng.integers(4)), int(rng.integers(8))
+
+        def S(w):
+            U2 = U.copy()
+            U2[l, mu] = expm(1j * w * lam[a] / 2) @ U[l, mu]
+            return fmod.action_dense(U2, phi, mass, dims, c0, res, poles)
+
+        fd = (S(eps) - S(-eps)) / (2 * eps)
+        worst = max(worst, abs(fd - Fa[l, mu, a]) / max(abs(fd), 1e-2))
+    return worst
+
+
+FORCE_MUTANTS = {
+    "odd-site sign dropped": ("        O[par == 1] *= -1\n", ""),
+    "staggered phase and boundary sign dropped": (
+        "H = 0.5j * s[:, None, None] * (W - np.conj(np.transpose(W, (0, 2, 1))))",
+        "H = 0.5j * (W - np.conj(np.transpose(W, (0, 2, 1))))"),
+    "Hermitian instead of anti-Hermitian part": (
+        "(W - np.conj(np.transpose(W, (0, 2, 1))))", "(W + np.conj(np.transpose(W, (0, 2, 1))))"),
+    "factor 1 instead of 1/2": ("F[:, mu] = 0.5 * (H", "F[:, mu] = 1.0 * (H"),
+    "outer product transposed": ('np.einsum("xa,xb->xab", z[xf], np.conj(z))',
+                                 'np.einsum("xa,xb->xba", z[xf], np.conj(z))'),
+}
+
+
+def test_force_finite_differences_hold_for_the_oracle():
+    from oracle import force
+
+    assert _force_fd_error(force) < 1e-7
+
+
+@pytest.mark.parametrize("name", sorted(FORCE_MUTANTS))
+def test_force_finite_differences_catch_planted_mistake(name):
+    assert _force_fd_error(_force_copy(FORCE_MUTANTS[name])) > 1e-3
+
+
+# ---- gauge force and the Omelyan integrator (Section 3.1) --------------------------------
+def _rhmc_copy(edit=None):
+    from oracle import force, rational, rhmc
+
+    src = inspect.getsource(rhmc)
+    if edit:
+        assert edit[0] in src
+        src = src.replace(edit[0], edit[1], 1)
+    src = src.replace("from . import force as force_mod\n", "").replace(
+        "from . import lattice, rational, solvers, staggered\n", "")
+    return _module("rhmc_copy", src, force_mod=force, lattice=lattice, rational=rational, solvers=solvers,
+                   staggered=staggered)
+
+
+GDIMS, GBETA = (4, 4, 4, 4), 5.4
+
+
+def _gauge_fd_error(rmod):
+    from scipy.linalg import expm
+
+    from oracle import force
+
+    U = inputs.gauge_field(GDIMS, seed=21)
+    Fa = force.force_components(rmod.gauge_force(U, GBETA, GDIMS))
+    lam = force.gell_mann()
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for _ in range(6):
+        l, mu, a = int(rng.integers(256)), int(rng.integers(4)), int(rng.integers(8))
+
+        def S(w):
+            U2 = U.copy()
+            U2[l, mu] = expm(1j * w * lam[a] / 2) @ U[l, mu]
+            return rmod.gauge_action(U2, GBETA, GDIMS)
+
+        fd = (S(1e-5) - S(-1e-5)) / 2e-5
+        worst = max(worst, abs(fd - Fa[l, mu, a]) / max(1.0, abs(fd)))
+    return worst
+
+
+class _GaugeOnly:
+    """H = 1/2 p^2 + S_g: the integrator's pins without solves."""
+
+    def __init__(self, rmod):
+        from oracle import force
+
+        self.r, self.f = rmod, force
+
+    def force(self, U, phi):
+        return self.f.force_components(self.r.gauge_force(U, GBETA, GDIMS))
+
+    def H(self, U, p):
+        return 0.5 * float(np.sum(p * p)) + self.r.gauge_action(U, GBETA, GDIMS)
+
+
+def _integrator_pins(rmod):
+    """(reversibility error, |dH(eps)| / |dH(eps/2)|) on 4^4 with the gauge action alone."""
+    act = _GaugeOnly(rmod)
+    U = inputs.gauge_field(GDIMS, seed=23)
+    V = int(np.prod(GDIMS))
+    p = inputs.counter_normal_pairs(24, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
+    U1, p1 = rmod.integrate(U, p, None, act, 0.2, 4)
+    U2, p2 = rmod.integrate(U1, -p1, None, act, 0.2, 4)
+    rev = max(np.max(np.abs(U2 - U)), np.max(np.abs(p2 + p)))
+    H0 = act.H(U, p)
+    dH = [act.H(*rmod.integrate(U, p, None, act, 0.2, n)) - H0 for n in (4, 8)]
+    return rev, abs(dH[0]) / abs(dH[1])
+
+
+GAUGE_MUTANTS = {
+    "force normalised with beta/6": ("F = -1j * beta / 12.0 *", "F = -1j * beta / 6.0 *"),
+    "upper staple without the last dagger": ("@ dag(U[xpnu, mu]) @ dag(U[:, nu])", "@ dag(U[xpnu, mu]) @ U[:, nu]"),
+    "lower staple with the wrong first link": ("down = dag(U[xpmu_mnu, nu])", "down = dag(U[xmnu, nu])"),
+}
+
+INTEGRATOR_MUTANTS = {
+    "middle kick 1 - lambda": ("p = p - (1.0 - 2.0 * lam) * eps", "p = p - (1.0 - lam) * eps"),
+    "last kick 2 lambda": ("w = 2.0 * lam if step < nsteps - 1 else lam", "w = 2.0 * lam"),
+    "drift of a full step": ("U = update_links(U, p, 0.5 * eps)\n        p = p -", "U = update_links(U, p, eps)\n        p = p -"),
+}
+
+
+def test_gauge_force_and_integrator_pins_hold_for_the_oracle():
+    from oracle import rhmc
+
+    assert _gauge_fd_error(rhmc) < 5e-7
+    rev, ratio = _integrator_pins(rhmc)
+    assert rev < 1e-10 and 3.0 < ratio < 5.5, (rev, ratio)
+
+
+@pytest.mark.parametrize("name", sorted(GAUGE_MUTANTS))
+def test_gauge_force_finite_differences_catch_planted_mistake(name):
+    assert _gauge_fd_error(_rhmc_copy(GAUGE_MUTANTS[name])) > 1e-3
+
+
+@pytest.mark.parametrize("name", sorted(INTEGRATOR_MUTANTS))
+def test_integrator_pins_catch_planted_mistake(name):
+    rev, ratio = _integrator_pins(_rhmc_copy(INTEGRATOR_MUTANTS[name]))
+    assert rev > 1e-8 or not (3.0 < ratio < 5.5), (name, rev, ratio)
