@@ -1,14 +1,17 @@
 """The oracle's pins catch plausible mistakes (Section 3.2 operator, Section 4 shifted CG,
-Section 3.1 fermion force, gauge force and molecular dynamics).
+Section 3.1 fermion force, gauge force and molecular dynamics, Eq. ratapprx / Appendix
+rational approximation).
 
 Each case plants one mistake in an in-memory copy of an oracle module: a wrong staggered phase,
 a periodic instead of antiperiodic t boundary, a dropped 1/2, a missing dagger or conjugation,
 a wrong sign between the hops or in A; a wrong sign, power or ratio in the shifted-CG
 recurrences; a dropped sign, phase or factor, the wrong Hermitian part or a transposed outer
 product in the fermion force; a wrong normalisation or staple in the gauge force; a wrong kick
-or drift in the Omelyan integrator.  The compact pins below (free field, anti-hermiticity,
+or drift in the Omelyan integrator; a wrong residue, node order or scale in the Zolotarev
+approximation.  The compact pins below (free field, anti-hermiticity,
 hermiticity, gauge covariance; residual collinearity; central finite differences of S_f and
-S_g; reversibility and the second-order energy error) must all hold for the real oracle, and
+S_g; reversibility and the second-order energy error; the relative error of the partial
+fractions against x^{-1/2}) must all hold for the real oracle, and
 at least one must fail for every mutant.  The files under oracle/ are never modified.
 """
 import inspect
@@ -301,3 +304,43 @@ def test_gauge_force_finite_differences_catch_planted_mistake(name):
 def test_integrator_pins_catch_planted_mistake(name):
     rev, ratio = _integrator_pins(_rhmc_copy(INTEGRATOR_MUTANTS[name]))
     assert rev > 1e-8 or not (3.0 < ratio < 5.5), (name, rev, ratio)
+
+
+# ---- rational approximation (Eq. ratapprx, Appendix) --------------------------------------
+def _rational_copy(edit=None):
+    from oracle import rational
+
+    src = inspect.getsource(rational)
+    if edit:
+        assert edit[0] in src
+        src = src.replace(edit[0], edit[1], 1)
+    return _module("rational_copy", src)
+
+
+def _rational_error(rmod):
+    """Max relative error of the partial-fraction form of the 12-pole x^{-1/2} on [0.04, 16.04],
+    evaluated term by term on a dense logarithmic grid (not through the routine's own estimate)."""
+    lo, hi = 0.04, 16.04
+    c0, res, poles, _ = rmod.zolotarev_inv_sqrt(12, lo, hi)
+    x = np.exp(np.linspace(np.log(lo), np.log(hi), 40001))
+    r = np.full_like(x, c0)
+    for c, d in zip(res, poles):
+        r += c / (x + d)
+    return float(np.max(np.abs(r * np.sqrt(x) - 1.0)))
+
+
+RATIONAL_MUTANTS = {
+    "residue with the reversed pole differences": ("np.prod(np.delete(poles, k) - dk)", "np.prod(dk - np.delete(poles, k))"),
+    "zeros and poles interleaved the other way": ("poles_u = c[0::2][:n]", "poles_u = c[1::2][:n]"),
+    "wrong power of the interval scale": ("K = D * lo ** -0.5 *", "K = D * lo ** 0.5 *"),
+    "Jacobi nodes of the wrong order": ("M = 2 * n + 1 if with_c0 else 2 * n", "M = 2 * n + 2 if with_c0 else 2 * n"),
+}
+
+
+def test_rational_error_holds_for_the_oracle():
+    assert _rational_error(_rational_copy()) < 1e-10
+
+
+@pytest.mark.parametrize("name", sorted(RATIONAL_MUTANTS))
+def test_rational_error_catches_planted_mistake(name):
+    assert _rational_error(_rational_copy(RATIONAL_MUTANTS[name])) > 1e-6
