@@ -1,6 +1,6 @@
 """The oracle's pins catch plausible mistakes (Section 3.2 operator, Section 4 shifted CG,
 Section 3.1 fermion force, gauge force and molecular dynamics, Eq. ratapprx / Appendix
-rational approximation).
+rational approximation, Section 5 16-bit and compressed-link storage).
 
 Each case plants one mistake in an in-memory copy of an oracle module: a wrong staggered phase,
 a periodic instead of antiperiodic t boundary, a dropped 1/2, a missing dagger or conjugation,
@@ -8,7 +8,8 @@ a wrong sign between the hops or in A; a wrong sign, power or ratio in the shift
 recurrences; a dropped sign, phase or factor, the wrong Hermitian part or a transposed outer
 product in the fermion force; a wrong normalisation or staple in the gauge force; a wrong kick
 or drift in the Omelyan integrator; a wrong residue, node order or scale in the Zolotarev
-approximation.  The compact pins below (free field, anti-hermiticity,
+approximation; a wrong rounding or scale in the 16-bit codes, a wrong reconstruction in the
+compressed links.  The compact pins below (free field, anti-hermiticity,
 hermiticity, gauge covariance; residual collinearity; central finite differences of S_f and
 S_g; reversibility and the second-order energy error; the relative error of the partial
 fractions against x^{-1/2}) must all hold for the real oracle, and
@@ -344,3 +345,59 @@ def test_rational_error_holds_for_the_oracle():
 @pytest.mark.parametrize("name", sorted(RATIONAL_MUTANTS))
 def test_rational_error_catches_planted_mistake(name):
     assert _rational_error(_rational_copy(RATIONAL_MUTANTS[name])) > 1e-6
+
+
+# ---- 16-bit vector storage and compressed links (Section 5) --------------------------------
+def _copy_of(modname, edit=None):
+    import importlib
+
+    src = inspect.getsource(importlib.import_module("oracle." + modname))
+    if edit:
+        assert edit[0] in src
+        src = src.replace(edit[0], edit[1], 1)
+    return _module(modname + "_copy", src)
+
+
+def _encode16_pins(m):
+    """Error bound and extreme code on random sites, exact codes, ties to even."""
+    rng = np.random.default_rng(5)
+    v = (rng.normal(size=(2048, 6)) * np.exp(rng.normal(size=(2048, 1)) * 3)).astype(np.float32)
+    q, s = m.encode(v)
+    d = m.decode(q, s)
+    n = np.max(np.abs(v), axis=1)
+    imax = np.argmax(np.abs(v), axis=1)
+    bound = bool(np.all(np.abs(d - v) <= (0.5 * s + 4e-7 * n)[:, None]))
+    extreme = bool(np.all(np.abs(q[np.arange(v.shape[0]), imax]) == 32767))
+    qt, _ = m.encode(np.array([[32767.0, 2.5, -3.5, 0.5, 1.5, -0.5]], dtype=np.float32))
+    ties = bool(np.array_equal(qt[0], np.array([32767, 2, -4, 0, 2, 0], dtype=np.int16)))
+    return bound and extreme and ties
+
+
+def _linkcomp_pins(m):
+    """8-real and 16-bit round trips of random SU(3) links within their storage error."""
+    U = inputs.gauge_field((2, 2, 2, 4), seed=17).reshape(-1, 3, 3)
+    r8 = np.max(np.abs(m.decode_r8(m.encode_r8(U)) - U))
+    l16 = np.max(np.abs(m.decode_l16(m.encode_l16(U)) - U))
+    return r8 < 1e-10 and l16 < 5e-5
+
+
+STORAGE_MUTANTS = {
+    "encode16: floor instead of round to nearest": ("encode16", ("np.clip(np.rint(prod)", "np.clip(np.floor(prod)")),
+    "encode16: scale 32768": ("encode16", ("QMAX = np.float32(32767.0)", "QMAX = np.float32(32768.0)")),
+    "linkcomp: third row without conjugation": ("linkcomp", ("return np.conj(np.cross(a, b))", "return np.cross(a, b)")),
+    "linkcomp: c1 from |b1| alone": ("linkcomp", ("np.sqrt(np.maximum(N - np.abs(b1) ** 2, 0.0))",
+                                                  "np.sqrt(np.maximum(1.0 - np.abs(b1) ** 2, 0.0))")),
+    "linkcomp: b3 with the wrong conjugate": ("linkcomp", ("b3 = (a3 * rhs_b[0] + np.conj(a2) * rhs_b[1]) / N",
+                                                           "b3 = (a3 * rhs_b[0] + a2 * rhs_b[1]) / N")),
+}
+
+
+def test_storage_pins_hold_for_the_oracle():
+    assert _encode16_pins(_copy_of("encode16")) and _linkcomp_pins(_copy_of("linkcomp"))
+
+
+@pytest.mark.parametrize("name", sorted(STORAGE_MUTANTS))
+def test_storage_pins_catch_planted_mistake(name):
+    modname, edit = STORAGE_MUTANTS[name]
+    pins = _encode16_pins if modname == "encode16" else _linkcomp_pins
+    assert not pins(_copy_of(modname, edit))
