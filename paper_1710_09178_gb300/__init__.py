@@ -60,6 +60,9 @@ EXPORTED = [
 
 
 class SolveStats(ctypes.Structure):
+    """lqcd_solve_stats: iterations, reliable updates, refinement work, the FP64-class true
+    residual of every shift, kernel launches and time of one mshift_cg call."""
+
     _fields_ = [
         ("iterations", ctypes.c_int),
         ("reliable_updates", ctypes.c_int),
@@ -74,6 +77,7 @@ class SolveStats(ctypes.Structure):
     ]
 
     def as_dict(self):
+        """The fields as a dict (true_residual cut to the solve's shifts)."""
         n = self.n_shifts
         return dict(iterations=self.iterations, reliable_updates=self.reliable_updates,
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
@@ -83,6 +87,8 @@ class SolveStats(ctypes.Structure):
 
 
 class BatchProblem(ctypes.Structure):
+    """lqcd_batch_problem: one independent shifted-CG problem of mshift_cg_batch."""
+
     _fields_ = [
         ("ctx", ctypes.c_void_p), ("shifts", ctypes.POINTER(ctypes.c_double)),
         ("residues", ctypes.POINTER(ctypes.c_double)), ("n", ctypes.c_int), ("c0", ctypes.c_double),
@@ -93,6 +99,9 @@ class BatchProblem(ctypes.Structure):
 
 
 class RhmcParams(ctypes.Structure):
+    """lqcd_rhmc_params: gauge coupling, trajectory length and steps, the rational
+    approximations of the action and the heatbath, solver tolerances and precisions."""
+
     _fields_ = [
         ("beta", ctypes.c_double), ("tau", ctypes.c_double), ("nsteps", ctypes.c_int), ("lambda_", ctypes.c_double),
         ("n_act", ctypes.c_int), ("act_shifts", ctypes.POINTER(ctypes.c_double)),
@@ -106,6 +115,8 @@ class RhmcParams(ctypes.Structure):
 
 
 class TrajResult(ctypes.Structure):
+    """lqcd_traj_result: the FP64 Hamiltonian pieces before and after, dH, acceptance, solver work."""
+
     _fields_ = [
         ("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
         ("kinetic0", ctypes.c_double), ("kinetic1", ctypes.c_double), ("gauge0", ctypes.c_double),
@@ -114,10 +125,13 @@ class TrajResult(ctypes.Structure):
     ]
 
     def as_dict(self):
+        """The fields as a dict."""
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class LqcdError(RuntimeError):
+    """A non-zero status of a library call; .code is the LQCD_* status."""
+
     def __init__(self, code, msg):
         super().__init__(f"lqcd error {code}: {msg}")
         self.code = code
@@ -201,6 +215,7 @@ class Context:
         self.handle = h
 
     def close(self):
+        """Free the context (lqcd_destroy); further calls on it are invalid."""
         if getattr(self, "handle", None):
             load_library().lqcd_destroy(self.handle)
             self.handle = None
@@ -212,12 +227,14 @@ class Context:
             pass
 
     def check(self, rc):
+        """Raise LqcdError with the context's last message unless rc is LQCD_OK."""
         if rc != LQCD_OK:
             msg = load_library().lqcd_last_error(self.handle)
             raise LqcdError(rc, msg.decode() if msg else "")
         return rc
 
     def set_stream(self, stream=None):
+        """Enqueue the context's work on `stream` (a cudaStream_t; default torch's current stream)."""
         return self.check(load_library().lqcd_set_stream(self.handle, stream if stream is not None
                                                          else _current_stream()))
 
@@ -232,6 +249,7 @@ class Context:
         return self.check(load_library().lqcd_share_gauge(self.handle, src.handle))
 
     def vector_bytes(self, prec):
+        """Bytes of one internal half-lattice vector of precision prec (lqcd_vector_bytes)."""
         return int(load_library().lqcd_vector_bytes(self.handle, prec))
 
     def new_vector(self, prec):
@@ -241,12 +259,15 @@ class Context:
         return torch.empty(self.vector_bytes(prec), dtype=torch.uint8, device="cuda")
 
     def pack(self, dst, prec, src):
+        """Canonical complex128 [V/2][3] cuda tensor src -> internal vector dst of precision prec."""
         return self.check(load_library().lqcd_pack_vector(self.handle, _ptr(dst), prec, _ptr(src)))
 
     def unpack(self, dst, src, prec):
+        """Internal vector src of precision prec -> canonical complex128 [V/2][3] cuda tensor dst."""
         return self.check(load_library().lqcd_unpack_vector(self.handle, _ptr(dst), _ptr(src), prec))
 
     def apply_A(self, q, p, sigma, prec, want_dot=False):
+        """q = (A + sigma) p on internal vectors (lqcd_apply_A); returns Re<p, q> if want_dot."""
         pq = ctypes.c_double(0.0)
         self.check(load_library().lqcd_apply_A(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
                                                ctypes.byref(pq) if want_dot else None))
@@ -260,9 +281,11 @@ class Context:
         return pq.value if want_dot else None
 
     def neighbour_table(self, fwd, bwd, sign):
+        """Fill int32 [2][4][V/2] tensors with the forward and backward neighbours and hop signs."""
         return self.check(load_library().lqcd_neighbour_table(self.handle, _ptr(fwd), _ptr(bwd), _ptr(sign)))
 
     def set_option(self, key, value):
+        """lqcd_set_option(key, value) with an OPT_* key."""
         return self.check(load_library().lqcd_set_option(self.handle, int(key), float(value)))
 
     def autotune(self, prec=FP32):
@@ -272,6 +295,7 @@ class Context:
         return best.value
 
     def launch_count(self):
+        """Kernels the library has launched on this context (graph nodes counted)."""
         return int(load_library().lqcd_launch_count(self.handle))
 
 
@@ -343,12 +367,14 @@ class FermionAction:
 
     @classmethod
     def function(cls):
+        """The torch.autograd.Function class (built on first use)."""
         if cls._fn is None:
             import torch
 
             class _F(torch.autograd.Function):
                 @staticmethod
                 def forward(actx, w, ctx, shifts, residues, c0, phi, tol, prec):
+                    """S_f and, saved for backward, the force in the algebra coordinates."""
                     if bool(torch.any(w != 0)):
                         raise ValueError("FermionAction is evaluated at w = 0 (update U itself, then reset w)")
                     Falg = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device=phi.device)
@@ -358,6 +384,7 @@ class FermionAction:
 
                 @staticmethod
                 def backward(actx, grad):
+                    """dS_f/dw times the incoming gradient."""
                     (Falg,) = actx.saved_tensors
                     return grad * Falg, None, None, None, None, None, None, None
 
@@ -366,6 +393,7 @@ class FermionAction:
 
     @classmethod
     def apply(cls, w, ctx, shifts, residues, c0, phi, tol=1e-10, prec=FP32):
+        """S_f at w = 0 as a differentiable scalar; its gradient with respect to w is the force."""
         return cls.function().apply(w, ctx, shifts, residues, c0, phi, tol, prec)
 
 
@@ -448,4 +476,6 @@ def lqcd_rational_coeffs(power, lo, hi, n):
 
 
 def rational_coeffs(power, lo, hi, n):
+    """(c0, residues, poles, max relative error) of the type-(n, n) approximation of x^power on
+    [lo, hi] (lqcd_rational_coeffs)."""
     return lqcd_rational_coeffs(power, lo, hi, n)
