@@ -136,7 +136,7 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, const PartialsR
 __device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRatio& pb) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
-  const double rr = sd->rr, stop2 = sd->stop2, alpha = sd->alpha;
+  const double stop2 = sd->stop2, alpha = sd->alpha;
   const int n = sd->n, m = sd->m, iter = sd->iter, maxiter = sd->maxiter;
   const int iter_ru = sd->iter_ru, ru_interval = sd->ru_interval;
   const double ru_delta2 = sd->ru_delta2, rr_ru_max = sd->rr_ru_max;
