@@ -17,6 +17,9 @@ paper (Gupta & Majumdar, arXiv:1710.09178) line by line rather than to be fast:
   force.py     fermion force dS_f/dU of phi^dagger r(A) phi   (Section 3.1 MD equations)
   rhmc.py      gauge action and force, heatbath, Omelyan MD, Metropolis (Section 3.1)
   linkcomp.py  8-real and 16-bit compressed SU(3) link storage   (Section 5 outlook)
+  cpp/         plain FP64 C++ twin of lattice/staggered/solvers/encode16 (one-core and
+               OpenMP builds), bound by cpp_oracle.py: the host-core timings and the
+               full-size solves come from it
 
 Each function names the passage it follows.  Where the paper is silent or
 ambiguous the oracle takes one stated reading, given in the docstring of the
