@@ -308,17 +308,37 @@ def time_dslash_graph(lq, torch, Ud, prec, reps, n_fields=STREAM_FIELDS):
             c.close()
 
 
-def cpu_baseline_oracle(U, b, coeffs, iters_per_solve, sample_iters):
-    """The oracle's shifted CG on the same input, a bounded number of iterations, scaled to one solve."""
-    from oracle import solvers, staggered
+def cpu_oracle_solves(U, b, coeffs):
+    """The C++ FP64 oracle's complete shifted-CG solve of the bench workload on the host cores: once
+    with OpenMP on every core and once on one core, each to the same 1e-10 stopping rule.  Returns
+    the timings (per solve, per iteration, per half-lattice hop) and the OpenMP solve's solutions and
+    y = c0 b + sum_k c_k x_k, against which the GPU results are measured."""
+    from oracle import cpp_oracle
 
     c0, res, poles, _ = coeffs
-    t0 = time.perf_counter()
-    solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles,
-                          fixed_iters=sample_iters)
-    dt = time.perf_counter() - t0
-    per_iter_ms = dt * 1e3 / sample_iters
-    return per_iter_ms * iters_per_solve, per_iter_ms, dt
+    out = {}
+    sol = None
+    for kind, threaded in (("all_cores", True), ("one_core", False)):
+        orc = cpp_oracle.load(threaded=threaded)
+        lat = orc.lattice(DIMS, U, MASS)
+        xs, info = lat.multishift_cg(b, poles, tol=TOL)
+        out[kind] = {"ms_per_solve": info["seconds"] * 1e3, "threads": orc.threads(),
+                     "iterations": info["iterations"], "shift_iterations": int(info["shift_iterations"]),
+                     "ms_per_iteration": info["seconds"] * 1e3 / max(1, info["iterations"]),
+                     "ms_per_dslash": info["seconds_dslash"] * 1e3 / max(1, info["dslash_calls"])}
+        if sol is None:
+            tr = lat.true_residuals(b, xs, poles)
+            out[kind]["max_true_residual"] = float(tr.max())
+            sol = (xs, orc.rational_apply(b, xs, c0, res))
+        lat.close()
+    return out, sol
+
+
+def errors_vs_oracle(xs_gpu, y_gpu, sol):
+    """Per shift |x_k - x_k^oracle| / |x_k^oracle| and |y - y^oracle| / |y^oracle| (FP64 norms)."""
+    xs_o, y_o = sol
+    ex = [float(np.linalg.norm(a - o) / np.linalg.norm(o)) for a, o in zip(xs_gpu, xs_o)]
+    return {"x_k": ex, "max_x_k": max(ex), "y": float(np.linalg.norm(y_gpu - y_o) / np.linalg.norm(y_o))}
 
 
 def host_cpu():
@@ -340,49 +360,50 @@ def host_cpu():
     return {"model": model, "nproc": os.cpu_count()}
 
 
-def oracle_iterations():
-    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations_32c8.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            return int(json.load(f)["iterations"])
-    return None
-
-
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 oracle on the host cores, same metric and unit, bounded samples."""
+    """--impl reference: the C++ FP64 oracle on all host cores (OpenMP), same metric and unit.
+
+    Every timed step is one complete shifted-CG solve of the bench workload (32^3x8, 16 poles,
+    true residual 1e-10); warm-up steps run one iteration each.  Under torchrun only rank 0 runs."""
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import cpp_oracle, rational
     from paper_1710_09178_gb300 import inputs
-    from oracle import rational, solvers, staggered
 
     U = inputs.gauge_field(DIMS, seed=GAUGE_SEED)
     b = inputs.gaussian_vector(DIMS, VEC_SEED)
     lo, hi = 4 * MASS * MASS, 16 + 4 * MASS * MASS
     c0, res, poles, err = rational.zolotarev_inv_sqrt(NPOLES, lo, hi)
-    iters = oracle_iterations()
-    sample = env_int("LQCD_REF_SAMPLE_ITERS", 4)
+    orc = cpp_oracle.load(threaded=True)
+    lat = orc.lattice(DIMS, U, MASS)
     for _ in range(args.warmup):
-        solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles, fixed_iters=1)
-    per = []
+        lat.multishift_cg(b, poles, fixed_iters=1)
+    per, infos = [], []
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        solvers.multishift_cg(lambda v: staggered.A_apply(U, v, MASS, DIMS, poles.min()), b, poles,
-                              fixed_iters=sample)
-        per.append((time.perf_counter() - t0) * 1e3 / sample)
-    per_iter = statistics.mean(per)
-    value = per_iter * iters if iters else None
+        xs, info = lat.multishift_cg(b, poles, tol=TOL)
+        per.append(info["seconds"] * 1e3)
+        infos.append(info)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(per)
+    last = infos[-1]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms/solve", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES, "tol": TOL,
-                   "precision": "fp64 oracle (numpy)"},
-        "cpu_baseline": {"value": value, "unit": "ms/solve", "cores": 1, "kind": "oracle", "host": host_cpu(),
-                         "sample": f"{sample} shifted-CG iterations per step at 32^3x8, 16 shifts, scaled by the "
-                                   f"{iters} iterations the oracle needs for a full solve (tests/golden)"},
+                   "precision": "fp64 oracle (C++, OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "ms/solve", "cores": orc.threads(), "kind": "oracle",
+                         "host": host_cpu(),
+                         "sample": f"complete solves: every step is one full shifted-CG solve at 32^3x8 with 16 "
+                                   f"shifts to 1e-10 ({last['iterations']} iterations, "
+                                   f"{last['seconds'] * 1e3 / max(1, last['iterations']):.1f} ms/iteration, "
+                                   f"{last['seconds_dslash'] * 1e3 / max(1, last['dslash_calls']):.2f} ms per "
+                                   f"half-lattice hop) on {orc.threads()} OpenMP threads"},
         "e2e": {"value": value, "unit": "ms/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed": wall,
     }
+    lat.close()
     print(json.dumps(line), flush=True)
 
 
@@ -679,6 +700,7 @@ def main():
     clk = clocks.stop()
     launches_timed = sum(s["kernel_launches"] for s in stats)
     total_ms, ms_per_solve, value = replica_aggregate(sum(times), args.steps, world, dist, "cuda")
+    results = {"fp32": ([x.cpu().numpy() for x in xs], y.cpu().numpy())}  # per-result errors vs the oracle
 
     extra = {}
     if not args.quick:
@@ -686,6 +708,7 @@ def main():
         for name, prec in (("fp64", lq.FP64), ("df64", lq.DF64), ("fp32_r12", lq.FP32_R12), ("fp16fix", lq.FP16FIX),
                            ("fp32_r8", lq.FP32_R8), ("fp32_l16", lq.FP32_L16)):
             tms, sts = time_solves(lq, torch, ctx, bd, xs, y, coeffs, prec, max(2, args.steps // 2), 1, flush_buf)
+            results[name] = ([x.cpu().numpy() for x in xs], y.cpu().numpy())
             extra[name] = {"ms_per_solve": statistics.mean(tms), "iterations": sts[-1]["iterations"],
                            "algorithmic_GBps": solve_algorithmic_bytes(sts[-1], int(np.prod(DIMS)) // 2,
                                                                        prec in (lq.FP64, lq.DF64))
@@ -776,16 +799,23 @@ def main():
                          "the MD energy error is large from it (it falls as step^2; acceptance over thermalised "
                          "chains is tested on 4^4)"}
 
-    # ---- CPU baseline: the oracle, bounded sample, scaled by the FP64 iteration count -------
+    # ---- CPU baseline: the C++ FP64 oracle's complete solve on the host cores; GPU errors against it ----
     cpu = None
+    errors = None
     if rank == 0 and not args.no_cpu_baseline:
-        iters_fp64 = extra.get("fp64", {}).get("iterations") or oracle_iterations() or stats[-1]["iterations"]
-        sample = env_int("LQCD_CPU_SAMPLE_ITERS", 12)
-        val, per_iter, dt = cpu_baseline_oracle(U, b, coeffs, iters_fp64, sample)
-        cpu = {"value": val, "unit": "ms/solve", "cores": 1, "kind": "oracle", "host": host_cpu(),
-               "sample": f"{sample} iterations of the oracle's shifted CG at 32^3x8 with 16 shifts ({dt:.1f} s, "
-                         f"{per_iter:.0f} ms/iteration, numpy single thread), scaled by {iters_fp64} iterations "
-                         f"per FP64 solve"}
+        oc, sol = cpu_oracle_solves(U, b, coeffs)
+        a, o = oc["all_cores"], oc["one_core"]
+        cpu = {"value": a["ms_per_solve"], "unit": "ms/solve", "cores": a["threads"], "kind": "oracle",
+               "host": host_cpu(),
+               "sample": f"one complete solve of the workload (32^3x8, 16 shifts, true residual 1e-10, "
+                         f"{a['iterations']} iterations) by the C++ FP64 oracle with OpenMP on {a['threads']} "
+                         f"threads; the same solve on one core beside it",
+               "all_cores": a, "one_core": o}
+        errors = {name: errors_vs_oracle(xr, yr, sol) for name, (xr, yr) in results.items()}
+        errors["note"] = ("|x_k - x_k^oracle| / |x_k^oracle| per shift (shift order of the poles) and the same for "
+                          "y = c0 b + sum c_k x_k; both sides solved to a true residual of 1e-10, so each x_k "
+                          "difference is bounded by about 2 kappa_k 1e-10 (kappa_k = (16 + 4m^2 + d_k) / "
+                          "(4m^2 + d_k))")
 
     last = stats[-1]
     line = {
@@ -821,6 +851,7 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+        line["errors_vs_oracle"] = errors
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -183,8 +183,9 @@ int dslash_eo_batch(lqcd_ctx* const* ctxs, void* const* out_devs, const void* co
 int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec, double* pq_host);
 
 /*
- * lqcd_apply_A_noalloc - the same operation, arguments and results as lqcd_apply_A, for
- * callers that must not allocate device memory when they call it (device memory owned by
+ * lqcd_apply_A_noalloc - the operation, arguments and results of lqcd_apply_A for the precisions
+ * LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8 and LQCD_FP32_L16 (LQCD_DF64 gets LQCD_ERR_ARG),
+ * for callers that must not allocate device memory when they call it (device memory owned by
  * a framework allocator or a fixed budget; loops where a cudaMalloc/cudaFree and the
  * device synchronisation it brings are not acceptable).  The paper has no counterpart;
  * this is a property of the library, not of the method.
@@ -192,9 +193,10 @@ int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, in
  *     (reduction ticket, dot result, per-block partial sums, odd-parity temporary) is one
  *     static device array of 8 MiB compiled into the library, present on every GPU that
  *     loads it until the process exits.
- *   - Size limit: V/2 <= 173392 sites for LQCD_FP64 and <= 346784 for LQCD_FP32 /
- *     LQCD_FP32_R12 (e.g. 32^3 x 8 fits in every precision); larger lattices get
- *     LQCD_ERR_ARG with a message naming the limit.
+ *   - Size limit: V/2 <= 170661 sites for LQCD_FP64 and <= 341322 for the FP32 modes
+ *     (e.g. 32^3 x 8 fits in every precision, 40^3 x 8 in the FP32 modes), whatever
+ *     LQCD_OPT_DSLASH_TPS is set to; larger lattices get LQCD_ERR_ARG with a message
+ *     naming the limit.
  *   - The first call on each device looks up the array's device address (with that device
  *     current) and caches it; make that first call before any stream capture.
  *   - Every call uses the same array: calls that may overlap on the GPU (other streams,

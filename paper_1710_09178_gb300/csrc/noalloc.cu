@@ -25,12 +25,16 @@
 namespace lqcd {
 
 // layout: [0, 256) ticket (unsigned) and dot result (double at byte 8);
-//         [256, 256 + 8192*8) per-block partial sums; the rest: the odd-parity temporary vector
+//         [256, 256 + 24576*8) per-block partial sums; the rest: the odd-parity temporary vector
 constexpr size_t kScratchBytes = 8u << 20;  // 8 MiB
 constexpr size_t kPartialsOffset = 256;
-constexpr size_t kMaxPartials = 8192;
+constexpr size_t kMaxPartials = 24576;
 constexpr size_t kTmpOffset = kPartialsOffset + kMaxPartials * sizeof(double);
 constexpr size_t kMaxTmpBytes = kScratchBytes - kTmpOffset;
+// One Dslash launch writes one partial per 128-thread block, at most V/2 * 8 / 128 of them
+// (8 threads per site, the most LQCD_OPT_DSLASH_TPS allows).  The slots cover that at the largest
+// FP32 lattice the temporary admits, so the temporary's limit is the only limit, for every option.
+static_assert((kMaxTmpBytes / 24) * 8 / 128 + 1 <= kMaxPartials, "partial-sum slots below the FP32 site limit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -62,8 +66,12 @@ using namespace lqcd;
 extern "C" int lqcd_apply_A_noalloc(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, int prec,
                                     double* pq_host) {
   if (!ctx) return LQCD_ERR_ARG;
-  if (!q_dev || !p_dev || q_dev == p_dev || !(prec == LQCD_FP64 || prec == LQCD_FP32 || prec == LQCD_FP32_R12))
-    return fail(ctx, LQCD_ERR_ARG, "lqcd_apply_A_noalloc: bad argument");
+  if (!q_dev || !p_dev || q_dev == p_dev) return fail(ctx, LQCD_ERR_ARG, "lqcd_apply_A_noalloc: bad argument");
+  if (!(prec == LQCD_FP64 || prec == LQCD_FP32 || prec == LQCD_FP32_R12 || prec == LQCD_FP32_R8 ||
+        prec == LQCD_FP32_L16))
+    return fail(ctx, LQCD_ERR_ARG,
+                "lqcd_apply_A_noalloc: precision must be LQCD_FP64, LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8 or "
+                "LQCD_FP32_L16");
   Geom g = make_geom(ctx);
   size_t tmp_bytes = (prec == LQCD_FP64 ? 48 : 24) * (size_t)ctx->Vh;
   if (tmp_bytes > kMaxTmpBytes)

@@ -2,8 +2,9 @@
 
 Runs only oracle/ (and the shared seeded input generator): the FP64 shifted CG for the 16-pole
 Zolotarev approximation of x^{-1/2} on [4m^2, 16 + 4m^2], m = 0.02, to 1e-10, and records the
-iteration count and the FP64 true residual of every shift.  bench.py's reference leg times a
-bounded sample of oracle iterations and scales it by this count.
+iteration count and the FP64 true residual of every shift.  tests/test_oracle_cpp.py checks the
+C++ oracle's own full-size solve against this record (same iteration count, same residuals to
+rounding).
 
     python tests/golden/make_oracle_iterations.py
 """

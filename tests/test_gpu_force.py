@@ -1,10 +1,12 @@
 """GPU parity of the fermion force (adjoint kernel, csrc/force.cu) against the oracle (Section 3.1 MD
 force of S_f = phi^+ r(A) phi, Eq. ratapprx).
 
-Bars: FP64 force and action within 1e-8 relative of the oracle when both solve to 1e-12 (the
-solutions themselves differ by up to kappa * 1e-12); FP32 mode within 2e-5; the autograd
-wrapper returns the same components; a directional finite difference of the GPU action matches
-the GPU force.
+Bars: the FP64 adjoint kernel within 1e-12 of the oracle's force of the same solutions X_k (the
+GPU's own FP64 solve, which the force call repeats bit for bit), and the action likewise; the
+whole FP64 force within 1e-8 relative of the oracle's when each side solves to 1e-12 itself (the
+solutions then differ by up to kappa * 1e-12); FP32 mode within 2e-5; the autograd wrapper
+returns the same components; a directional finite difference of the GPU action matches the GPU
+force.
 """
 import numpy as np
 import pytest
@@ -45,6 +47,30 @@ def test_force_matches_oracle(dims, mass, n, prec, tol):
     assert np.max(np.abs(Fa.cpu().numpy() - force.force_components(oF))) <= 2 * tol * scale
     oS = force.action(U, phi, mass, dims, c0, res, poles, tol=1e-12)
     assert abs(S - oS) <= 1e-10 * abs(oS)
+
+
+@pytest.mark.parametrize("dims,mass,n", [((4, 4, 4, 4), 0.1, 8), ((10, 6, 4, 6), 0.05, 12), ((16, 16, 16, 8), 0.05, 14)])
+def test_fp64_force_kernel_matches_oracle_on_the_same_solutions(dims, mass, n):
+    # Y_k = D_oe X_k and the per-link adjoint contraction, isolated from the solver: the oracle
+    # evaluates the force of exactly the X_k the GPU solve returned
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+    from gpu_util import gpu_mshift
+    from oracle import solvers
+
+    ctx, U, phi, c0, res, poles = _setup(dims, mass, n)
+    rc, st, xs, _ = gpu_mshift(ctx, phi, poles, res, c0, tol=1e-12, prec=FP64)
+    assert rc == 0
+    V = int(np.prod(dims))
+    F = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    rc, S, st2 = lq.fermion_force(ctx, poles, res, c0, to_dev(phi), F=F, tol=1e-12, prec=FP64)
+    torch.cuda.synchronize()
+    assert rc == 0 and st2["iterations"] == st["iterations"]
+    oF = force.fermion_force(U, phi, mass, dims, c0, res, poles, xs=xs)
+    assert np.max(np.abs(F.cpu().numpy() - oF)) <= 1e-12 * np.max(np.abs(oF))
+    oS = float(np.real(np.vdot(phi, solvers.rational_apply(phi, xs, c0, res))))
+    assert abs(S - oS) <= 1e-12 * abs(oS)
 
 
 def test_autograd_wrapper_returns_the_force():

@@ -1,9 +1,12 @@
 """GPU parity of the shifted CG (Section 4, ref. [mcg]) and the rational application (Eq. ratapprx).
 
 Bars:
-  - FP64, fixed iteration count (no shift stopped): every x_k within 1e-11 relative of
-    the oracle run for the same number of iterations (the two differ only in
-    the summation order of the dot products);
+  - FP64, fixed iteration count (no shift stopped): every x_k within 1e-12 relative of
+    the oracle run for the same number of iterations (the two differ only in the
+    summation order of the dot products and in when the x_k, p_k updates are applied);
+    double-FP32 (~48-bit arithmetic) within 1e-11;
+  - FP64 without refinement, converged: the same stopping iteration for every shift as
+    the oracle, and every x_k within 1e-12 relative of the oracle's;
   - converged solves, every precision: the FP64 true residual |b - (A+d_k)x_k|/|b|
     computed by the oracle is <= the requested 1e-10 for every shift, and x_k is within
     kappa_k * 2e-10 of the oracle's converged solution (kappa_k bounds the condition number);
@@ -41,8 +44,27 @@ def test_fp64_fixed_iterations_match_oracle(dims, iters, prec):
     assert rc == lq.LQCD_ERR_NOT_CONVERGED and st["iterations"] == iters
     oxs, info = solvers.multishift_cg(lambda v: staggered.A_apply(U, v, mass, dims, poles.min()), b, poles,
                                       fixed_iters=iters)
+    bar = 1e-12 if prec == FP64 else 1e-11
     for x, ox in zip(xs, oxs):
-        assert rel_norm(x, ox) < 1e-11
+        assert rel_norm(x, ox) < bar
+
+
+def test_fp64_fixed_iterations_match_oracle_32c8():
+    # the bench workload (32^3 x 8, m 0.02, 16-pole x^{-1/2}, gauge seed 5, source seed 6) in FP64
+    # for 20 iterations with no shift stopped, against the C++ oracle's 20 iterations: 1e-12
+    import paper_1710_09178_gb300 as lq
+    from oracle import cpp_oracle
+
+    dims, mass, iters = (32, 32, 32, 8), 0.02, 20
+    ctx, U = make_context(dims, mass, gauge_seed=5)
+    b = inputs.gaussian_vector(dims, 6)
+    c0, res, poles, _ = lq.rational_coeffs(-0.5, 4 * mass ** 2, 16 + 4 * mass ** 2, 16)
+    ctx.set_option(lq.OPT_REFINE, 0)
+    rc, st, xs, _ = gpu_mshift(ctx, b, poles, tol=1e-300, maxiter=iters, prec=FP64)
+    assert rc == lq.LQCD_ERR_NOT_CONVERGED and st["iterations"] == iters
+    oxs, _ = cpp_oracle.load(threaded=True).lattice(dims, U, mass).multishift_cg(b, poles, fixed_iters=iters)
+    for x, ox in zip(xs, oxs):
+        assert rel_norm(x, ox) < 1e-12
 
 
 def _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec, tol=1e-10):
@@ -218,31 +240,53 @@ def test_fp64_unrefined_solve_matches_oracle_with_same_stopping_rule(dims, mass,
     assert st["iterations"] == info["iterations"]
     assert st["shift_iterations"] == info["shift_iterations"]  # every shift stopped in the same iteration
     for x, ox in zip(xs, oxs):
-        assert rel_norm(x, ox) < 1e-9
+        assert rel_norm(x, ox) < 1e-12
     otr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, oxs, poles)
     assert np.allclose(st["true_residual"], otr, rtol=0.1, atol=1e-12)  # near tol the residuals differ at rounding level
 
 
-@pytest.mark.parametrize("prec,power", [(FP32, -0.5), (DF64, -0.5), (FP32, 0.25)])
-def test_full_size_32c8_solve_certified_by_oracle(prec, power):
-    # the benchmark's workload and launch configuration (32^3 x 8, m 0.02, 16-pole x^{-1/2} on
-    # [4m^2, 16 + 4m^2], gauge seed 5, source seed 6, default options; and the heatbath's x^{1/4}):
-    # the oracle's FP64 true residual of every returned x_k is at most tol and equals the one the
-    # solve reports, and the returned y is the oracle's c0 b + sum_k c_k x_k of the returned x_k
+@pytest.fixture(scope="module")
+def oracle_32c8():
+    """The C++ oracle's lattice for the bench workload (32^3 x 8, m 0.02, gauge seed 5) and its own
+    converged 16-pole x^{-1/2} and x^{1/4} solves of source seed 6, with the library's coefficients."""
+    import paper_1710_09178_gb300 as lq
+    from oracle import cpp_oracle
+
     dims, mass = (32, 32, 32, 8), 0.02
-    ctx, U = make_context(dims, mass, gauge_seed=5)
+    from gpu_util import seeded_gauge
+
+    U = seeded_gauge(dims, 5)
     b = inputs.gaussian_vector(dims, 6)
+    lat = cpp_oracle.load(threaded=True).lattice(dims, U, mass)
     lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
-    if power == -0.5:
-        c0, res, poles, _ = rational.zolotarev_inv_sqrt(16, lo, hi)
-    else:
-        c0, res, poles, _ = rational.remez_power(power, lo, hi, 16)
+    out = {}
+    for power in (-0.5, 0.25):
+        c0, res, poles, _ = lq.rational_coeffs(power, lo, hi, 16)
+        oxs, _ = lat.multishift_cg(b, poles, tol=1e-10)
+        out[power] = (c0, res, poles, oxs)
+    return dims, mass, U, b, lat, out
+
+
+@pytest.mark.parametrize("prec,power", [(FP32, -0.5), (DF64, -0.5), (FP64, -0.5), (FP32, 0.25)])
+def test_full_size_32c8_solve_certified_by_oracle(oracle_32c8, prec, power):
+    # the benchmark's workload and launch configuration (32^3 x 8, m 0.02, 16-pole x^{-1/2} on
+    # [4m^2, 16 + 4m^2] from lqcd_rational_coeffs, gauge seed 5, source seed 6, default options; and
+    # the heatbath's x^{1/4}): the oracle's FP64 true residual of every returned x_k is at most tol and
+    # equals the one the solve reports; every x_k is within 2 kappa_k tol of the oracle's own solve
+    # (kappa_k = (16 + 4m^2 + d_k) / (4m^2 + d_k) bounds the condition number of A + d_k); the returned
+    # y is the oracle's c0 b + sum_k c_k x_k of the returned x_k
+    dims, mass, U, b, lat, orc = oracle_32c8
+    c0, res, poles, oxs = orc[power]
+    ctx, _ = make_context(dims, mass, gauge_seed=5)
     rc, st, xs, y = gpu_mshift(ctx, b, poles, res, c0, prec=prec, want_y=True)
     assert rc == 0
-    tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), b, xs, poles)
+    tr = lat.true_residuals(b, xs, poles)
     assert np.all(tr <= 1e-10), tr
     rep = np.array(st["true_residual"][: len(poles)])
     assert np.all(np.abs(rep - tr) <= 1e-12 + 2e-3 * tr), (rep, tr)
+    lmin = 4 * mass ** 2
+    for x, ox, s in zip(xs, oxs, poles):
+        assert rel_norm(x, ox) <= 2 * (16 + lmin + s) / (lmin + s) * 1e-10
     yo = solvers.rational_apply(b, xs, c0, res)
     assert rel_norm(y, yo) < 1e-13
 

@@ -227,3 +227,22 @@ def test_encode16_matches_numpy_and_rounds_half_to_even(orc):
     # components at (k + 1/2) / 32767 of the norm are exact float32 ties
     qt, _ = orc.encode16(np.array([[32767.0, 2.5, -3.5, 0.5, 1.5, -0.5]], dtype=np.float32))
     assert np.array_equal(qt[0], np.array([32767, 2, -4, 0, 2, 0], dtype=np.int16))
+
+
+def test_full_size_solve_reproduces_the_numpy_oracle_record():
+    # the 32^3 x 8 workload (16-pole x^{-1/2}, m = 0.02, tol 1e-10) solved by the numpy oracle once
+    # (tests/golden/oracle_iterations_32c8.json, written by make_oracle_iterations.py): the C++ oracle
+    # stops at the same iteration with the same true residuals up to rounding
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_iterations_32c8.json")) as f:
+        rec = json.load(f)
+    dims, mass = (32, 32, 32, 8), rec["mass"]
+    U, b = inputs.gauge_field(dims, seed=rec["gauge_seed"]), inputs.gaussian_vector(dims, rec["source_seed"])
+    c0, res, poles, err = rational.zolotarev_inv_sqrt(rec["poles"], 4 * mass ** 2, 16 + 4 * mass ** 2)
+    lat = cpp_oracle.load(threaded=True).lattice(dims, U, mass)
+    xs, info = lat.multishift_cg(b, poles, tol=rec["tol"])
+    assert info["iterations"] == rec["iterations"]
+    tr = lat.true_residuals(b, xs, poles)
+    assert np.allclose(tr, rec["true_residuals"], rtol=1e-4, atol=0)
