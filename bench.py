@@ -25,7 +25,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -75,16 +74,16 @@ def kernel_source_hash():
 
 
 def profiled_traffic(workload_key):
-    """DRAM bytes per launch of the FP32 Dslash from the committed ncu summary, if it matches this source."""
-    p = os.path.join(ROOT, "profiles", "dslash_fp32_32c8.md")
+    """DRAM bytes per launch of the FP32 Dslash from the committed ncu record
+    (profiles/dslash_fp32_32c8.json), if it was captured on this kernel source."""
+    p = os.path.join(ROOT, "profiles", "dslash_fp32_32c8.json")
     if not os.path.exists(p):
         return None
-    txt = open(p).read()
-    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("source_hash") != kernel_source_hash():
         return None
-    return float(t.group(1))
+    return float(rec["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -410,12 +409,16 @@ def run_reference(args, rank, world):
 TRAJ_DIMS, TRAJ_MASS, TRAJ_BETA, TRAJ_TAU, TRAJ_STEPS, TRAJ_POLES = (24, 24, 24, 6), 0.025, 5.4, 1.0, 25, 16
 
 
-def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS):
+def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS, n_therm=0):
     """RHMC trajectories on 24^3x6 (beta 5.4, m 0.025, 16-pole x^{-1/2} and x^{1/4}, Omelyan tau 1, 25 steps).
 
     Momenta, Gaussian sources and Metropolis numbers come from the counter-based generator (seed 9
     and per-trajectory streams).  MD force solves in mixed precision to md_tol; heatbath and
-    Hamiltonian solves in mixed precision to a true FP64 residual of 1e-10."""
+    Hamiltonian solves in mixed precision to a true FP64 residual of 1e-10.  The first n_therm
+    trajectories thermalise the synthetic start: they are accepted whatever their dH (Metropolis
+    number 0), which leaves the chain's fixed point alone and only shortens the approach to it; the
+    remaining n_traj - n_therm use the Metropolis test.  Every trajectory's result carries the
+    plaquette action per site after it."""
     from paper_1710_09178_gb300 import inputs
 
     lo, hi = 4 * TRAJ_MASS ** 2, 16 + 4 * TRAJ_MASS ** 2
@@ -429,7 +432,7 @@ def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS):
     for t in range(n_traj):
         mom = inputs.counter_normal_pairs(9000 + t, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
         xi = inputs.gaussian_vector(TRAJ_DIMS, 9500 + t)
-        uni = float(inputs.counter_uniform(9999, np.array([t], dtype=np.uint64), 0)[0])
+        uni = 0.0 if t < n_therm else float(inputs.counter_uniform(9999, np.array([t], dtype=np.uint64), 0)[0])
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         md = torch.from_numpy(mom).cuda()
@@ -440,9 +443,28 @@ def run_trajectories(lq, torch, n_traj, md_tol=1e-7, nsteps=TRAJ_STEPS):
         e1.record()
         e1.synchronize()
         res["event_ms"] = e0.elapsed_time(e1)
+        res["therm"] = t < n_therm
+        res["plaquette_action_per_site"] = (res["gauge1"] if res["accepted"] else res["gauge0"]) / TRAJ_BETA / (6 * V)
         out.append(res)
     ctx.close()
     return out
+
+
+def rhmc_summary(tr, nsteps):
+    """Acceptance and <exp(-dH)> over the Metropolis trajectories of run_trajectories."""
+    meas = [r for r in tr if not r["therm"]]
+    dh = np.array([r["dH"] for r in meas])
+    ex = np.exp(-dh)
+    return {"workload": "24^3x6", "beta": TRAJ_BETA, "mass": TRAJ_MASS, "tau": TRAJ_TAU, "steps": nsteps,
+            "poles": TRAJ_POLES, "thermalising_trajectories": len(tr) - len(meas), "measured_trajectories": len(meas),
+            "acceptance": float(np.mean([r["accepted"] for r in meas])) if meas else None,
+            "mean_exp_minus_dH": float(ex.mean()) if meas else None,
+            "stderr_exp_minus_dH": float(ex.std(ddof=1) / np.sqrt(len(ex))) if len(ex) > 1 else None,
+            "mean_dH": float(dh.mean()) if meas else None,
+            "dH": [r["dH"] for r in tr], "accepted": [r["accepted"] for r in tr],
+            "plaquette_action_per_site": [r["plaquette_action_per_site"] for r in tr],
+            "ms_per_trajectory": float(np.median([r["event_ms"] for r in tr])),
+            "solves_per_trajectory": tr[-1]["solves"], "iterations_per_trajectory": tr[-1]["iterations"]}
 
 
 C4_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 4), (16, 16, 16, 4), (16, 16, 16, 8)]
@@ -613,6 +635,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
+    ap.add_argument("--therm", type=int, default=20, help="thermalising trajectories before the --rhmc ones")
     ap.add_argument("--batch", action="store_true", help="run the 64-lattice batched workload, print one JSON line")
     args = ap.parse_args()
     if args.batch:
@@ -633,19 +656,8 @@ def main():
         __graft_entry__.build()
         import paper_1710_09178_gb300 as lq
 
-        tr = run_trajectories(lq, torch, args.rhmc, nsteps=args.traj_steps)
-        dh = np.array([r["dH"] for r in tr])
-        ex = np.exp(-dh)
-        print(json.dumps({"rhmc": {"workload": "24^3x6", "beta": TRAJ_BETA, "mass": TRAJ_MASS, "tau": TRAJ_TAU,
-                                   "steps": args.traj_steps, "trajectories": len(tr),
-                                   "acceptance": float(np.mean([r["accepted"] for r in tr])),
-                                   "mean_exp_minus_dH": float(ex.mean()),
-                                   "stderr_exp_minus_dH": float(ex.std(ddof=1) / np.sqrt(len(ex))) if len(ex) > 1 else None,
-                                   "dH": dh.tolist(), "ms_per_trajectory": [r["event_ms"] for r in tr],
-                                   "solves_per_trajectory": tr[-1]["solves"],
-                                   "iterations_per_trajectory": tr[-1]["iterations"],
-                                   "plaquette_action_per_site": [r["gauge1"] / TRAJ_BETA / (6 * np.prod(TRAJ_DIMS)) for r in tr]}}),
-              flush=True)
+        tr = run_trajectories(lq, torch, args.rhmc + args.therm, nsteps=args.traj_steps, n_therm=args.therm)
+        print(json.dumps({"rhmc": rhmc_summary(tr, args.traj_steps)}), flush=True)
         return
     if args.profile:
         run_profile_target(args.profile, args.prec)

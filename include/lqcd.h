@@ -77,6 +77,7 @@ typedef struct {
   double true_residual[LQCD_MAX_SHIFTS]; /* |b - (A + d_k) x_k| / |b| in FP64, per shift */
   double ms;              /* wall time of the call on its stream (CUDA events) */
   int shift_iterations;   /* sum over base iterations of the shifts still iterating */
+  int df_iterations;      /* mixed modes: base iterations of the double-FP32 first phase (LQCD_OPT_DF_SWITCH) */
 } lqcd_solve_stats;
 
 /*
@@ -235,6 +236,13 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
                                         double-FP32 arithmetic (FP32 hi/lo pairs, exact products, TwoSum
                                         accumulation; ~48-bit, FP32 units only) and the solutions kept as
                                         double-FP32 pairs during the solve (default), 0 = FP64 */
+#define LQCD_OPT_DF_SWITCH 9         /* mixed modes with double-FP32 residuals: the shifted CG runs its first
+                                        iterations in double-FP32 (as LQCD_DF64) and changes to the mode's FP32
+                                        arithmetic at the first window end with |r| <= value |b| (default 1e-3;
+                                        0 = FP32 from the start).  FP32 rounding at iteration j perturbs the
+                                        shifted solutions by about eps_32 |r_j|, and they get no reliable
+                                        update of their own: starting in double-FP32 leaves them far closer
+                                        to the tolerance and shortens the per-shift refinement */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*
@@ -388,6 +396,17 @@ int rhmc_trajectory(lqcd_ctx* ctx, const lqcd_rhmc_params* prm, double* U_dev, c
  */
 int lqcd_rational_coeffs(double power, double lo, double hi, int n, double* c0, double* residues, double* poles,
                          double* err);
+
+/*
+ * lqcd_bounds_word - error word of the debug build's device-side neighbour-index checks
+ * (liblqcd_debug.so, built with LQCD_DEBUG_BOUNDS; a property of the library, the paper has no
+ * counterpart).  In that build every kernel that computes a neighbour
+ * address tests it against [0, V) before using it; a failing test sets bit 1 (LQCD_BOUNDS_NEIGHBOUR)
+ * of the context's word, the hop reads site 0 instead, and the kernel neither faults nor traps.
+ * Waits for the device, then stores the word (0 = no violation) in *word.  The release build stores
+ * 0 and returns LQCD_ERR_STATE.
+ */
+int lqcd_bounds_word(lqcd_ctx* ctx, unsigned* word);
 
 /* Number of kernels the library has launched on this context (graph nodes counted). */
 long long lqcd_launch_count(const lqcd_ctx* ctx);

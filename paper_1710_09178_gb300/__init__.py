@@ -19,6 +19,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblqcd.so")
+LIB_DEBUG_PATH = os.path.join(HERE, "liblqcd_debug.so")
 
 LQCD_OK = 0
 LQCD_ERR_ARG = 1
@@ -46,6 +47,7 @@ OPT_DSLASH_TPS = 5
 OPT_RELIABLE_DELTA = 6
 OPT_PDL = 7
 OPT_DF_RESID = 8
+OPT_DF_SWITCH = 9
 
 MAX_SHIFTS = 32
 MAX_BATCH = 128
@@ -55,7 +57,7 @@ EXPORTED = [
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
     "fermion_force", "rhmc_trajectory", "mshift_cg_batch", "lqcd_autotune",
-    "lqcd_share_gauge", "dslash_eo_batch",
+    "lqcd_share_gauge", "dslash_eo_batch", "lqcd_bounds_word",
 ]
 
 
@@ -74,6 +76,7 @@ class SolveStats(ctypes.Structure):
         ("true_residual", ctypes.c_double * MAX_SHIFTS),
         ("ms", ctypes.c_double),
         ("shift_iterations", ctypes.c_int),
+        ("df_iterations", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -83,7 +86,7 @@ class SolveStats(ctypes.Structure):
                     refine_iterations=self.refine_iterations, refined_shifts=self.refined_shifts,
                     refine_rounds=self.refine_rounds,
                     kernel_launches=self.kernel_launches, true_residual=list(self.true_residual[:n]), ms=self.ms,
-                    shift_iterations=self.shift_iterations)
+                    shift_iterations=self.shift_iterations, df_iterations=self.df_iterations)
 
 
 class BatchProblem(ctypes.Structure):
@@ -138,6 +141,7 @@ class LqcdError(RuntimeError):
 
 
 _lib = None
+_lib_debug = None
 
 
 def load_library(path: str = LIB_PATH):
@@ -145,6 +149,20 @@ def load_library(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _bind(path)
+    return _lib
+
+
+def load_debug_library():
+    """liblqcd_debug.so, the build with device-side neighbour-index checks (build.build(debug=True)),
+    loaded beside the release library; pass it to Context(..., lib=...) to run contexts on it."""
+    global _lib_debug
+    if _lib_debug is None:
+        _lib_debug = _bind(LIB_DEBUG_PATH)
+    return _lib_debug
+
+
+def _bind(path):
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` first")
     lib = ctypes.CDLL(path)
@@ -175,12 +193,12 @@ def load_library(path: str = LIB_PATH):
         "lqcd_autotune": (i, [vp, i, ctypes.POINTER(ctypes.c_int)]),
         "lqcd_share_gauge": (i, [vp, vp]),
         "dslash_eo_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
+        "lqcd_bounds_word": (i, [vp, ctypes.POINTER(ctypes.c_uint)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
 
 
@@ -201,8 +219,9 @@ def _current_stream():
 class Context:
     """Owns one lqcd_ctx (device workspace and internal gauge copies) for a lattice."""
 
-    def __init__(self, dims, mass, stream=None):
-        lib = load_library()
+    def __init__(self, dims, mass, stream=None, lib=None):
+        lib = lib if lib is not None else load_library()
+        self.lib = lib
         self.dims = tuple(int(d) for d in dims)
         self.mass = float(mass)
         self.V = int(np.prod(self.dims))
@@ -217,7 +236,7 @@ class Context:
     def close(self):
         """Free the context (lqcd_destroy); further calls on it are invalid."""
         if getattr(self, "handle", None):
-            load_library().lqcd_destroy(self.handle)
+            self.lib.lqcd_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -229,28 +248,28 @@ class Context:
     def check(self, rc):
         """Raise LqcdError with the context's last message unless rc is LQCD_OK."""
         if rc != LQCD_OK:
-            msg = load_library().lqcd_last_error(self.handle)
+            msg = self.lib.lqcd_last_error(self.handle)
             raise LqcdError(rc, msg.decode() if msg else "")
         return rc
 
     def set_stream(self, stream=None):
         """Enqueue the context's work on `stream` (a cudaStream_t; default torch's current stream)."""
-        return self.check(load_library().lqcd_set_stream(self.handle, stream if stream is not None
+        return self.check(self.lib.lqcd_set_stream(self.handle, stream if stream is not None
                                                          else _current_stream()))
 
     def set_gauge(self, U):
         """U: complex128 cuda tensor of shape (V, 4, 3, 3), canonical layout."""
         assert tuple(U.shape) == (self.V, 4, 3, 3) and U.is_contiguous()
-        return self.check(load_library().lqcd_set_gauge(self.handle, _ptr(U)))
+        return self.check(self.lib.lqcd_set_gauge(self.handle, _ptr(U)))
 
     def share_gauge(self, src):
         """Use src's gauge copies (lqcd_share_gauge); src must outlive this context."""
         self._gauge_src = src  # keep the owner alive
-        return self.check(load_library().lqcd_share_gauge(self.handle, src.handle))
+        return self.check(self.lib.lqcd_share_gauge(self.handle, src.handle))
 
     def vector_bytes(self, prec):
         """Bytes of one internal half-lattice vector of precision prec (lqcd_vector_bytes)."""
-        return int(load_library().lqcd_vector_bytes(self.handle, prec))
+        return int(self.lib.lqcd_vector_bytes(self.handle, prec))
 
     def new_vector(self, prec):
         """Uninitialised internal vector of precision prec (uint8 cuda tensor)."""
@@ -260,48 +279,48 @@ class Context:
 
     def pack(self, dst, prec, src):
         """Canonical complex128 [V/2][3] cuda tensor src -> internal vector dst of precision prec."""
-        return self.check(load_library().lqcd_pack_vector(self.handle, _ptr(dst), prec, _ptr(src)))
+        return self.check(self.lib.lqcd_pack_vector(self.handle, _ptr(dst), prec, _ptr(src)))
 
     def unpack(self, dst, src, prec):
         """Internal vector src of precision prec -> canonical complex128 [V/2][3] cuda tensor dst."""
-        return self.check(load_library().lqcd_unpack_vector(self.handle, _ptr(dst), _ptr(src), prec))
+        return self.check(self.lib.lqcd_unpack_vector(self.handle, _ptr(dst), _ptr(src), prec))
 
     def apply_A(self, q, p, sigma, prec, want_dot=False):
         """q = (A + sigma) p on internal vectors (lqcd_apply_A); returns Re<p, q> if want_dot."""
         pq = ctypes.c_double(0.0)
-        self.check(load_library().lqcd_apply_A(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
+        self.check(self.lib.lqcd_apply_A(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
                                                ctypes.byref(pq) if want_dot else None))
         return pq.value if want_dot else None
 
     def apply_A_noalloc(self, q, p, sigma, prec, want_dot=False):
         """apply_A with the library's static scratch instead of allocated scratch (see include/lqcd.h)."""
         pq = ctypes.c_double(0.0)
-        self.check(load_library().lqcd_apply_A_noalloc(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
+        self.check(self.lib.lqcd_apply_A_noalloc(self.handle, _ptr(q), _ptr(p), float(sigma), prec,
                                                        ctypes.byref(pq) if want_dot else None))
         return pq.value if want_dot else None
 
     def neighbour_table(self, fwd, bwd, sign):
         """Fill int32 [2][4][V/2] tensors with the forward and backward neighbours and hop signs."""
-        return self.check(load_library().lqcd_neighbour_table(self.handle, _ptr(fwd), _ptr(bwd), _ptr(sign)))
+        return self.check(self.lib.lqcd_neighbour_table(self.handle, _ptr(fwd), _ptr(bwd), _ptr(sign)))
 
     def set_option(self, key, value):
         """lqcd_set_option(key, value) with an OPT_* key."""
-        return self.check(load_library().lqcd_set_option(self.handle, int(key), float(value)))
+        return self.check(self.lib.lqcd_set_option(self.handle, int(key), float(value)))
 
     def autotune(self, prec=FP32):
         """Pick the fastest Dslash threads-per-site on this lattice (lqcd_autotune); returns it."""
         best = ctypes.c_int(0)
-        self.check(load_library().lqcd_autotune(self.handle, int(prec), ctypes.byref(best)))
+        self.check(self.lib.lqcd_autotune(self.handle, int(prec), ctypes.byref(best)))
         return best.value
 
     def launch_count(self):
         """Kernels the library has launched on this context (graph nodes counted)."""
-        return int(load_library().lqcd_launch_count(self.handle))
+        return int(self.lib.lqcd_launch_count(self.handle))
 
 
 def dslash_eo(ctx: Context, out, in_, out_parity: int, prec: int):
     """out = D_oe in (out_parity=1) or D_eo in (out_parity=0); internal vectors of precision prec."""
-    return ctx.check(load_library().dslash_eo(ctx.handle, _ptr(out), _ptr(in_), int(out_parity), int(prec)))
+    return ctx.check(ctx.lib.dslash_eo(ctx.handle, _ptr(out), _ptr(in_), int(out_parity), int(prec)))
 
 
 def dslash_eo_batch(ctxs, outs, ins, out_parities, prec: int):
@@ -311,7 +330,7 @@ def dslash_eo_batch(ctxs, outs, ins, out_parities, prec: int):
     if not (len(outs) == len(ins) == len(out_parities) == n):
         raise ValueError("dslash_eo_batch: lists of different lengths")
     H = ctypes.c_void_p * n
-    rc = load_library().dslash_eo_batch(H(*[c.handle.value for c in ctxs]), H(*[_ptr(o) for o in outs]),
+    rc = ctxs[0].lib.dslash_eo_batch(H(*[c.handle.value for c in ctxs]), H(*[_ptr(o) for o in outs]),
                                         H(*[_ptr(x) for x in ins]),
                                         (ctypes.c_int * n)(*[int(p) for p in out_parities]), n, int(prec))
     return ctxs[0].check(rc)
@@ -324,7 +343,7 @@ def mshift_cg(ctx: Context, shifts, residues, c0, b, xs=None, y=None, tol=1e-10,
     b, xs[k], y: complex128 cuda tensors of shape (Vh, 3) (canonical layout).
     Returns (status, stats dict).
     """
-    lib = load_library()
+    lib = ctx.lib
     n = len(shifts)
     sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
     rs = (ctypes.c_double * n)(*[float(c) for c in residues]) if residues is not None else None
@@ -344,7 +363,7 @@ def fermion_force(ctx: Context, shifts, residues, c0, phi, F=None, Falg=None, wa
     Returns (status, S_f or None, stats dict).  dS_f/dw^a = tr(lambda^a F) = Falg[..., a] for
     U -> exp(i w.lambda/2) U.
     """
-    lib = load_library()
+    lib = ctx.lib
     n = len(shifts)
     sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
     rs = (ctypes.c_double * n)(*[float(c) for c in residues])
@@ -403,7 +422,7 @@ def mshift_cg_batch(problems, nthreads=16, raise_on_error=True):
     problems: list of dicts with keys ctx, shifts, residues, c0, b, xs (list or None), y (or None),
     tol, maxiter, prec.  Returns (status, [status per problem], [stats dict per problem]).
     """
-    lib = load_library()
+    lib = problems[0]["ctx"].lib if problems else load_library()
     n = len(problems)
     arr = (BatchProblem * n)()
     keep = []
@@ -437,7 +456,7 @@ def rhmc_trajectory(ctx: Context, U, mom, xi, uniform, beta, tau, nsteps, act, h
     """One RHMC trajectory (see include/lqcd.h).  act = (c0, residues, shifts) of x^{-1/2},
     heat = (c0, residues, shifts) of x^{1/4}; U (V,4,3,3) complex128 updated in place if accepted;
     mom (V,4,8) float64; xi (Vh,3) complex128.  Returns (status, result dict)."""
-    lib = load_library()
+    lib = ctx.lib
     arr = lambda v: (ctypes.c_double * len(v))(*[float(x) for x in v])
     a_c0, a_res, a_sh = act
     keep = [arr(a_sh), arr(a_res)]

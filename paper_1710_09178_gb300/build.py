@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblqcd.so")
+# the debug build: every computed neighbour address checked on the device (csrc/bounds.h)
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "liblqcd_debug.so")
 
 CU_SOURCES = ["capi.cu", "pack.cu", "dslash.cu", "solver.cu", "mrhs.cu", "force.cu", "trajectory.cu", "batch.cu", "noalloc.cu", "df64.cu"]
 CPP_SOURCES = ["rational.cpp"]
@@ -48,33 +51,36 @@ def _sources_newer_than(target: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link liblqcd.so; returns its path.  Skips the work when up to date."""
-    if not force and not ptxas_info and not _sources_newer_than(LIB):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile and link liblqcd.so (debug=True: liblqcd_debug.so, with the device-side neighbour-index
+    checks); returns its path.  Skips the work when up to date."""
+    lib, bdir = (LIB_DEBUG, BUILD_DEBUG) if debug else (LIB, BUILD)
+    if not force and not ptxas_info and not _sources_newer_than(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = nvcc_path()
+    defs = ["-DLQCD_DEBUG_BOUNDS"] if debug else []
     jobs = []
     for src in CU_SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(bdir, src + ".o")
         extra = ["-Xptxas", "-v"] if ptxas_info else []
-        jobs.append([nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj])
+        jobs.append([nvcc, *ARCH, *NVCC_FLAGS, *defs, *extra, "-c", os.path.join(CSRC, src), "-o", obj])
     for src in CPP_SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
-        jobs.append(["g++", *CXX_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj])
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        obj = os.path.join(bdir, src + ".o")
+        jobs.append(["g++", *CXX_FLAGS, *defs, "-c", os.path.join(CSRC, src), "-o", obj])
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose or ptxas_info:
         for o in outs:
             if o.strip():
                 print(o, file=sys.stderr)
-    objs = [os.path.join(BUILD, s + ".o") for s in CU_SOURCES + CPP_SOURCES]
-    tmp = LIB + ".tmp"
+    objs = [os.path.join(bdir, s + ".o") for s in CU_SOURCES + CPP_SOURCES]
+    tmp = lib + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

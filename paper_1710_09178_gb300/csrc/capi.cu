@@ -23,6 +23,9 @@ Geom make_geom(const lqcd_ctx* ctx) {
   g.dnx = make_fastdiv((unsigned)g.nx);
   g.dny = make_fastdiv((unsigned)g.ny);
   g.dnz = make_fastdiv((unsigned)g.nz);
+#ifdef LQCD_DEBUG_BOUNDS
+  g.err = ctx->bounds_word;
+#endif
   return g;
 }
 
@@ -76,6 +79,13 @@ int lqcd_create(lqcd_ctx** out, const int dims[4], double mass, void* stream) {
   c->Vh = V / 2;
   c->mass = mass;
   c->stream = static_cast<cudaStream_t>(stream);
+#ifdef LQCD_DEBUG_BOUNDS
+  if (cudaMalloc(&c->bounds_word, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->bounds_word, 0, sizeof(unsigned)) != cudaSuccess) {
+    delete c;
+    return LQCD_ERR_CUDA;
+  }
+#endif
   *out = c;
   return LQCD_OK;
 }
@@ -92,7 +102,8 @@ int lqcd_destroy(lqcd_ctx* ctx) {
     for (void* b : g)
       if (b) cudaFree(b);
   }
-  void* bufs[] = {ctx->partials, ctx->tickets, ctx->scalars, ctx->tmp_odd};
+  for (auto& kv : ctx->batch_tables) cudaFree(kv.second);
+  void* bufs[] = {ctx->partials, ctx->tickets, ctx->scalars, ctx->tmp_odd, ctx->bounds_word};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -100,6 +111,19 @@ int lqcd_destroy(lqcd_ctx* ctx) {
 }
 
 const char* lqcd_last_error(const lqcd_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int lqcd_bounds_word(lqcd_ctx* ctx, unsigned* word) {
+  if (!ctx || !word) return LQCD_ERR_ARG;
+  *word = 0u;
+#ifdef LQCD_DEBUG_BOUNDS
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(word, ctx->bounds_word, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "lqcd_bounds_word");
+  return LQCD_OK;
+#else
+  return fail(ctx, LQCD_ERR_STATE, "lqcd_bounds_word: neighbour-index checks are compiled into the debug build only");
+#endif
+}
 
 int lqcd_set_stream(lqcd_ctx* ctx, void* stream) {
   if (!ctx) return LQCD_ERR_ARG;
@@ -247,6 +271,44 @@ int dslash_eo_batch(lqcd_ctx* const* ctxs, void* const* out_devs, const void* co
   int dev = 0, n_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_check(c0, e, "dslash_eo_batch");
+  // the whole call's descriptor table, in one persistent launch when it is (or can now be) in device memory
+  BatchTable tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.n = n;
+  for (int l = 0; l < n; ++l) {
+    const lqcd_ctx* c = ctxs[l];
+    tab.lat[l].g = make_geom(c);
+    tab.lat[l].links = link_copy(c->gauge, prec);
+    tab.lat[l].in = in_devs[l];
+    tab.lat[l].out = out_devs[l];
+    tab.lat[l].out_parity = out_parities[l];
+    tab.chunk_end[l + 1] = tab.chunk_end[l] + batch_items(c->Vh);
+  }
+  std::string key(reinterpret_cast<const char*>(&tab), sizeof(tab));
+  key.append(reinterpret_cast<const char*>(&prec), sizeof(prec));
+  void* dev_tab = nullptr;
+  for (const auto& kv : c0->batch_tables)
+    if (kv.first == key) dev_tab = kv.second;
+  if (!dev_tab && c0->batch_tables.size() < kMaxBatchTables) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(c0->stream, &cs);
+    if (e != cudaSuccess) return cuda_check(c0, e, "dslash_eo_batch");
+    if (cs == cudaStreamCaptureStatusNone) {
+      // first use of this set of descriptors: upload once (the table stays until ctxs[0] is destroyed,
+      // so graphs that captured launches reading it stay valid)
+      e = cudaMalloc(&dev_tab, sizeof(BatchTable));
+      if (e == cudaSuccess) e = cudaMemcpy(dev_tab, &tab, sizeof(BatchTable), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_check(c0, e, "dslash_eo_batch table");
+      c0->batch_tables.emplace_back(key, dev_tab);
+    }
+  }
+  if (dev_tab) {
+    e = launch_dslash_batch_table(static_cast<const BatchTable*>(dev_tab), tab.chunk_end[n], prec, c0->tickets + 7,
+                                  n_sm, c0->stream);
+    c0->launches += 1;
+    return cuda_check(c0, e, "dslash_eo_batch");
+  }
   // kBatchPerLaunch lattices per persistent launch, consecutive launches on ctxs[0]'s stream
   for (int l0 = 0; l0 < n && e == cudaSuccess; l0 += kBatchPerLaunch) {
     BatchArgs a;
@@ -368,6 +430,10 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
     case LQCD_OPT_USE_GRAPH: ctx->use_graph = v ? 1 : 0; break;
     case LQCD_OPT_PDL: ctx->use_pdl = v ? 1 : 0; break;
     case LQCD_OPT_DF_RESID: ctx->df_resid = v ? 1 : 0; break;
+    case LQCD_OPT_DF_SWITCH:
+      if (!(value >= 0.0 && value < 1.0)) return fail(ctx, LQCD_ERR_ARG, "df switch must be in [0, 1)");
+      ctx->df_switch = value;
+      break;
     case LQCD_OPT_DSLASH_TPS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return fail(ctx, LQCD_ERR_ARG, "tps must be 0,1,2,4,8");
       ctx->dslash_tps = v;

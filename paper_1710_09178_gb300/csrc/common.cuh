@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bounds.h"
 #include "lqcd.h"
 
 namespace lqcd {
@@ -41,6 +42,9 @@ struct Geom {
   int nxy;  // nx*ny
   int nxyz; // nx*ny*nz
   FastDiv dnx, dny, dnz;
+#ifdef LQCD_DEBUG_BOUNDS
+  unsigned* err;  // the context's error word (debug build only)
+#endif
 };
 
 struct Site {
@@ -83,6 +87,31 @@ __device__ __forceinline__ int neighbour_bwd(const Geom& g, const Site& s, int m
     case 2: return (s.z == 0) ? s.l + (g.nz - 1) * g.nxy : s.l - g.nxy;
     default: return (s.t == 0) ? s.l + (g.nt - 1) * g.nxyz : s.l - g.nxyz;
   }
+}
+
+// Half-lattice index of a computed neighbour address l.  The debug build checks l first
+// (bounds.h): an address outside the lattice sets LQCD_BOUNDS_NEIGHBOUR in the context's error
+// word and is replaced by site 0; the release build takes l >> 1 as it is.
+__device__ __forceinline__ int neighbour_half(const Geom& g, int l) {
+#ifdef LQCD_DEBUG_BOUNDS
+  if (!lqcd_neighbour_ok(l, g.vh)) {
+    atomicOr(g.err, LQCD_BOUNDS_NEIGHBOUR);
+    return 0;
+  }
+#endif
+  return l >> 1;
+}
+
+// A computed neighbour address l used as a full-lattice site address (the gauge-action kernels),
+// checked like neighbour_half in the debug build.
+__device__ __forceinline__ int neighbour_addr(const Geom& g, int l) {
+#ifdef LQCD_DEBUG_BOUNDS
+  if (!lqcd_neighbour_ok(l, g.vh)) {
+    atomicOr(g.err, LQCD_BOUNDS_NEIGHBOUR);
+    return 0;
+  }
+#endif
+  return l;
 }
 
 // eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z)

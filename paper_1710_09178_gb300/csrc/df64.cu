@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
   const int p = k.out_parity;
   pdl_wait();
   pdl_trigger();
-  if (k.done && *k.done) return;  // uniform
+  if ((k.done && *k.done) || (k.halt && *k.halt)) return;  // uniform
 
   float sr[3] = {0.f, 0.f, 0.f}, cr[3] = {0.f, 0.f, 0.f}, si[3] = {0.f, 0.f, 0.f}, ci[3] = {0.f, 0.f, 0.f};
   if (valid) {
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
     for (int h = 0; h < 8; ++h) {
       const int mu = h >> 1;
       const bool fwd = (h & 1) == 0;
-      const int j = (fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu)) >> 1;
+      const int j = neighbour_half(g, fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu));
       const int lp = fwd ? p : 1 - p;
       const int li = fwd ? i : j;
       const Mat3<float> Uh = load_link32(k.links_hi, lp, mu, li, vh, pol_hi);
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, DfUpdArgs a
   pdl_trigger();
   SolverDev* sd = a.sd;
   if (*reinterpret_cast<const volatile int*>(&sd->done)) return;  // the scalar block may set it meanwhile
+  if (a.halt && *a.halt) return;
   const int m = sd->m;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, DfUpdArgs a
   pdl_trigger();
   SolverDev* sd = a.sd;
   if (*reinterpret_cast<const volatile int*>(&sd->done)) return;
+  if (a.halt && *a.halt) return;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;

@@ -191,10 +191,10 @@ struct SiteHops {
       const int h = sub + q * TPS;  // TPS divides 8, so h < 8 and its parity is sub's
       const int mu = h >> 1;
       if ((h & 1) == 0) {
-        nb[q] = neighbour_fwd(g, s, mu) >> 1;
+        nb[q] = neighbour_half(g, neighbour_fwd(g, s, mu));
         sg[q] = (LF >= kL12) ? link_sign_fwd(g, s, mu) : 1;
       } else {
-        nb[q] = neighbour_bwd(g, s, mu) >> 1;
+        nb[q] = neighbour_half(g, neighbour_bwd(g, s, mu));
         sg[q] = (LF >= kL12) ? link_sign_bwd(g, s, mu) : 1;
       }
     }
@@ -281,28 +281,19 @@ constexpr int kBatchChunk = 128;
 static_assert(sizeof(BatchArgs) <= 4000, "the batch descriptors travel as the kernel's parameter block");
 static_assert(kBatchPerLaunch <= kBatchChunk, "one thread per descriptor");
 
+// The persistent loop shared by both batched kernels: blocks take 128-site chunks of any lattice
+// from the work counter until none are left (lat and chunk_end already in shared memory).
 template <int LF>
-__global__ void __launch_bounds__(kBatchChunk, 7) dslash_batch_kernel(BatchArgs a, unsigned* head) {
+__device__ __forceinline__ void batch_loop(const BatchLattice* lat, const int* chunk_end, int n, unsigned* head,
+                                           int* item_s) {
   typedef typename LinkTraits<LF>::T T;
   typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
-  __shared__ BatchLattice lat[kBatchPerLaunch];
-  __shared__ int chunk_end[kBatchPerLaunch + 1];
-  __shared__ int item_s;
-#pragma unroll
-  for (int j = 0; j < kBatchPerLaunch; ++j)
-    if (threadIdx.x == j) lat[j] = a.lat[j];
-#pragma unroll
-  for (int j = 0; j <= kBatchPerLaunch; ++j)
-    if (threadIdx.x == j) chunk_end[j] = a.chunk_end[j];
-  const int n = a.n;
-  if (n < 1 || n > kBatchPerLaunch) return;  // uniform; the host never passes such a block
-  __syncthreads();
   const int n_items = chunk_end[n];
   const uint64_t pol = link_policy<LF>();
   for (;;) {
-    if (threadIdx.x == 0) item_s = (int)atomicAdd(head, 1u);
+    if (threadIdx.x == 0) *item_s = (int)atomicAdd(head, 1u);
     __syncthreads();
-    const int it = item_s;
+    const int it = *item_s;
     __syncthreads();  // item_s is written again at the top of the next round
     if (it >= n_items) break;
     int l = 0;  // the lattice of item it: chunk_end[l] <= it < chunk_end[l + 1] (binary search)
@@ -334,6 +325,39 @@ __global__ void __launch_bounds__(kBatchChunk, 7) dslash_batch_kernel(BatchArgs 
   }
 }
 
+// descriptors in the parameter block (up to kBatchPerLaunch lattices), copied to shared memory
+template <int LF>
+__global__ void __launch_bounds__(kBatchChunk, 7) dslash_batch_kernel(BatchArgs a, unsigned* head) {
+  __shared__ BatchLattice lat[kBatchPerLaunch];
+  __shared__ int chunk_end[kBatchPerLaunch + 1];
+  __shared__ int item_s;
+#pragma unroll
+  for (int j = 0; j < kBatchPerLaunch; ++j)
+    if (threadIdx.x == j) lat[j] = a.lat[j];
+#pragma unroll
+  for (int j = 0; j <= kBatchPerLaunch; ++j)
+    if (threadIdx.x == j) chunk_end[j] = a.chunk_end[j];
+  const int n = a.n;
+  if (n < 1 || n > kBatchPerLaunch) return;  // uniform; the host never passes such a block
+  __syncthreads();
+  batch_loop<LF>(lat, chunk_end, n, head, &item_s);
+}
+
+// descriptors in a device table (up to kMaxBatch lattices), copied to shared memory
+template <int LF>
+__global__ void __launch_bounds__(kBatchChunk, 7) dslash_batch_table_kernel(const BatchTable* __restrict__ tab,
+                                                                             unsigned* head) {
+  __shared__ BatchLattice lat[kMaxBatch];
+  __shared__ int chunk_end[kMaxBatch + 1];
+  __shared__ int item_s;
+  const int n = tab->n;
+  if (n < 1 || n > kMaxBatch) return;  // uniform; the host never uploads such a table
+  for (int j = threadIdx.x; j < n; j += blockDim.x) lat[j] = tab->lat[j];
+  for (int j = threadIdx.x; j <= n; j += blockDim.x) chunk_end[j] = tab->chunk_end[j];
+  __syncthreads();
+  batch_loop<LF>(lat, chunk_end, n, head, &item_s);
+}
+
 int batch_items(int vh) { return (vh + kBatchChunk - 1) / kBatchChunk; }
 
 cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, int n_sm, cudaStream_t st) {
@@ -348,6 +372,22 @@ cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, in
     case LQCD_FP32_R8: dslash_batch_kernel<kL8><<<grid, kBatchChunk, 0, st>>>(a, head); break;
     case LQCD_FP32_L16: dslash_batch_kernel<kL16><<<grid, kBatchChunk, 0, st>>>(a, head); break;
     default: dslash_batch_kernel<kL32><<<grid, kBatchChunk, 0, st>>>(a, head); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dslash_batch_table(const BatchTable* tab, int n_items, int prec, unsigned* head, int n_sm,
+                                      cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min(n_items, 7 * n_sm);  // one resident wave of persistent blocks
+  switch (prec) {
+    case LQCD_FP64: dslash_batch_table_kernel<kL64><<<grid, kBatchChunk, 0, st>>>(tab, head); break;
+    case LQCD_FP32_R12: dslash_batch_table_kernel<kL12><<<grid, kBatchChunk, 0, st>>>(tab, head); break;
+    case LQCD_FP32_R8: dslash_batch_table_kernel<kL8><<<grid, kBatchChunk, 0, st>>>(tab, head); break;
+    case LQCD_FP32_L16: dslash_batch_table_kernel<kL16><<<grid, kBatchChunk, 0, st>>>(tab, head); break;
+    default: dslash_batch_table_kernel<kL32><<<grid, kBatchChunk, 0, st>>>(tab, head); break;
   }
   return cudaGetLastError();
 }

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128) force_kernel(Geom g, ForceArgs a) {
   const int i = sidx - p * g.vh;
   const int vh = g.vh;
   Site s = site_of(g, p, i);
-  const int j = neighbour_fwd(g, s, mu) >> 1;
+  const int j = neighbour_half(g, neighbour_fwd(g, s, mu));
   // O = sum_k c_k Z_k(x+mu) Z_k(x)^dagger, Z = X on even sites, Y on odd sites
   Mat3<T> O;
 #pragma unroll

@@ -27,7 +27,8 @@ struct SolverDev {
                    // its scalar block overwrites rr
   double bb;       // |b|^2
   double stop2;    // tol^2 |b|^2: shift k stops when zeta_k^2 |r|^2 <= stop2
-  double alpha, alpha_prev, beta, beta_prev;
+  double alpha, beta;
+  double alpha_prev, beta_prev;  // alpha and beta of the iteration before the pending window
   double pq;
   double a_diag;   // 4 m^2 + sigma_0
   // FP32 and (hi, lo) copies of alpha, beta and a_diag, written once by the scalar steps so that
@@ -40,6 +41,7 @@ struct SolverDev {
   int n;
   int m;           // iterations accumulated in the pending window
   int n_active;
+  int halt1;       // precision schedule: the double-FP32 phase is over (its kernels return at entry)
   int first;       // pending window is the first of the solve (p_k0 = b, x_k0 = 0)
   int maxiter;     // the beta step sets done once iter reaches it
   // reliable updates: due when ru_interval iterations have passed since the last one, or when
@@ -52,10 +54,15 @@ struct SolverDev {
   int shift_iters;  // sum over iterations of the active shifts (statistics)
   int windows_run;  // windows executed by the graph loop (bounded by max_windows whatever the flags say)
   int max_windows;
+  int windows_df;   // of which in the double-FP32 phase of the precision schedule
+  int demoted;      // the change from the double-FP32 to the FP32 phase has run
+  double switch2;   // the double-FP32 phase ends at the first window end with |r|^2 <= switch2
   unsigned ticket[4];
   double s[kMaxShifts];  // sigma_k - sigma_0
-  double zeta[kMaxShifts], zeta_prev[kMaxShifts], zeta_new[kMaxShifts];
-  double zratio[kMaxShifts];  // zeta_new / zeta of the running iteration (alpha step -> beta step)
+  double zeta[kMaxShifts], zeta_prev[kMaxShifts];
+  // base scalars of the pending window's iterations (alpha_j, beta_j, |r_j+1|^2): the per-shift
+  // recurrences are replayed from them once per window (window_scalars_kernel)
+  double alpha_h[kWindow], beta_h[kWindow], rr_h[kWindow];
   int active[kMaxShifts];   // shift still iterating
   int wactive[kMaxShifts];  // shift takes part in the pending window
   // pending window: p_k = P p_k0 + sum_i pi_i R_i,  x_k = x_k0 + X p_k0 + sum_i chi_i R_i
@@ -90,6 +97,7 @@ struct lqcd_ctx {
   long long launches = 0;
   // solver options
   int reliable_interval = 100;
+  double df_switch = 1e-3;  // mixed modes: double-FP32 iterations until |r| <= df_switch |b| (0: none)
   double reliable_delta = 0.01;
   int refine = 1;
   int batch = 20;  // iterations per host-polled batch when graphs are off
@@ -105,6 +113,9 @@ struct lqcd_ctx {
   void* tmp_odd = nullptr;     // odd-parity temporary of lqcd_apply_A (sized for FP64)
   unsigned* tickets = nullptr;  // reduction tickets for stand-alone reductions
   double* scalars = nullptr;    // device scalars for stand-alone reductions
+  unsigned* bounds_word = nullptr;  // debug build: device error word of the neighbour-index checks
+  // dslash_eo_batch descriptor tables uploaded from this context (key: the host bytes of the table)
+  std::vector<std::pair<std::string, void*>> batch_tables;
 };
 
 namespace lqcd {
@@ -142,10 +153,13 @@ struct DslashArgs {
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
 
-// dslash.cu: the batched half-Dslash (dslash_eo_batch).  One launch takes up to kBatchPerLaunch
-// lattices, whose descriptors travel in the kernel's parameter block (under 4 KB); larger
-// batches are split into consecutive launches.
+// dslash.cu: the batched half-Dslash (dslash_eo_batch).  All lattices of a call run in one
+// persistent launch whose descriptors (BatchTable) sit in device memory: each distinct set of
+// descriptors is uploaded once and cached on the first context.  A set first met while the stream is
+// being captured into a CUDA graph cannot be uploaded then; it travels in the kernel's parameter
+// block instead (BatchArgs, under 4 KB: up to kBatchPerLaunch lattices per launch).
 constexpr int kMaxBatch = 128;
+constexpr size_t kMaxBatchTables = 256;  // descriptor tables cached per context (about 11 KB each)
 constexpr int kBatchPerLaunch = 32;
 struct BatchLattice {
   Geom g;
@@ -159,8 +173,15 @@ struct BatchArgs {
   int chunk_end[kBatchPerLaunch + 1];  // prefix sums of the lattices' item counts
   BatchLattice lat[kBatchPerLaunch];
 };
+struct BatchTable {
+  int n;
+  int chunk_end[kMaxBatch + 1];
+  BatchLattice lat[kMaxBatch];
+};
 int batch_items(int vh);
 cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, int n_sm, cudaStream_t st);
+cudaError_t launch_dslash_batch_table(const BatchTable* dev_table, int n_items, int prec, unsigned* head, int n_sm,
+                                      cudaStream_t st);
 int dslash_grid_blocks(const Geom& g, int prec, int tps);
 
 // df64.cu: residuals b - (A + sigma) x in double-FP32 arithmetic
@@ -185,6 +206,7 @@ struct DfArgs {
   double* partials = nullptr;       // one per block
   unsigned* ticket = nullptr;       // null: the A-apply's sum stays as (hi, lo) partials (inside the solve)
   const int* done = nullptr;        // if non-null and *done, the kernel returns at entry
+  const int* halt = nullptr;        // likewise (the end of the double-FP32 phase of a mixed solve)
   int out_parity = 0;
 };
 // double-FP32 vectors of the LQCD_DF64 solve: [3][Vh] float2 hi, then [3][Vh] float2 lo
@@ -198,6 +220,7 @@ struct DfUpdArgs {
   const double* pq_partials;  // (hi, lo) partials of Re<p, q> left by the A-apply
   int n_pq;
   double* rr_partials;  // (hi, lo) partials of |r|^2: written by the r update, read by the p update
+  const int* halt;      // if non-null and *halt, the kernels return at entry (end of the double-FP32 phase)
 };
 struct DfFlushArgs {
   const void* ring;

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) mrhs_dslash_kernel(Geom g, const void* li
     for (int h = 0; h < 8; ++h) {
       const int mu = h >> 1;
       const bool fwd = (h & 1) == 0;
-      const int j = (fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu)) >> 1;
+      const int j = neighbour_half(g, fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu));
       const int sg = (LF == 2) ? (fwd ? link_sign_fwd(g, s, mu) : link_sign_bwd(g, s, mu)) : 1;
       auto W = fwd ? mrhs_link<LF>(links, p, mu, i, vh, sg, pol) : mrhs_link<LF>(links, 1 - p, mu, j, vh, sg, pol);
 #pragma unroll

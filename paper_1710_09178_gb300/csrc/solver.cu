@@ -5,11 +5,12 @@
 //   1. tmp = D_oe p                                          (dslash.cu)
 //   2. q = (4m^2 + sigma_0) p - D_eo tmp, per-block partials of (p, q)   (dslash.cu epilogue)
 //   3. alpha from those partials, r -= alpha q, R[m] = r, partials of (r, r);
-//      an extra block runs the alpha step (solver_dev.cuh)               (r_update_kernel)
-//   4. beta from those partials, p = r + beta p; an extra block runs the
-//      beta step                                                        (p_update_kernel)
-// Every kWindow iterations the window kernel applies the pending x_k / p_k
-// updates of all shifts at once (flush_kernel): each shift vector is read and
+//      an extra block stores alpha (solver_dev.cuh)                      (r_update_kernel)
+//   4. beta from those partials, p = r + beta p; an extra block stores beta and
+//      decides the base stopping test and the reliable update           (p_update_kernel)
+// Every kWindow iterations one warp replays the per-shift recurrences of the window
+// from the stored alpha and beta (window_scalars_kernel), and the window kernel applies
+// the pending x_k / p_k updates of all shifts at once (flush_kernel): each shift vector is read and
 // written once per window instead of once per iteration, which is what makes
 // the multi-shift update (the heaviest loop of the shifted CG in Section 7)
 // cheap.  Iteration batches are captured in CUDA graphs; kernels return at entry
@@ -317,6 +318,74 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
   }
 }
 
+// Per-shift recurrences of the pending window (one warp), right before the window update.
+__global__ void window_scalars_kernel(SolverDev* sd) {
+  pdl_wait();
+  pdl_trigger();
+  window_scalars(sd);
+}
+
+// Precision schedule of the mixed modes.  The error that FP32 arithmetic (links, Krylov vectors)
+// puts into the shifted solutions at iteration j scales with |r_j|: an error of relative size eps in
+// the matrix-vector product at iteration j perturbs the attainable residual by about eps |r_j|
+// (relaxation of inexact Krylov methods, van den Eshof & Sleijpen, SIAM J. Matrix Anal. Appl. 26
+// (2004) 125).  The shifted solutions have no reliable update of their own, so with FP32 from the
+// start their true residuals end near eps_32 |b| ~ 1e-7 |b| and need a long refinement.  The solve
+// therefore runs in double-FP32 (~48-bit) until |r| <= df_switch |b| and in FP32 (with reliable
+// updates) after that; the FP32 errors then enter at most at ~eps_32 df_switch |b|.
+//
+// End of every window of the double-FP32 phase: the phase ends once |r|^2 <= switch2 (or the solve
+// is done, or the window budget is spent); in a captured graph this ends the phase's while loop.
+__global__ void loop_ctl_df_kernel(cudaGraphConditionalHandle handle, SolverDev* sd, int set_cond) {
+  if (threadIdx.x != 0) return;
+  if (!sd->halt1) {
+    const int wr = sd->windows_run + 1;
+    sd->windows_run = wr;
+    sd->windows_df += 1;
+    if (sd->done || sd->rr <= sd->switch2 || wr >= sd->max_windows) sd->halt1 = 1;
+  }
+  if (set_cond) cudaGraphSetConditional(handle, sd->halt1 ? 0u : 1u);
+}
+
+struct DemoteArgs {
+  const float2* r_df;  // (hi, lo) vectors, [3][Vh] hi first
+  const float2* p_df;
+  const float2* pk_df[kMaxShifts];
+  void* r;             // the FP32 phase's vectors
+  void* p;
+  void* pk[kMaxShifts];
+  int n;
+  const SolverDev* sd;
+};
+
+// The change of phase, once (after the window that ended the double-FP32 phase): r, p and the active
+// shifts' p_k to the FP32 phase's storage, each the (hi, lo) pair rounded to FP32 (its hi part).
+template <int SF>
+__global__ void __launch_bounds__(256) demote_kernel(Geom g, DemoteArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const SolverDev* sd = a.sd;
+  if (!sd->halt1 || sd->demoted || sd->done) return;
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vh) return;
+  store_vec(static_cast<float2*>(a.r), i, vh, load_vec(a.r_df, i, vh));
+  store_vec(static_cast<float2*>(a.p), i, vh, load_vec(a.p_df, i, vh));
+  for (int k = 0; k < a.n; ++k)
+    if (sd->active[k]) store_s<SF, float>(a.pk[k], i, vh, load_vec(a.pk_df[k], i, vh));
+}
+
+// after demote_kernel: mark the change done and start the reliable-update bookkeeping of the FP32 phase
+__global__ void demoted_kernel(SolverDev* sd) {
+  if (threadIdx.x != 0) return;
+  if (sd->halt1 && !sd->demoted) {
+    sd->demoted = 1;
+    sd->iter_ru = sd->iter;
+    sd->rr_ru_max = sd->rr;
+    sd->ru_skip = 1;
+  }
+}
+
 // r (Krylov precision) = r64 after a reliable update; |r|^2 = scal[0]
 template <typename T>
 __global__ void ru_finish_kernel(Geom g, const double2* __restrict__ r64, void* r, const SolverDev* sd) {
@@ -407,7 +476,7 @@ __global__ void zero_kernel(int n3, double2* __restrict__ x) {
 // Host side
 // ---------------------------------------------------------------------------
 struct StatusWords {
-  int iter, done, status, n, m, n_active;
+  int iter, done, status, n, m, n_active, halt1;
 };
 
 struct Workspace {
@@ -429,6 +498,11 @@ struct Workspace {
   // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
   bool df = false;
   float2 *dfx_h = nullptr, *dfx_l = nullptr, *dft_h = nullptr, *dft_l = nullptr, *dfb_h = nullptr, *dfb_l = nullptr;
+  // precision schedule of the mixed modes: the double-FP32 phase's Krylov, window and shift vectors
+  // ((hi, lo) pairs, 48 bytes per site); the solutions are shared with the FP32 phase
+  bool sched = false;
+  void *dr = nullptr, *dp = nullptr, *dq = nullptr, *dtmp = nullptr, *dring = nullptr;
+  void* dpk[kMaxShifts] = {};
   SolverDev* sd = nullptr;
   int* ru_count = nullptr;
   StatusWords* host_status = nullptr;  // pinned, 2 slots
@@ -439,6 +513,7 @@ struct Workspace {
   unsigned* tickets = nullptr;
   std::map<std::tuple<const void*, const void*, int, int>, cudaGraphExec_t> graphs;
   std::map<std::tuple<const void*, const void*, int, int>, int> graph_nodes;
+  std::map<std::tuple<const void*, const void*, int, int>, int> graph_nodes_df;  // per double-FP32 window
 };
 
 static size_t vec_bytes(long long vh, int prec) {
@@ -463,13 +538,14 @@ void free_workspace(lqcd_ctx* ctx) {
   for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
   void* bufs[] = {w->dfx_h, w->dfx_l, w->dft_h, w->dft_l, w->dfb_h, w->dfb_l,
                   w->r, w->p, w->q, w->tmp, w->ring, w->b64, w->r64, w->tmp64, w->e64, w->rb64, w->sd,
-                  w->ru_count, w->partials, w->tickets};
+                  w->ru_count, w->partials, w->tickets, w->dr, w->dp, w->dq, w->dtmp, w->dring};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int k = 0; k < kMaxShifts; ++k) {
     if (w->pk[k]) cudaFree(w->pk[k]);
     if (w->xk[k]) cudaFree(w->xk[k]);
     if (w->xdf[k]) cudaFree(w->xdf[k]);
+    if (w->dpk[k]) cudaFree(w->dpk[k]);
   }
   if (w->host_status) cudaFreeHost(w->host_status);
   if (w->host_scal) cudaFreeHost(w->host_scal);
@@ -525,6 +601,17 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   LQ_CUDA(cudaMalloc(&w->rb64, w->dbytes));
   w->df = prec == LQCD_DF64 || (prec != LQCD_FP64 && ctx->df_resid);
   w->xdfmode = w->df;
+  // precision schedule: the mixed modes with double-FP32 residuals start in double-FP32
+  w->sched = w->df && prec != LQCD_DF64 && ctx->df_switch > 0.0;
+  if (w->sched) {
+    const size_t b48 = vec_bytes(vh, LQCD_DF64);
+    LQ_CUDA(cudaMalloc(&w->dr, b48));
+    LQ_CUDA(cudaMalloc(&w->dp, b48));
+    LQ_CUDA(cudaMalloc(&w->dq, b48));
+    LQ_CUDA(cudaMalloc(&w->dtmp, b48));
+    LQ_CUDA(cudaMalloc(&w->dring, b48 * kWindow));
+    for (int k = 0; k < n; ++k) LQ_CUDA(cudaMalloc(&w->dpk[k], b48));
+  }
   if (w->df) {
     float2** dfb[] = {&w->dfx_h, &w->dfx_l, &w->dft_h, &w->dft_l, &w->dfb_h, &w->dfb_l};
     for (float2** b : dfb) LQ_CUDA(cudaMalloc(b, 24 * (size_t)vh));
@@ -558,15 +645,30 @@ struct Launcher {
   }
 };
 
+// the (hi, lo) vectors a double-FP32 iteration and window work on: those of the LQCD_DF64 solve,
+// or the double-FP32 phase of a mixed solve's precision schedule
+struct DfBufs {
+  void *r, *p, *q, *tmp, *ring;
+  size_t slot_bytes;
+  void* const* pk;
+  const int* halt;  // the phase's end flag (null for LQCD_DF64)
+};
+
+static DfBufs df_bufs(Workspace* w, bool phase) {
+  if (phase) return DfBufs{w->dr, w->dp, w->dq, w->dtmp, w->dring, w->dbytes, w->dpk,
+                           &w->sd->halt1};
+  return DfBufs{w->r, w->p, w->q, w->tmp, w->ring, w->sbytes, w->pk, nullptr};
+}
+
 // the four kernels of one base iteration
-static cudaError_t enqueue_iteration_df(Launcher& L);
+static cudaError_t enqueue_iteration_df(Launcher& L, const DfBufs& B);
 
 static cudaError_t enqueue_iteration(Launcher& L) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
   cudaStream_t st = w->st;
   const int* done = &w->sd->done;
-  if (w->kprec == LQCD_DF64) return enqueue_iteration_df(L);
+  if (w->kprec == LQCD_DF64) return enqueue_iteration_df(L, df_bufs(w, false));
   DslashArgs d1;
   d1.out = w->tmp;
   d1.in = w->p;
@@ -620,8 +722,9 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   return e;
 }
 
-// the four kernels of one base iteration of the double-FP32 solve (LQCD_DF64)
-static cudaError_t enqueue_iteration_df(Launcher& L) {
+// the four kernels of one base iteration of the double-FP32 solve (LQCD_DF64, or the double-FP32
+// phase of a mixed solve)
+static cudaError_t enqueue_iteration_df(Launcher& L, const DfBufs& B) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
   cudaStream_t st = w->st;
@@ -631,22 +734,23 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   DfArgs d;
   d.links_hi = ctx->gauge.u32;
   d.links_lo = ctx->gauge.u32lo;
-  d.in_hi = hi(w->p);
-  d.in_lo = lo(w->p);
-  d.out_hi = hi(w->tmp);
-  d.out_lo = lo(w->tmp);
+  d.in_hi = hi(B.p);
+  d.in_lo = lo(B.p);
+  d.out_hi = hi(B.tmp);
+  d.out_lo = lo(B.tmp);
   d.done = &w->sd->done;
+  d.halt = B.halt;
   d.out_parity = 1;
   cudaError_t e = launch_df_dslash(L.g, d, 0, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
   DfArgs a = d;
-  a.in_hi = hi(w->tmp);
-  a.in_lo = lo(w->tmp);
-  a.out_hi = hi(w->q);
-  a.out_lo = lo(w->q);
-  a.x_hi = hi(w->p);
-  a.x_lo = lo(w->p);
+  a.in_hi = hi(B.tmp);
+  a.in_lo = lo(B.tmp);
+  a.out_hi = hi(B.q);
+  a.out_lo = lo(B.q);
+  a.x_hi = hi(B.p);
+  a.x_lo = lo(B.p);
   a.a_dev = &w->sd->a_diag;
   a.a_devdf = &w->sd->a_diag_df;
   a.partials = w->partials;  // no ticket: the r update sums the partials and runs the alpha step
@@ -655,15 +759,16 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
   DfUpdArgs u;
-  u.r = hi(w->r);
-  u.q = hi(w->q);
-  u.p = hi(w->p);
-  u.ring = w->ring;
-  u.slot_bytes = w->sbytes;
+  u.r = hi(B.r);
+  u.q = hi(B.q);
+  u.p = hi(B.p);
+  u.ring = B.ring;
+  u.slot_bytes = B.slot_bytes;
   u.sd = w->sd;
   u.pq_partials = w->partials;
   u.n_pq = df_dslash_grid_blocks(L.g);
   u.rr_partials = w->partials_b;
+  u.halt = B.halt;
   e = launch_df_r_update(L.g, u, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
@@ -672,8 +777,31 @@ static cudaError_t enqueue_iteration_df(Launcher& L) {
   return e;
 }
 
-static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n) {
+// the window end: per-shift recurrences, then the window update of every x_k, p_k (double-FP32 when
+// df_phase, i.e. in the first phase of the precision schedule)
+static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n, bool df_phase = false) {
   Workspace* w = L.w;
+  cudaError_t e = launch_k(L.next_pdl(), window_scalars_kernel, dim3(1), dim3(32), w->st, w->sd);
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  if (df_phase || w->sfmt == kSDF) {
+    const DfBufs B = df_bufs(w, df_phase);
+    DfFlushArgs df;
+    memset(&df, 0, sizeof(df));
+    df.ring = B.ring;
+    df.slot_bytes = B.slot_bytes;
+    for (int k = 0; k < n; ++k) {
+      df.pk[k] = static_cast<float2*>(B.pk[k]);
+      df.xk[k] = reinterpret_cast<float2*>(xs[k]);
+    }
+    df.b_hi = w->dfb_h;
+    df.b_lo = w->dfb_l;
+    df.sd = w->sd;
+    df.partials = w->partials;
+    df.ticket = w->tickets + 2;
+    L.nlaunch += 1;
+    return launch_df_flush(L.g, df, w->st, L.next_pdl());
+  }
   FlushArgs fa;
   memset(&fa, 0, sizeof(fa));
   fa.ring = w->ring;
@@ -686,23 +814,6 @@ static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2*
   fa.sd = w->sd;
   fa.partials = w->partials;
   fa.ticket = w->tickets + 2;
-  if (w->sfmt == kSDF) {
-    DfFlushArgs df;
-    memset(&df, 0, sizeof(df));
-    df.ring = w->ring;
-    df.slot_bytes = w->sbytes;
-    for (int k = 0; k < n; ++k) {
-      df.pk[k] = static_cast<float2*>(w->pk[k]);
-      df.xk[k] = reinterpret_cast<float2*>(xs[k]);
-    }
-    df.b_hi = w->dfb_h;
-    df.b_lo = w->dfb_l;
-    df.sd = w->sd;
-    df.partials = w->partials;
-    df.ticket = w->tickets + 2;
-    L.nlaunch += 1;
-    return launch_df_flush(L.g, df, w->st, L.next_pdl());
-  }
   int nb = (L.g.vh + 127) / 128;
   const bool pdl = L.next_pdl();
   L.nlaunch += 1;
@@ -803,6 +914,41 @@ static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma,
   return e;
 }
 
+// one window of the double-FP32 phase of the precision schedule, its phase test and the (guarded,
+// one-time) change to the FP32 phase
+static cudaError_t enqueue_df_window(Launcher& L, double2* const* xs, const double2* b64, int n,
+                                     cudaGraphConditionalHandle handle, int set_cond) {
+  Workspace* w = L.w;
+  const DfBufs B = df_bufs(w, true);
+  cudaError_t e;
+  for (int it = 0; it < kWindow; ++it)
+    if ((e = enqueue_iteration_df(L, B)) != cudaSuccess) return e;
+  if ((e = enqueue_flush(L, xs, b64, n, true)) != cudaSuccess) return e;
+  loop_ctl_df_kernel<<<1, 32, 0, w->st>>>(handle, w->sd, set_cond);
+  L.nlaunch += 1;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  DemoteArgs da;
+  memset(&da, 0, sizeof(da));
+  da.r_df = static_cast<const float2*>(w->dr);
+  da.p_df = static_cast<const float2*>(w->dp);
+  da.r = w->r;
+  da.p = w->p;
+  for (int k = 0; k < n; ++k) {
+    da.pk_df[k] = static_cast<const float2*>(w->dpk[k]);
+    da.pk[k] = w->pk[k];
+  }
+  da.n = n;
+  da.sd = w->sd;
+  const dim3 grid((L.g.vh + 255) / 256);
+  if (w->sfmt == kS16) e = launch_k(L.next_pdl(), demote_kernel<kS16>, grid, dim3(256), w->st, L.g, da);
+  else e = launch_k(L.next_pdl(), demote_kernel<kS32>, grid, dim3(256), w->st, L.g, da);
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  demoted_kernel<<<1, 32, 0, w->st>>>(w->sd);
+  L.nlaunch += 1;
+  return cudaGetLastError();
+}
+
 // iteration batch: windows x (kWindow iterations, flush, reliable update if due).  The reliable-update
 // kernels return at entry unless the beta step marked one as due (ru_skip == 0).
 static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2* b64, int n, int k0, double sigma0,
@@ -844,13 +990,15 @@ static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2*
 
 // Solve (A + shifts[k]) xs[k] = b64 for all k (FP64 internal vectors).
 static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts, int n, double tol,
-                      int maxiter, bool use_ru, int* iters, int* n_ru, int* status) {
+                      int maxiter, bool use_ru, int* iters, int* n_ru, int* status, int* iters_df) {
   Workspace* w = ctx->ws;
   Launcher L{ctx, w, make_geom(ctx), 0};
   int k0 = 0;
   for (int k = 1; k < n; ++k)
     if (shifts[k] < shifts[k0]) k0 = k;
   double sigma0 = shifts[k0];
+  // precision schedule: double-FP32 windows first (mixed modes with double-FP32 residuals)
+  const bool sched = w->sched && use_ru;
   InitParams ip;
   memset(&ip, 0, sizeof(ip));
   ip.n = n;
@@ -860,10 +1008,13 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   ip.maxiter = maxiter;
   ip.ru_interval = ctx->reliable_interval;
   ip.ru_delta = ctx->reliable_delta;
+  ip.df_switch = sched ? ctx->df_switch : 0.0;
   LQ_CUDA(cudaMemsetAsync(w->ru_count, 0, sizeof(int), w->st));
   int nb = (L.g.vh + 255) / 256;
   if (w->kprec == LQCD_DF64)
     LQ_CUDA(launch_df_init(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4, w->st));
+  else if (sched)
+    LQ_CUDA(launch_df_init(L.g, b64, w->dr, w->dp, w->sd, ip, w->partials, w->tickets + 4, w->st));
   else if (w->kprec == LQCD_FP64)
     init_kernel<double><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
   else
@@ -873,14 +1024,15 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
 
   if (ctx->use_graph) {
     // One graph per (source, solution set, shift count, base shift): a while-node repeats
-    // [kWindow iterations, window update, reliable update if due, loop control] until done.
-    auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0), k0);
+    // [kWindow iterations, window update, reliable update if due, loop control] until done; with the
+    // precision schedule a first while-node repeats the double-FP32 windows until that phase ends.
+    auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0) + (sched ? 2 : 0), k0);
     auto it = w->graphs.find(key);
     if (it == w->graphs.end()) {
       // with programmatic dependent launch first; captured again without it if the driver
       // refuses programmatic edges inside the conditional body
       cudaGraphExec_t exec = nullptr;
-      int nodes = 0;
+      int nodes = 0, nodes_df = 0;
       cudaError_t e = cudaErrorUnknown;
       for (int attempt = 0; attempt < 2 && e != cudaSuccess; ++attempt) {
         const bool pdl = attempt == 0 && ctx->use_pdl;
@@ -891,6 +1043,27 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
         }
         cudaGraph_t graph;
         LQ_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphNode_t prev = nullptr;
+        e = cudaSuccess;
+        if (sched) {
+          cudaGraphConditionalHandle h1;
+          LQ_CUDA(cudaGraphConditionalHandleCreate(&h1, graph, 1, cudaGraphCondAssignDefault));
+          cudaGraphNodeParams cp1 = {};
+          cp1.type = cudaGraphNodeTypeConditional;
+          cp1.conditional.handle = h1;
+          cp1.conditional.type = cudaGraphCondTypeWhile;
+          cp1.conditional.size = 1;
+          LQ_CUDA(cudaGraphAddNode(&prev, graph, nullptr, nullptr, 0, &cp1));
+          Launcher C1{ctx, w, L.g, 0};
+          C1.pdl = pdl;
+          LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, cp1.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal));
+          e = enqueue_df_window(C1, xs, b64, n, h1, 1);
+          cudaGraph_t captured1;
+          cudaError_t e1 = cudaStreamEndCapture(w->st, &captured1);
+          if (e == cudaSuccess) e = e1;
+          nodes_df = C1.nlaunch;
+        }
         cudaGraphConditionalHandle handle;
         LQ_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
         cudaGraphNodeParams cp = {};
@@ -899,12 +1072,12 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
         cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
         cudaGraphNode_t cnode;
-        LQ_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+        LQ_CUDA(cudaGraphAddNode(&cnode, graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         Launcher C{ctx, w, L.g, 0};
         C.pdl = pdl;
         LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
+        if (e == cudaSuccess) e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
         if (e == cudaSuccess) {
           loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, w->sd);
           C.nlaunch += 1;
@@ -920,46 +1093,67 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
       LQ_CUDA(e);
       w->graphs[key] = exec;
       w->graph_nodes[key] = nodes;
+      w->graph_nodes_df[key] = nodes_df;
       it = w->graphs.find(key);
     }
     LQ_CUDA(cudaGraphLaunch(it->second, w->st));
-    LQ_CUDA(cudaMemcpyAsync(&w->host_status[1], &w->sd->windows_run, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+    // windows_run, max_windows, windows_df
+    int* wins = reinterpret_cast<int*>(&w->host_status[1]);
+    LQ_CUDA(cudaMemcpyAsync(wins, &w->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
     LQ_CUDA(cudaStreamSynchronize(w->st));
-    L.nlaunch += w->graph_nodes[key] * w->host_status[1].iter;  // kernel nodes per window x windows run
+    // kernel nodes per window x windows run, in each phase
+    L.nlaunch += w->graph_nodes[key] * (wins[0] - wins[2]) + w->graph_nodes_df[key] * wins[2];
   } else {
+    // host-polled batches of windows (at most two in flight) until `finished` says so
     const int windows = std::max(1, ctx->batch / kWindow);
     const int per_batch = windows * kWindow;
     const int max_batches = (maxiter + per_batch - 1) / per_batch;
-    int launched = 0, checked = 0;
-    bool finished = false;
-    while (!finished) {
-      if (launched < max_batches) {
-        LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
-        int slot = launched & 1;
-        LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
-                                w->st));
-        LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
-        ++launched;
+    auto run_batches = [&](bool df_phase) -> int {
+      int launched = 0, checked = 0;
+      bool finished = false;
+      while (!finished) {
+        if (launched < max_batches) {
+          if (df_phase) {
+            for (int wdx = 0; wdx < windows; ++wdx) LQ_CUDA(enqueue_df_window(L, xs, b64, n, 0, 0));
+          } else {
+            LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
+          }
+          int slot = launched & 1;
+          LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
+                                  w->st));
+          LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
+          ++launched;
+        }
+        if (launched - checked >= 2 || launched == max_batches) {
+          int slot = checked & 1;
+          LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
+          StatusWords sw = w->host_status[slot];
+          ++checked;
+          if (sw.done || (df_phase && sw.halt1) || checked == max_batches) finished = true;
+        }
       }
-      if (launched - checked >= 2 || launched == max_batches) {
-        int slot = checked & 1;
-        LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
-        StatusWords sw = w->host_status[slot];
-        ++checked;
-        if (sw.done || checked == max_batches) finished = true;
-      }
+      return LQCD_OK;
+    };
+    if (sched) {
+      int rc = run_batches(true);
+      if (rc != LQCD_OK) return rc;
     }
+    int rc = run_batches(false);
+    if (rc != LQCD_OK) return rc;
   }
   // drain a batch still in flight and read the final state
   LQ_CUDA(cudaMemcpyAsync(&w->host_status[0], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
-  int ru_host = 0;
+  int ru_host = 0, wins_df[3] = {0, 0, 0};
   LQ_CUDA(cudaMemcpyAsync(&ru_host, w->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaMemcpyAsync(&w->shift_iters_host, &w->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+  LQ_CUDA(cudaMemcpyAsync(wins_df, &w->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
   StatusWords last = w->host_status[0];
   ctx->launches += L.nlaunch;
   *iters = last.iter;
   *n_ru = ru_host;
+  // iterations of the double-FP32 phase: the windows it ran, the last one possibly partial
+  *iters_df = sched ? std::min(last.iter, kWindow * wins_df[2]) : 0;
   if (last.status != LQCD_OK) *status = last.status;
   else if (!last.done || last.n_active > 0) *status = LQCD_ERR_NOT_CONVERGED;
   else *status = LQCD_OK;
@@ -1052,13 +1246,13 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
     ctx->launches += 1;
   }
 
-  int iters = 0, n_ru = 0, st_main = LQCD_OK;
+  int iters = 0, n_ru = 0, st_main = LQCD_OK, iters_df = 0;
   // The solutions live as (hi, lo) FP32 pairs through the solve, the checks and the refinement
   // (every mode but LQCD_FP64) and become FP64 at the end; LQCD_DF64 needs no reliable updates.
   const bool dfsolve = prec == LQCD_DF64;
   double2* const* xs_run = w->xdfmode ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
   rc = solve_core(ctx, w->b64, xs_run, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, &iters, &n_ru,
-                  &st_main);
+                  &st_main, &iters_df);
   if (rc != LQCD_OK) return rc;
   LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
   LQ_CUDA(cudaStreamSynchronize(w->st));
@@ -1160,6 +1354,7 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
     stats->kernel_launches = (int)(ctx->launches - launches0);
     stats->n_shifts = n;
     stats->shift_iterations = w->shift_iters_host;
+    stats->df_iterations = iters_df;
     for (int k = 0; k < n; ++k) stats->true_residual[k] = tres[k];
     stats->ms = ms;
   }

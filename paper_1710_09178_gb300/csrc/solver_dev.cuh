@@ -1,6 +1,6 @@
-// solver_dev.cuh - the scalar steps of the shifted CG, run by one block right after the global
-// sum it needs is known: the extra block of the r and p update kernels in the base iteration,
-// the last block of a reduction kernel elsewhere.
+// solver_dev.cuh - the scalar steps of the shifted CG: the base steps run by one block right after
+// the global sum they need is known (the extra block of the r and p update kernels), and the
+// per-shift recurrences of a window, replayed once per window before the window update.
 //
 // Shifted CG (Section 4; ref. [mcg]): base system A + sigma_0 with sigma_0 the
 // smallest shift, s_k = sigma_k - sigma_0, residual collinearity r_k = zeta_k r.
@@ -9,6 +9,7 @@
 //   beta step (needs (r,r) new): beta = (r,r)_new/(r,r);  beta_k = beta (zeta_k'/zeta_k)^2;
 //       p_k = zeta_k' r_new + beta_k p_k;  stop shift k once zeta_k'^2 (r,r)_new <= tol^2 (b,b);
 //       and decide whether a reliable update is due at the end of the window
+// (the zeta_k parts of both steps are deferred to the window end, window_scalars())
 // The x_k and p_k updates are not applied vector by vector: they are folded into
 // the coefficients of the pending window,
 //   p_k = P p_k0 + sum_i pi_i R_i,   x_k = x_k0 + X p_k0 + sum_i chi_i R_i,
@@ -21,10 +22,6 @@
 
 namespace lqcd {
 
-// The steps run in one warp of that block; every lane k < n owns shift k.  All loads of a
-// lane are issued before any store (the state lives in global memory and a chain of dependent
-// round trips would cost far more than the arithmetic, most of which is FP64).
-
 // parameters of a fresh solve (host to the init kernel)
 struct InitParams {
   int n;
@@ -34,6 +31,7 @@ struct InitParams {
   double s[kMaxShifts];
   double a_diag;
   double tol;
+  double df_switch;  // precision schedule: end of the double-FP32 phase at |r| <= df_switch |b| (0: no phase)
 };
 
 // Scalar state of a fresh solve; last block of the init kernel, all threads call, bb identical in
@@ -43,7 +41,7 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
   const int trivial = !(bb > 0.0);  // b = 0 (every x_k = 0) or a non-finite source
   if (k < ip.n) {
     sd->s[k] = ip.s[k];
-    sd->zeta[k] = sd->zeta_prev[k] = sd->zeta_new[k] = 1.0;
+    sd->zeta[k] = sd->zeta_prev[k] = 1.0;
     sd->active[k] = sd->wactive[k] = trivial ? 0 : 1;
     sd->P[k] = 1.0;
     sd->X[k] = 0.0;
@@ -75,21 +73,97 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
     sd->shift_iters = 0;
     sd->max_windows = ip.maxiter / kWindow + 2;
     sd->n_active = trivial ? 0 : ip.n;
+    sd->halt1 = ip.df_switch > 0.0 ? 0 : 1;
+    sd->demoted = 0;
+    sd->windows_df = 0;
+    sd->switch2 = ip.df_switch * ip.df_switch * bb;
     sd->status = isfinite(bb) ? LQCD_OK : LQCD_ERR_NONFINITE;
     sd->done = trivial ? 1 : 0;
   }
 }
 
+// The base iteration needs only alpha and beta; the per-shift recurrences (zeta_k, the window
+// coefficients, the stopping tests of the shifts) depend on nothing but the sequence of alpha and
+// beta.  So the two steps below store the base scalars of the iteration and decide the base
+// stopping test, and window_scalars() replays the per-shift recurrences of the whole window once,
+// before the window update, with the same operations in the same order as an iteration-by-iteration
+// evaluation.  The base shift stops last: for s_k >= 0, |zeta_k| <= 1 (zeta_k is the inverse of the
+// base residual polynomial at -s_k), and zeta_0 = 1 exactly, so "every shift has stopped" is "the
+// base residual has": |r_new|^2 <= tol^2 |b|^2.
+
 // the block that runs the step; all its threads call.  pa = (Re<p, q>, alpha = |r|^2 / Re<p, q>
-// with its FP32 and (hi, lo) copies), formed once by thread 0 (every FP64 division costs tens of
-// cycles per warp on GB300's narrow FP64 pipe, and the step is on the iteration's critical path).
+// with its FP32 and (hi, lo) copies), formed once by thread 0 of every block.
 __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, const PartialsRatio& pa) {
+  if (threadIdx.x != 0) return;
+  const double pq = pa.sum, alpha = pa.ratio;
+  const bool ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
+  const int m = sd->m;
+  sd->pq = pq;
+  sd->rr_b = sd->rr;
+  sd->alpha = alpha;
+  sd->alpha_f = pa.ratio_f;
+  sd->alpha_df = pa.ratio_df;
+  if (m < kWindow) sd->alpha_h[m] = alpha;
+  if (!ok) {
+    sd->status = LQCD_ERR_NONFINITE;
+    sd->done = 1;
+  }
+}
+
+// the block that runs the step; all its threads call.  pb = (|r_new|^2, beta = |r_new|^2 / |r|^2
+// with its FP32 and (hi, lo) copies), formed once by thread 0 of every block.
+__device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRatio& pb) {
+  if (threadIdx.x != 0) return;
+  const double rr_new = pb.sum, beta = pb.ratio;
+  const int m = sd->m, iter = sd->iter;
+  if (!(isfinite(rr_new) && isfinite(beta))) {
+    sd->beta = beta;
+    sd->status = LQCD_ERR_NONFINITE;
+    sd->done = 1;
+    return;
+  }
+  if (m >= kWindow) {  // the host flushes every kWindow iterations; never index past the window
+    sd->beta = beta;
+    sd->status = LQCD_ERR_STATE;
+    sd->done = 1;
+    return;
+  }
+  sd->beta_h[m] = beta;
+  sd->rr_h[m] = rr_new;
+  const int it = iter + 1;
+  // the base shift's test (zeta_0 = 1): zeta_0^2 |r_new|^2 <= tol^2 |b|^2
+  const int done = (rr_new <= sd->stop2 || it >= sd->maxiter) ? 1 : 0;
+  sd->beta = beta;
+  sd->beta_f = pb.ratio_f;
+  sd->beta_df = pb.ratio_df;
+  sd->m = m + 1;
+  sd->rr = rr_new;
+  sd->iter = it;
+  if (done) sd->done = 1;
+  const double rmax = fmax(sd->rr_ru_max, rr_new);
+  sd->rr_ru_max = rmax;
+  const int due = (it - sd->iter_ru >= sd->ru_interval) || (rr_new < sd->ru_delta2 * rmax);
+  sd->ru_skip = (done || !due) ? 1 : 0;
+}
+
+// Per-shift recurrences of the pending window's m iterations, replayed from alpha_h, beta_h, rr_h;
+// one warp, lane k owns shift k.  Iteration j (alpha = alpha_h[j], beta = beta_h[j]):
+//   alpha part:  den = alpha beta_prev (zeta_prev - zeta) + zeta_prev alpha_prev (1 + s_k alpha)
+//                q = zeta_prev alpha_prev / den,  zeta' = zeta q,  alpha_k = alpha q
+//                x_k += alpha_k p_k    ->  X += alpha_k P,  chi_i += alpha_k pi_i  (i < j)
+//   beta part:   beta_k = beta q^2
+//                p_k = zeta' r_j+1 + beta_k p_k  ->  P *= beta_k, pi_i *= beta_k (i < j), pi_j = zeta'
+//                shift k stops once zeta'^2 |r_j+1|^2 <= tol^2 |b|^2 (then takes no later residual)
+// (zeta' = zeta zeta_prev alpha_prev / den, formed as zeta q: one FP64 division.)
+__device__ __forceinline__ void window_scalars(SolverDev* sd) {
   if (threadIdx.x >= 32) return;
   const int k = threadIdx.x;
-  const double rr = sd->rr, alpha_prev = sd->alpha_prev, beta_prev = sd->beta_prev;
   const int n = sd->n, m = sd->m;
+  const double stop2 = sd->stop2;
+  double ap = sd->alpha_prev, bp = sd->beta_prev;
   const bool mine = k < n;
-  const int act = mine ? sd->active[k] : 0;
+  const int act0 = mine ? sd->active[k] : 0;
+  int act = act0;
   double z = 1.0, zp = 1.0, sk = 0.0, P = 0.0, X = 0.0, pi[kWindow], chi[kWindow];
   if (act) {
     z = sd->zeta[k];
@@ -97,118 +171,59 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, const PartialsR
     sk = sd->s[k];
     P = sd->P[k];
     X = sd->X[k];
+  }
+#pragma unroll
+  for (int i = 0; i < kWindow; ++i) pi[i] = chi[i] = 0.0;
+  int shift_iters = 0;
+  for (int j = 0; j < m; ++j) {
+    const double alpha = sd->alpha_h[j], beta = sd->beta_h[j], rr_new = sd->rr_h[j];
+    shift_iters += __popc(__ballot_sync(0xffffffffu, act != 0));
+    if (act) {
+      const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + sk * alpha);
+      const double q = zp * ap / den;
+      const double zn = z * q;
+      const double ak = alpha * q;
+      X = X + ak * P;
+#pragma unroll
+      for (int i = 0; i < kWindow; ++i)
+        if (i < j) chi[i] = chi[i] + ak * pi[i];
+      const double bk = beta * q * q;
+      P = P * bk;
+      const bool stop = zn * zn * rr_new <= stop2;
+#pragma unroll
+      for (int i = 0; i < kWindow; ++i) {
+        if (i < j) pi[i] = pi[i] * bk;
+        else if (i == j) pi[i] = zn;
+        else if (stop) pi[i] = 0.0;
+        if (i == j || (i > j && stop)) chi[i] = 0.0;
+      }
+      zp = z;
+      z = zn;
+      if (stop) act = 0;
+    }
+    ap = alpha;
+    bp = beta;
+  }
+  if (act0) {
+    sd->zeta[k] = z;
+    sd->zeta_prev[k] = zp;
+    sd->P[k] = P;
+    sd->X[k] = X;
 #pragma unroll
     for (int i = 0; i < kWindow; ++i) {
-      pi[i] = (i < m) ? sd->pi[k][i] : 0.0;
-      chi[i] = (i < m) ? sd->chi[k][i] : 0.0;
+      if (i < m) {
+        sd->pi[k][i] = pi[i];
+        sd->chi[k][i] = chi[i];
+      }
     }
+    sd->active[k] = act;
   }
-  const double pq = pa.sum, alpha = pa.ratio;
-  const bool ok = (pq > 0.0) && isfinite(alpha) && isfinite(pq);
+  const int n_active = __popc(__ballot_sync(0xffffffffu, act != 0));
   if (k == 0) {
-    sd->pq = pq;
-    sd->rr_b = rr;
-    sd->alpha = alpha;
-    sd->alpha_f = pa.ratio_f;
-    sd->alpha_df = pa.ratio_df;
-    if (!ok) {
-      sd->status = LQCD_ERR_NONFINITE;
-      sd->done = 1;
-    }
-  }
-  if (!ok || !act) return;
-  const double den = alpha * beta_prev * (zp - z) + zp * alpha_prev * (1.0 + sk * alpha);
-  // zeta_k' = zeta_k zeta_k^old alpha_old / den, formed as zeta_k q with q = zeta_k'/zeta_k (one
-  // FP64 division instead of two; q is reused by the beta step)
-  const double q = zp * alpha_prev / den;
-  const double zn = z * q;
-  const double ak = alpha * q;
-  sd->zeta_new[k] = zn;
-  sd->zratio[k] = q;
-  sd->X[k] = X + ak * P;
-#pragma unroll
-  for (int i = 0; i < kWindow; ++i)
-    if (i < m) sd->chi[k][i] = chi[i] + ak * pi[i];
-}
-
-// the block that runs the step; all its threads call.  pb = (|r_new|^2, beta = |r_new|^2 / |r|^2
-// with its FP32 and (hi, lo) copies), formed once by thread 0.
-__device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRatio& pb) {
-  if (threadIdx.x >= 32) return;
-  const int k = threadIdx.x;
-  const double stop2 = sd->stop2, alpha = sd->alpha;
-  const int n = sd->n, m = sd->m, iter = sd->iter, maxiter = sd->maxiter;
-  const int iter_ru = sd->iter_ru, ru_interval = sd->ru_interval;
-  const double ru_delta2 = sd->ru_delta2, rr_ru_max = sd->rr_ru_max;
-  const bool mine = k < n;
-  const int act = mine ? sd->active[k] : 0;
-  double z = 1.0, zn = 1.0, zr = 1.0, P = 0.0, pi[kWindow];
-  if (act) {
-    z = sd->zeta[k];
-    zn = sd->zeta_new[k];
-    zr = sd->zratio[k];
-    P = sd->P[k];
-#pragma unroll
-    for (int i = 0; i < kWindow; ++i) pi[i] = (i < m) ? sd->pi[k][i] : 0.0;
-  }
-  const double rr_new = pb.sum, beta = pb.ratio;
-  const bool ok = isfinite(rr_new) && isfinite(beta);
-  if (!ok) {
-    if (k == 0) {
-      sd->beta = beta;
-      sd->status = LQCD_ERR_NONFINITE;
-      sd->done = 1;
-    }
-    return;
-  }
-  if (m >= kWindow) {  // the host flushes every kWindow iterations; never index past the window
-    if (k == 0) {
-      sd->beta = beta;
-      sd->status = LQCD_ERR_STATE;
-      sd->done = 1;
-    }
-    return;
-  }
-  int still = 0;
-  if (act) {
-    const double bk = beta * zr * zr;  // zr = zn / z, formed by the alpha step
-    sd->P[k] = P * bk;
-    const bool stop = zn * zn * rr_new <= stop2;
-#pragma unroll
-    for (int i = 0; i < kWindow; ++i) {
-      if (i < m) sd->pi[k][i] = pi[i] * bk;
-      // this iteration's residual enters at position m; a shift that stops here takes no later one
-      else if (i == m) sd->pi[k][i] = zn;
-      else if (stop) sd->pi[k][i] = 0.0;
-      if (i == m || (i > m && stop)) sd->chi[k][i] = 0.0;
-    }
-    sd->zeta_prev[k] = z;
-    sd->zeta[k] = zn;
-    if (stop) sd->active[k] = 0;
-    still = !stop;
-  }
-  // count shifts still active (warp 0 holds all of them, n <= 32)
-  const unsigned bal = __ballot_sync(0xffffffffu, still);
-  const unsigned bal_it = __ballot_sync(0xffffffffu, act != 0);
-  if (k == 0) {
-    const int n_active = __popc(bal);
-    sd->shift_iters += __popc(bal_it);
-    const int it = iter + 1;
-    const int done = (n_active == 0 || it >= maxiter) ? 1 : 0;
-    sd->beta = beta;
-    sd->beta_f = pb.ratio_f;
-    sd->beta_df = pb.ratio_df;
+    sd->alpha_prev = ap;
+    sd->beta_prev = bp;
     sd->n_active = n_active;
-    sd->m = m + 1;
-    sd->rr = rr_new;
-    sd->alpha_prev = alpha;
-    sd->beta_prev = beta;
-    sd->iter = it;
-    if (done) sd->done = 1;
-    const double rmax = fmax(rr_ru_max, rr_new);
-    sd->rr_ru_max = rmax;
-    const int due = (it - iter_ru >= ru_interval) || (rr_new < ru_delta2 * rmax);
-    sd->ru_skip = (done || !due) ? 1 : 0;
+    sd->shift_iters += shift_iters;
   }
 }
 

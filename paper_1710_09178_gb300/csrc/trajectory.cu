@@ -89,7 +89,7 @@ __device__ __forceinline__ void add_to(M3& a, const M3& b) {
 }
 
 __device__ __forceinline__ int addr_shift(const Geom& g, const Site& s, int mu, int step) {
-  return step > 0 ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu);
+  return neighbour_addr(g, step > 0 ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu));
 }
 
 __device__ __forceinline__ Site site_at(const Geom& g, int l) {
@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(128) plaquette_kernel(Geom g, const double2* _
   if (l < V) {
     Site s = site_at(g, l);
     for (int mu = 0; mu < 4; ++mu) {
-      int xm = neighbour_fwd(g, s, mu);
+      int xm = neighbour_addr(g, neighbour_fwd(g, s, mu));
       M3 Um = ldm(U + ((size_t)l * 4 + mu) * 9);
       for (int nu = mu + 1; nu < 4; ++nu) {
-        int xn = neighbour_fwd(g, s, nu);
+        int xn = neighbour_addr(g, neighbour_fwd(g, s, nu));
         M3 a = mm(Um, ldm(U + ((size_t)xm * 4 + nu) * 9));
         M3 b = mm(ldm(U + ((size_t)l * 4 + nu) * 9), ldm(U + ((size_t)xn * 4 + mu) * 9));
         // Re tr(a b^+) = sum_ij Re(a_ij conj(b_ij))
@@ -144,16 +144,16 @@ __global__ void __launch_bounds__(128) gauge_force_kernel(Geom g, const double2*
   if (t >= 4LL * V) return;
   const int l = (int)(t >> 2), mu = (int)(t & 3);
   Site s = site_at(g, l);
-  const int xpmu = neighbour_fwd(g, s, mu);
+  const int xpmu = neighbour_addr(g, neighbour_fwd(g, s, mu));
   Site sp = site_at(g, xpmu);
   M3 A;
 #pragma unroll
   for (int i = 0; i < 9; ++i) A.e[i] = make_double2(0, 0);
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
-    const int xpnu = neighbour_fwd(g, s, nu);
-    const int xmnu = neighbour_bwd(g, s, nu);
-    const int xpmu_mnu = neighbour_bwd(g, sp, nu);
+    const int xpnu = neighbour_addr(g, neighbour_fwd(g, s, nu));
+    const int xmnu = neighbour_addr(g, neighbour_bwd(g, s, nu));
+    const int xpmu_mnu = neighbour_addr(g, neighbour_bwd(g, sp, nu));
     // up = U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ ; down = U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)
     M3 up = mm(mm(ldm(U + ((size_t)xpmu * 4 + nu) * 9), dagger(ldm(U + ((size_t)xpnu * 4 + mu) * 9))),
                dagger(ldm(U + ((size_t)l * 4 + nu) * 9)));

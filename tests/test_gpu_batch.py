@@ -131,3 +131,51 @@ def test_dslash_batch_rejects_bad_arguments():
     with pytest.raises(lq.LqcdError):
         lq.dslash_eo_batch([ctx] * (lq.MAX_BATCH + 1), [w] * (lq.MAX_BATCH + 1), [v] * (lq.MAX_BATCH + 1),
                            [0] * (lq.MAX_BATCH + 1), lq.FP32)
+
+
+def test_dslash_batch_of_many_lattices_in_one_launch_and_under_capture():
+    # 70 lattices (more than one parameter block holds): one persistent launch from the uploaded
+    # descriptor table; a new set of descriptors first met inside a CUDA-graph capture takes the
+    # parameter-block launches instead.  Both give the bits of one dslash_eo per lattice.
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    sizes = [(4, 4, 4, 4), (6, 4, 2, 4), (8, 4, 4, 2), (2, 2, 2, 2), (10, 6, 4, 6)]
+    ctxs, ins, outs, pars = [], [], [], []
+    for li in range(70):
+        dims = sizes[li % len(sizes)]
+        ctx, _ = make_context(dims, 0.05, gauge_seed=100 + li % 7)
+        vin = ctx.new_vector(lq.FP32)
+        ctx.pack(vin, lq.FP32, to_dev(inputs.gaussian_vector(dims, 200 + li)))
+        ctxs.append(ctx)
+        ins.append(vin)
+        outs.append(ctx.new_vector(lq.FP32))
+        pars.append((li // 3) & 1)
+    launches = ctxs[0].launch_count()
+    lq.dslash_eo_batch(ctxs, outs, ins, pars, lq.FP32)
+    torch.cuda.synchronize()
+    assert ctxs[0].launch_count() - launches == 1
+    singles = []
+    for ctx, vin, vout, p in zip(ctxs, ins, outs, pars):
+        single = ctx.new_vector(lq.FP32)
+        lq.dslash_eo(ctx, single, vin, p, lq.FP32)
+        torch.cuda.synchronize()
+        assert torch.equal(single, vout)
+        singles.append(single)
+    # the other parity, first met during a capture on the contexts' stream
+    s = torch.cuda.Stream()
+    for c in ctxs:
+        c.set_stream(s.cuda_stream)
+    outs2 = [c.new_vector(lq.FP32) for c in ctxs]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        lq.dslash_eo_batch(ctxs, outs2, ins, [1 - p for p in pars], lq.FP32)
+    g.replay()
+    torch.cuda.synchronize()
+    for ctx, vin, vout, p in zip(ctxs, ins, outs2, pars):
+        single = ctx.new_vector(lq.FP32)
+        lq.dslash_eo(ctx, single, vin, 1 - p, lq.FP32)
+        torch.cuda.synchronize()
+        assert torch.equal(single, vout)

@@ -166,3 +166,38 @@ def test_chain_resumes_from_checkpoint(tmp_path):
     ctx2.close()
     assert first + rest == full
     assert np.array_equal(Uc.cpu().numpy().view(np.uint64), Ua.cpu().numpy().view(np.uint64))
+
+
+def test_trajectory_is_reversible_at_24c6():
+    # The RHMC workload's lattice and integrator (24^3 x 6, beta 5.4, m 0.025, tau 1 in 25 Omelyan
+    # steps, 16-pole x^{-1/2}): with every solve and the MD in FP64, one trajectory forward and one
+    # back from the proposal with reversed momenta return the links to 1e-10 (Section 3.1: the MD map
+    # is reversible) and dH changes sign
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass, beta, tau, nsteps = (24, 24, 24, 6), 0.025, 5.4, 1.0, 25
+    lo, hi = 4 * mass ** 2, 16 + 4 * mass ** 2
+    c0, res, poles, _ = lq.rational_coeffs(-0.5, lo, hi, 16)
+    ctx, U0 = make_context(dims, mass, gauge_seed=9)
+    V = int(np.prod(dims))
+    p0 = inputs.counter_normal_pairs(9000, np.arange(4 * V, dtype=np.uint64), 4).reshape(V, 4, 8)
+    phi = to_dev(inputs.gaussian_vector(dims, 9500))  # any pseudofermion field serves for reversibility
+    Ud = to_dev(U0)
+    links = torch.empty_like(Ud)
+    mom = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+    act = (c0, res, poles)
+    rc, r1 = lq.rhmc_trajectory(ctx, Ud, to_dev(p0), phi, 1.0 + 1e9, beta, tau, nsteps, act, tol=1e-12,
+                                prec=FP64, prec_action=FP64, phi_given=True, mom_out=mom, links_out=links)
+    assert rc == 0 and r1["accepted"] == 0
+    U1 = links.clone()
+    back_links = torch.empty_like(Ud)
+    back_mom = torch.empty_like(mom)
+    rc, r2 = lq.rhmc_trajectory(ctx, U1, -mom, phi, 1.0 + 1e9, beta, tau, nsteps, act, tol=1e-12, prec=FP64,
+                                prec_action=FP64, phi_given=True, mom_out=back_mom, links_out=back_links)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.max(np.abs(back_links.cpu().numpy() - U0)) < 1e-10
+    assert np.max(np.abs(back_mom.cpu().numpy() + p0)) < 1e-8
+    assert abs(r1["dH"] + r2["dH"]) < 1e-6 * max(1.0, abs(r1["dH"]))
