@@ -497,21 +497,39 @@ def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True
             xs = [torch.empty_like(b) for _ in range(npoles)]
             problems.append(dict(ctx=ctx, shifts=poles, residues=res, c0=c0, b=b, xs=xs, y=torch.empty_like(b),
                                  tol=1e-10, prec=lq.FP32))
+    # the same sources as one multi-right-hand-side problem per lattice (mshift_cg_multi on the owner
+    # context: the four pseudofermions share the kernel launches and the FP32 Dslash link loads)
+    multi = []
+    for l, owner in enumerate(owners):
+        mine = problems[l * n_pf:(l + 1) * n_pf]
+        multi.append(dict(ctx=owner, shifts=mine[0]["shifts"], residues=mine[0]["residues"], c0=mine[0]["c0"],
+                          bs=[p["b"] for p in mine], xss=[[torch.empty_like(p["b"]) for _ in p["xs"]] for p in mine],
+                          ys=[torch.empty_like(p["b"]) for p in mine], tol=1e-10, prec=lq.FP32))
     # warm-up (workspace allocation, graph capture), then timed runs
     lq.mshift_cg_batch(problems, nthreads=nthreads)
+    lq.mshift_cg_batch(multi, nthreads=min(nthreads, len(multi)))
     torch.cuda.synchronize()
     out = {}
-    for name, nt in (("sequential", 1), ("batched", nthreads)):
+    for name, probs, nt in (("sequential", problems, 1), ("batched", problems, nthreads),
+                            ("multi_rhs_batched", multi, min(nthreads, len(multi)))):
         t0 = time.perf_counter()
-        rc, st, stats = lq.mshift_cg_batch(problems, nthreads=nt)
+        rc, st, stats = lq.mshift_cg_batch(probs, nthreads=nt)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        flat = [x for s in stats for x in (s if isinstance(s, list) else [s])]
         out[name] = {"ms": dt * 1e3, "problems_per_s": len(problems) / dt, "status_ok": all(x == 0 for x in st),
-                     "max_true_residual": max(max(s["true_residual"]) for s in stats)}
+                     "max_true_residual": max(max(s["true_residual"]) for s in flat), "host_threads": nt,
+                     "solve_calls": len(probs)}
+    # the multi-RHS solves against the stand-alone ones (bit-identical when the stand-alone solve runs
+    # one thread per site; the autotuned contexts may run more, which reorders the Dslash sums)
+    out["multi_rhs_vs_single_max_rel_diff"] = max(
+        float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+        for l, mp in enumerate(multi) for f in range(n_pf) for a, c in zip(mp["xss"][f], problems[l * n_pf + f]["xs"]))
     sites = sum(int(np.prod(d)) // 2 for d, _ in picks) * n_pf
     out.update({"lattices": n_lat, "pseudofermions": n_pf, "poles": npoles, "problems": len(problems),
                 "even_sites_total": sites, "threads": nthreads,
                 "speedup": out["sequential"]["ms"] / out["batched"]["ms"],
+                "speedup_multi_rhs": out["sequential"]["ms"] / out["multi_rhs_batched"]["ms"],
                 "volumes_drawn": {str(v): sum(1 for d, _ in picks if d == v) for v in C4_VOLUMES},
                 "autotuned_tps": {str(v): sorted(set(t for (d, _), t in zip(picks, tps) if d == v)) for v in C4_VOLUMES}
                 if autotune else None})
@@ -521,6 +539,23 @@ def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True
         o.close()
     out["dslash_batch"] = run_batch_dslash(lq, torch, picks)
     return out
+
+
+def batch_summary(b, peak):
+    """The batch workload's headline numbers for the default bench line."""
+    d = b["dslash_batch"]["persistent_batch"]
+    return {"workload": f"{b['lattices']} lattices (8^4, 12^3x4, 16^3x4, 16^3x8 drawn with seed 7) x "
+                        f"{b['pseudofermions']} pseudofermions, {b['poles']}-pole x^-1/2 to 1e-10, FP32 mode",
+            "problems": b["problems"],
+            "ms_sequential": b["sequential"]["ms"], "ms_batched": b["batched"]["ms"],
+            "ms_multi_rhs_batched": b["multi_rhs_batched"]["ms"],
+            "problems_per_s_multi_rhs": b["multi_rhs_batched"]["problems_per_s"],
+            "problems_per_s_batched": b["batched"]["problems_per_s"],
+            "multi_rhs_vs_single_max_rel_diff": b["multi_rhs_vs_single_max_rel_diff"],
+            "max_true_residual": max(b[k]["max_true_residual"] for k in ("sequential", "batched", "multi_rhs_batched")),
+            "dslash_sweep_us": d["us_per_sweep"], "dslash_sweep_GBps": d["algorithmic_GBps"],
+            "dslash_sweep_frac_of_hbm": d["algorithmic_GBps"] / peak,
+            "dslash_launches_per_sweep": d["launches_per_sweep"]}
 
 
 def run_batch_dslash(lq, torch, picks, reps=20):
@@ -585,6 +620,97 @@ def run_batch_dslash(lq, torch, picks, reps=20):
     return res
 
 
+def tiled_field(torch, base_dims, reps, seed):
+    """The seeded field of base_dims tiled reps[mu] times along each direction (a valid SU(3) field
+    of the larger lattice, periodic with the base extents), built on the device."""
+    from paper_1710_09178_gb300 import inputs
+
+    U = torch.from_numpy(inputs.gauge_field(base_dims, seed=seed)).cuda()
+    nx, ny, nz, nt = base_dims
+    U = U.reshape(nt, nz, ny, nx, 4, 3, 3)  # l = x + nx (y + ny (z + nz t))
+    U = U.repeat(reps[3], reps[2], reps[1], reps[0], 1, 1, 1)
+    dims = tuple(b * r for b, r in zip(base_dims, reps))
+    return dims, U.reshape(-1, 4, 3, 3).contiguous()
+
+
+def run_formats(lq, torch, dims_list=((32, 32, 32, 8), (48, 48, 48, 12)), reps=20):
+    """Every link format of the half-Dslash (FP32 18-real, 12-real, 8-real, 16-bit) with 1, 2 and 4
+    threads per site, at 32^3x8 (FP32 links 75.5 MB, inside the L2) and 48^3x12 (382 MB, the
+    seeded 24^3x6 field tiled 2x2x2x2): CUDA-event time per launch of a graph of launches
+    rotating over enough copies of the field that every launch reads its links from HBM, and the
+    mixed solve (16 poles, tol 1e-10) in each format."""
+    from paper_1710_09178_gb300 import inputs
+
+    fmts = (("fp32", lq.FP32), ("fp32_r12", lq.FP32_R12), ("fp32_r8", lq.FP32_R8), ("fp32_l16", lq.FP32_L16))
+    peak, _ = read_peaks()
+    out = {}
+    flush = L2Flusher(torch)
+    for dims in dims_list:
+        if dims == (32, 32, 32, 8):
+            U = torch.from_numpy(inputs.gauge_field(dims, seed=GAUGE_SEED)).cuda()
+            src = "seeded field, seed 5"
+        else:
+            dims, U = tiled_field(torch, (24, 24, 24, 6), (2, 2, 2, 2), 9)
+            src = "the seeded 24^3x6 field (seed 9) tiled 2x2x2x2"
+        vh = int(np.prod(dims)) // 2
+        n_fields = max(2, int(np.ceil(2 * 160e6 / (72 * 4 * 2 * vh))) + 1)
+        res = {"source": src, "fields_rotated": n_fields}
+        for name, prec in fmts:
+            row = {}
+            for tps in (1, 2, 4):
+                s_ = torch.cuda.Stream()
+                torch.cuda.synchronize()
+                sctx = []
+                for _ in range(n_fields):
+                    c = lq.Context(dims, MASS, stream=s_.cuda_stream)
+                    c.set_gauge(U)
+                    c.set_option(lq.OPT_DSLASH_TPS, tps)
+                    vin, vout = c.new_vector(prec), c.new_vector(prec)
+                    vin.view(torch.float32).normal_()
+                    sctx.append((c, vin, vout))
+                with torch.cuda.stream(s_):
+                    for i in range(2 * n_fields):
+                        c, vin, vout = sctx[i % n_fields]
+                        lq.dslash_eo(c, vout, vin, (i // n_fields) & 1, prec)
+                    s_.synchronize()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=s_, capture_error_mode="thread_local"):
+                        for i in range(reps * n_fields):
+                            c, vin, vout = sctx[i % n_fields]
+                            lq.dslash_eo(c, vout, vin, (i // n_fields) & 1, prec)
+                    g.replay()
+                    ms = []
+                    for _ in range(3):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(s_)
+                        g.replay()
+                        e1.record(s_)
+                        e1.synchronize()
+                        ms.append(e0.elapsed_time(e1) / (reps * n_fields))
+                torch.cuda.synchronize()
+                for c, _, _ in sctx:
+                    c.close()
+                m = statistics.median(ms)
+                gbs = DSLASH_BYTES_PER_SITE[name] * vh / (m * 1e-3) / 1e9
+                row[f"tps{tps}"] = {"us": m * 1e3, "algorithmic_GBps": gbs, "frac_of_hbm": gbs / peak}
+            # the mixed solve in this format
+            ctx = lq.Context(dims, MASS)
+            ctx.set_gauge(U)
+            b = torch.from_numpy(inputs.gaussian_vector(dims, VEC_SEED)).cuda()
+            c0, rr, poles, _ = lq.rational_coeffs(-0.5, 4 * MASS * MASS, 16 + 4 * MASS * MASS, NPOLES)
+            xs = [torch.empty_like(b) for _ in poles]
+            tms, sts = time_solves(lq, torch, ctx, b, xs, None, (c0, rr, poles, None), prec, 3, 1, flush)
+            row["solve_ms"] = statistics.median(tms)
+            row["solve_iterations"] = sts[-1]["iterations"]
+            row["solve_refine_iterations"] = sts[-1]["refine_iterations"]
+            row["solve_max_true_residual"] = max(sts[-1]["true_residual"])
+            ctx.close()
+            res[name] = row
+        out["x".join(str(d) for d in dims)] = res
+    return out
+
+
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
     `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
@@ -636,8 +762,20 @@ def main():
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
     ap.add_argument("--therm", type=int, default=20, help="thermalising trajectories before the --rhmc ones")
+    ap.add_argument("--rhmc-meas", type=int, default=12, help="Metropolis trajectories of the default run's RHMC part")
     ap.add_argument("--batch", action="store_true", help="run the 64-lattice batched workload, print one JSON line")
+    ap.add_argument("--formats", action="store_true", help="link formats x threads per site at 32^3x8 and 48^3x12")
     args = ap.parse_args()
+    if args.formats:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_1710_09178_gb300 as lq
+
+        print(json.dumps({"formats": run_formats(lq, torch)}), flush=True)
+        return
     if args.batch:
         import torch
 
@@ -801,15 +939,16 @@ def main():
 
     # ---- one RHMC trajectory on 24^3x6 (NEXT rows: force + integrator), after one warm-up ----
     traj = None
+    batch = None
     if not args.quick:
-        tr = run_trajectories(lq, torch, 2)
-        t = tr[-1]
-        traj = {"workload": "24^3x6, beta 5.4, m 0.025, 16 poles, Omelyan tau 1, 25 steps",
-                "ms_per_trajectory": t["event_ms"], "dH": t["dH"], "accepted": t["accepted"],
-                "solves": t["solves"], "iterations": t["iterations"],
-                "start": "the synthetic exp(i 0.5 H) field, far rougher than an equilibrium ensemble at beta 5.4: "
-                         "the MD energy error is large from it (it falls as step^2; acceptance over thermalised "
-                         "chains is tested on 4^4)"}
+        # 20 thermalising trajectories from the synthetic start (accepted whatever their dH), then 12
+        # with the Metropolis test: acceptance and <exp(-dH)> of the equilibrated chain
+        tr = run_trajectories(lq, torch, args.therm + args.rhmc_meas, n_therm=args.therm)
+        traj = rhmc_summary(tr, TRAJ_STEPS)
+        traj["start"] = ("the synthetic exp(i 0.5 H) field, thermalised by the first trajectories (accepted whatever "
+                         "their dH); the summary statistics cover the Metropolis trajectories after them")
+        # the batched workload: 64 lattices x 4 pseudofermions
+        batch = batch_summary(run_batch(lq, torch), read_peaks()[0])
 
     # ---- CPU baseline: the C++ FP64 oracle's complete solve on the host cores; GPU errors against it ----
     cpu = None
@@ -857,6 +996,7 @@ def main():
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/solve", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "rhmc_trajectory": traj,
+        "batch": batch,
         "gpu_launches": launches_timed,
         "clocks": clk,
         "wall_s_timed": t_wall,

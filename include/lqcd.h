@@ -279,6 +279,31 @@ int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n
               lqcd_solve_stats* stats);
 
 /*
+ * mshift_cg_multi - mshift_cg for nrhs right-hand sides on one lattice at once (e.g. the
+ * pseudofermions of one gauge field in a batched RHMC; a property of the library, the paper
+ * solves one source at a time).  Every system runs exactly the shifted CG that mshift_cg runs on
+ * it alone (the same iterations, reliable updates, phase change and refinement, with identical
+ * results); they share the kernel launches, and in the FP32 iterations the Dslash loads every link
+ * once for all of them.
+ *   nrhs    : 1 <= nrhs <= LQCD_MAX_RHS
+ *   b_devs  : host array of nrhs device sources, complex128 [Vh][3] each, all distinct
+ *   x_devs  : NULL, or host array of nrhs entries, each NULL or a host array of n device outputs as
+ *             in mshift_cg
+ *   y_devs  : NULL, or host array of nrhs entries, each NULL or a device output as in mshift_cg
+ *   stats   : NULL, or host array of nrhs lqcd_solve_stats (per system; kernel_launches and ms
+ *             count the whole call)
+ *   other arguments as in mshift_cg.  nrhs > 1 needs an FP32 Krylov mode (LQCD_FP32, LQCD_FP32_R12,
+ *   LQCD_FP32_R8, LQCD_FP32_L16, LQCD_FP16FIX) and double-FP32 residuals (LQCD_OPT_DF_RESID 1,
+ *   the default): LQCD_ERR_ARG otherwise.
+ * Returns LQCD_OK when every system converged, else the first failing system's status.
+ * Synchronises the context stream.
+ */
+#define LQCD_MAX_RHS 4
+int mshift_cg_multi(lqcd_ctx* ctx, int nrhs, const double* shifts, const double* residues, int n, double c0,
+                    const double* const* b_devs, double* const* const* x_devs, double* const* y_devs, double tol,
+                    int maxiter, int prec, lqcd_solve_stats* stats);
+
+/*
  * fermion_force - derivative of the pseudofermion action S_f = phi^+ r(A) phi,
  * r(A) = c0 + sum_k c_k (A + d_k)^{-1}, with respect to the links: the force of the
  * momentum equation of the MD step (Section 3.1; r from Eq. ratapprx, usually the x^{-1/2}
@@ -312,16 +337,22 @@ typedef struct {
   double tol;
   int maxiter;
   int prec;
-  lqcd_solve_stats* stats;    /* may be NULL */
-  int status;                 /* output: mshift_cg's status for this problem */
+  lqcd_solve_stats* stats;    /* may be NULL; an array of nrhs entries when nrhs >= 2 */
+  int status;                 /* output: mshift_cg's (mshift_cg_multi's) status for this problem */
+  int nrhs;                   /* 0 or 1: the one source b_dev (mshift_cg); 2 .. LQCD_MAX_RHS: the sources
+                                 b_devs of one lattice solved together (mshift_cg_multi) */
+  const double* const* b_devs;   /* nrhs >= 2: as in mshift_cg_multi (b_dev, x_dev, y_dev unused) */
+  double* const* const* x_devs;
+  double* const* y_devs;
 } lqcd_batch_problem;
 
 /*
  * mshift_cg_batch - many independent shifted-CG solves (independent lattices of any size and
  * several pseudofermions per lattice, as in the batched RHMC workloads) run concurrently: a
  * pool of nthreads host threads takes problems in order, and every problem's solve graph runs on
- * its own context's stream, so solves of small lattices share the GPU.  Each problem's results
- * are exactly those of mshift_cg on its own.  Returns LQCD_OK when every problem did, else the
+ * its own context's stream, so solves of small lattices share the GPU.  A problem with nrhs >= 2
+ * solves several sources of its lattice together (mshift_cg_multi).  Each problem's results
+ * are exactly those of mshift_cg (mshift_cg_multi) on its own.  Returns LQCD_OK when every problem did, else the
  * first failing status (every problem's status is stored).  LQCD_ERR_ARG if two problems share a
  * context.  The calling thread's current device is used by all workers.
  */

@@ -51,13 +51,14 @@ OPT_DF_SWITCH = 9
 
 MAX_SHIFTS = 32
 MAX_BATCH = 128
+MAX_RHS = 4
 
 EXPORTED = [
     "lqcd_create", "lqcd_destroy", "lqcd_last_error", "lqcd_set_stream", "lqcd_set_gauge", "lqcd_vector_bytes",
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
     "fermion_force", "rhmc_trajectory", "mshift_cg_batch", "lqcd_autotune",
-    "lqcd_share_gauge", "dslash_eo_batch", "lqcd_bounds_word",
+    "lqcd_share_gauge", "dslash_eo_batch", "lqcd_bounds_word", "mshift_cg_multi",
 ]
 
 
@@ -98,6 +99,8 @@ class BatchProblem(ctypes.Structure):
         ("b_dev", ctypes.c_void_p), ("x_dev", ctypes.POINTER(ctypes.c_void_p)), ("y_dev", ctypes.c_void_p),
         ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec", ctypes.c_int),
         ("stats", ctypes.POINTER(SolveStats)), ("status", ctypes.c_int),
+        ("nrhs", ctypes.c_int), ("b_devs", ctypes.POINTER(ctypes.c_void_p)),
+        ("x_devs", ctypes.POINTER(ctypes.c_void_p)), ("y_devs", ctypes.POINTER(ctypes.c_void_p)),
     ]
 
 
@@ -194,6 +197,8 @@ def _bind(path):
         "lqcd_share_gauge": (i, [vp, vp]),
         "dslash_eo_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
         "lqcd_bounds_word": (i, [vp, ctypes.POINTER(ctypes.c_uint)]),
+        "mshift_cg_multi": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(d), i, d, ctypes.POINTER(vp),
+                                ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, i, ctypes.POINTER(SolveStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -356,6 +361,38 @@ def mshift_cg(ctx: Context, shifts, residues, c0, b, xs=None, y=None, tol=1e-10,
     return rc, st.as_dict()
 
 
+def mshift_cg_multi(ctx: Context, shifts, residues, c0, bs, xs=None, ys=None, tol=1e-10, maxiter=20000, prec=FP32,
+                    raise_on_error=True):
+    """mshift_cg for several right-hand sides bs[s] of one lattice at once (mshift_cg_multi).
+
+    bs[s], xs[s][k], ys[s]: complex128 cuda tensors of shape (Vh, 3); xs and ys may be None, and so
+    may any xs[s] or ys[s].  Returns (status, [stats dict per right-hand side])."""
+    lib = ctx.lib
+    n, S = len(shifts), len(bs)
+    vp = ctypes.c_void_p
+    sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+    rs = (ctypes.c_double * n)(*[float(c) for c in residues]) if residues is not None else None
+    bp = (vp * S)(*[_ptr(b) for b in bs])
+    keep = []
+    xp = None
+    if xs is not None:
+        rows = []
+        for s in range(S):
+            if xs[s] is None:
+                rows.append(None)
+            else:
+                row = (vp * n)(*[_ptr(x) for x in xs[s]])
+                keep.append(row)
+                rows.append(ctypes.cast(row, vp).value)
+        xp = (vp * S)(*rows)
+    yp = (vp * S)(*[_ptr(y) for y in ys]) if ys is not None else None
+    st = (SolveStats * S)()
+    rc = lib.mshift_cg_multi(ctx.handle, S, sh, rs, n, float(c0), bp, xp, yp, float(tol), int(maxiter), int(prec), st)
+    if raise_on_error and rc not in (LQCD_OK,):
+        ctx.check(rc)
+    return rc, [st[s].as_dict() for s in range(S)]
+
+
 def fermion_force(ctx: Context, shifts, residues, c0, phi, F=None, Falg=None, want_action=True, tol=1e-10,
                   maxiter=20000, prec=FP32, raise_on_error=True):
     """Force of S_f = phi^+ r(A) phi: F (V,4,3,3 complex128) and/or Falg (V,4,8 float64) device tensors.
@@ -420,34 +457,68 @@ def mshift_cg_batch(problems, nthreads=16, raise_on_error=True):
     """Run independent shifted-CG problems concurrently (mshift_cg_batch).
 
     problems: list of dicts with keys ctx, shifts, residues, c0, b, xs (list or None), y (or None),
-    tol, maxiter, prec.  Returns (status, [status per problem], [stats dict per problem]).
+    tol, maxiter, prec; a problem with several sources of its lattice has bs (list of sources), xss
+    (list of lists or None), ys (list or None) instead of b, xs, y (mshift_cg_multi).  Returns
+    (status, [status per problem], [stats dict per problem, or list of them per source]).
     """
     lib = problems[0]["ctx"].lib if problems else load_library()
     n = len(problems)
     arr = (BatchProblem * n)()
     keep = []
-    stats = [SolveStats() for _ in range(n)]
+    stats = []
+    vp = ctypes.c_void_p
     for i, pr in enumerate(problems):
         ns = len(pr["shifts"])
         sh = (ctypes.c_double * ns)(*[float(v) for v in pr["shifts"]])
         rs = (ctypes.c_double * ns)(*[float(v) for v in pr["residues"]])
-        xs = pr.get("xs")
-        xp = (ctypes.c_void_p * ns)(*[_ptr(x) for x in xs]) if xs is not None else None
-        keep += [sh, rs, xp]
+        keep += [sh, rs]
         a = arr[i]
         a.ctx = pr["ctx"].handle
         a.shifts, a.residues, a.n, a.c0 = sh, rs, ns, float(pr.get("c0", 0.0))
-        a.b_dev = _ptr(pr["b"])
-        a.x_dev = xp
-        a.y_dev = _ptr(pr.get("y"))
+        if "bs" in pr:
+            S = len(pr["bs"])
+            a.nrhs = S
+            bp = (vp * S)(*[_ptr(b) for b in pr["bs"]])
+            keep.append(bp)
+            a.b_devs = ctypes.cast(bp, ctypes.POINTER(vp))
+            xss = pr.get("xss")
+            if xss is not None:
+                rows = []
+                for row in xss:
+                    if row is None:
+                        rows.append(None)
+                    else:
+                        r = (vp * ns)(*[_ptr(x) for x in row])
+                        keep.append(r)
+                        rows.append(ctypes.cast(r, vp).value)
+                xp = (vp * S)(*rows)
+                keep.append(xp)
+                a.x_devs = ctypes.cast(xp, ctypes.POINTER(vp))
+            ys = pr.get("ys")
+            if ys is not None:
+                yp = (vp * S)(*[_ptr(y) for y in ys])
+                keep.append(yp)
+                a.y_devs = ctypes.cast(yp, ctypes.POINTER(vp))
+            st = (SolveStats * S)()
+            a.stats = ctypes.cast(st, ctypes.POINTER(SolveStats))
+        else:
+            xs = pr.get("xs")
+            xp = (vp * ns)(*[_ptr(x) for x in xs]) if xs is not None else None
+            keep.append(xp)
+            a.b_dev = _ptr(pr["b"])
+            a.x_dev = xp
+            a.y_dev = _ptr(pr.get("y"))
+            st = SolveStats()
+            a.stats = ctypes.pointer(st)
+        stats.append(st)
         a.tol, a.maxiter, a.prec = float(pr.get("tol", 1e-10)), int(pr.get("maxiter", 20000)), int(pr.get("prec", FP32))
-        a.stats = ctypes.pointer(stats[i])
     rc = lib.mshift_cg_batch(arr, n, int(nthreads))
     st = [arr[i].status for i in range(n)]
     if raise_on_error and rc != LQCD_OK:
         bad = st.index(rc) if rc in st else 0
         problems[bad]["ctx"].check(rc)
-    return rc, st, [s.as_dict() for s in stats]
+    out = [[x.as_dict() for x in s] if isinstance(s, ctypes.Array) else s.as_dict() for s in stats]
+    return rc, st, out
 
 
 def rhmc_trajectory(ctx: Context, U, mom, xi, uniform, beta, tau, nsteps, act, heat=None, tol=1e-10, md_tol=0.0,

@@ -1,7 +1,8 @@
 // batch.cu - many independent problems at once, and the Dslash launch-shape autotuner.
 //
 // Batching.  A workload of many independent lattices (different sizes and masses) and several
-// pseudofermions per lattice runs as many shifted-CG solves.  Each problem has its own context
+// pseudofermions per lattice runs as many shifted-CG solves (one per pseudofermion, or one
+// multi-right-hand-side solve per lattice, mshift_cg_multi).  Each problem has its own context
 // (gauge copies, workspace, non-blocking stream and captured solve graph); mshift_cg_batch runs
 // them from a pool of host threads so that their graphs execute concurrently on the GPU.  Small
 // lattices cannot fill 152 SMs on their own (16^3 x 8 has 16384 output sites per half-Dslash,
@@ -103,8 +104,12 @@ extern "C" int mshift_cg_batch(lqcd_batch_problem* probs, int nprob, int nthread
       int i = next.fetch_add(1);
       if (i >= nprob) break;
       lqcd_batch_problem& p = probs[i];
-      p.status = mshift_cg(p.ctx, p.shifts, p.residues, p.n, p.c0, p.b_dev, p.x_dev, p.y_dev, p.tol, p.maxiter,
-                           p.prec, p.stats);
+      if (p.nrhs >= 2)
+        p.status = mshift_cg_multi(p.ctx, p.nrhs, p.shifts, p.residues, p.n, p.c0, p.b_devs, p.x_devs, p.y_devs,
+                                   p.tol, p.maxiter, p.prec, p.stats);
+      else
+        p.status = mshift_cg(p.ctx, p.shifts, p.residues, p.n, p.c0, p.b_dev, p.x_dev, p.y_dev, p.tol, p.maxiter,
+                             p.prec, p.stats);
     }
   };
   std::vector<std::thread> pool;

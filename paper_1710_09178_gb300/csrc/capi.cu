@@ -459,6 +459,34 @@ int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n
   return run_mshift(ctx, shifts, residues, n, c0, b_dev, x_dev, y_dev, tol, maxiter, prec, stats);
 }
 
+int mshift_cg_multi(lqcd_ctx* ctx, int nrhs, const double* shifts, const double* residues, int n, double c0,
+                    const double* const* b_devs, double* const* const* x_devs, double* const* y_devs, double tol,
+                    int maxiter, int prec, lqcd_solve_stats* stats) {
+  if (!ctx) return LQCD_ERR_ARG;
+  if (nrhs < 1 || nrhs > LQCD_MAX_RHS || !b_devs || !shifts || n < 1 || n > LQCD_MAX_SHIFTS || !prec_valid(prec) ||
+      maxiter < 1 || !(tol > 0.0))
+    return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: bad argument");
+  if (nrhs > 1 && !(vec_fp32(prec) || prec == LQCD_FP16FIX))
+    return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: more than one right-hand side needs an FP32 Krylov mode");
+  if (nrhs > 1 && !ctx->df_resid)
+    return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: more than one right-hand side needs LQCD_OPT_DF_RESID 1");
+  if (y_devs && !residues) return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: y requested without residues");
+  for (int k = 0; k < n; ++k)
+    if (!(shifts[k] >= 0.0) || !isfinite(shifts[k]))
+      return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: shifts must be >= 0");
+  for (int s = 0; s < nrhs; ++s) {
+    if (!b_devs[s]) return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: null source");
+    if (x_devs && x_devs[s])
+      for (int k = 0; k < n; ++k)
+        if (!x_devs[s][k]) return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: null x_k pointer");
+    for (int t = 0; t < s; ++t)
+      if (b_devs[t] == b_devs[s] || (y_devs && y_devs[s] && y_devs[t] == y_devs[s]))
+        return fail(ctx, LQCD_ERR_ARG, "mshift_cg_multi: right-hand sides share a buffer");
+  }
+  if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "mshift_cg_multi: no gauge field loaded");
+  return run_mshift_multi(ctx, nrhs, shifts, residues, n, c0, b_devs, x_devs, y_devs, tol, maxiter, prec, stats);
+}
+
 long long lqcd_launch_count(const lqcd_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 }  // extern "C"

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __
 // solve, without a ticket, the sum stays as per-block (hi, lo) partials for the r update);
 // EPI 2: r_out = fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
 template <int EPI>
-__global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, DfArgs k) {
+__global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_constant__ PerSys<DfArgs> pk) {
+  const DfArgs& k = pk.s[blockIdx.y];  // system blockIdx.y
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < vh;
@@ -192,11 +193,17 @@ cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2*
 
 int df_dslash_grid_blocks(const Geom& g) { return (g.vh + 127) / 128; }
 
+cudaError_t launch_df_dslash_multi(const Geom& g, const PerSys<DfArgs>& a, int S, int epi, cudaStream_t st, bool pdl) {
+  const dim3 grid((unsigned)df_dslash_grid_blocks(g), (unsigned)S);
+  if (epi == 2) return launch_k(pdl, df_dslash_kernel<2>, grid, dim3(128), st, g, a);
+  if (epi == 1) return launch_k(pdl, df_dslash_kernel<1>, grid, dim3(128), st, g, a);
+  return launch_k(pdl, df_dslash_kernel<0>, grid, dim3(128), st, g, a);
+}
+
 cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl) {
-  const unsigned nb = (unsigned)df_dslash_grid_blocks(g);
-  if (epi == 2) return launch_k(pdl, df_dslash_kernel<2>, dim3(nb), dim3(128), st, g, a);
-  if (epi == 1) return launch_k(pdl, df_dslash_kernel<1>, dim3(nb), dim3(128), st, g, a);
-  return launch_k(pdl, df_dslash_kernel<0>, dim3(nb), dim3(128), st, g, a);
+  PerSys<DfArgs> p;
+  p.s[0] = a;
+  return launch_df_dslash_multi(g, p, 1, epi, st, pdl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -230,7 +237,8 @@ __global__ void __launch_bounds__(256) df_init_kernel(Geom g, const double2* __r
 
 // r -= alpha q; R[m] = r; (hi, lo) partials of |r|^2.  alpha comes from the A-apply's partials
 // (every block, the same bits); one extra block runs the alpha step.
-__global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, DfUpdArgs a) {
+__global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __grid_constant__ PerSys<DfUpdArgs> args) {
+  const DfUpdArgs& a = args.s[blockIdx.y];  // system blockIdx.y
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
@@ -273,7 +281,8 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, DfUpdArgs a
 
 // p = r + beta p, one site per thread; beta from the r update's partials; one extra block runs
 // the beta step.
-__global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, DfUpdArgs a) {
+__global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, const __grid_constant__ PerSys<DfUpdArgs> args) {
+  const DfUpdArgs& a = args.s[blockIdx.y];  // system blockIdx.y
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
@@ -305,7 +314,8 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, DfUpdArgs a
 // The pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i, all in
 // double-FP32 (the window coefficients split from FP64 once per block).  One colour at a time
 // keeps the window's residuals (2 x kWindow float2 pairs) in registers.
-__global__ void __launch_bounds__(128) df_flush_kernel(Geom g, DfFlushArgs a) {
+__global__ void __launch_bounds__(128) df_flush_kernel(Geom g, const __grid_constant__ PerSys<DfFlushArgs> pa) {
+  const DfFlushArgs& a = pa.s[blockIdx.y];  // system blockIdx.y
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
@@ -415,17 +425,17 @@ cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, 
   return cudaGetLastError();
 }
 
-// the update kernels: one block per 256 sites plus the scalar block
-cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(pdl, df_r_update_kernel, dim3((g.vh + 255) / 256 + 1), dim3(256), st, g, a);
+// the update kernels: one block per 256 sites plus the scalar block, per system
+cudaError_t launch_df_r_update(const Geom& g, const PerSys<DfUpdArgs>& a, int S, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_r_update_kernel, dim3((g.vh + 255) / 256 + 1, S), dim3(256), st, g, a);
 }
 
-cudaError_t launch_df_p_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(pdl, df_p_update_kernel, dim3((g.vh + 255) / 256 + 1), dim3(256), st, g, a);
+cudaError_t launch_df_p_update(const Geom& g, const PerSys<DfUpdArgs>& a, int S, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_p_update_kernel, dim3((g.vh + 255) / 256 + 1, S), dim3(256), st, g, a);
 }
 
-cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl) {
-  return launch_k(pdl, df_flush_kernel, dim3((g.vh + 127) / 128), dim3(128), st, g, a);
+cudaError_t launch_df_flush(const Geom& g, const PerSys<DfFlushArgs>& a, int S, cudaStream_t st, bool pdl) {
+  return launch_k(pdl, df_flush_kernel, dim3((g.vh + 127) / 128, S), dim3(128), st, g, a);
 }
 
 cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st) {

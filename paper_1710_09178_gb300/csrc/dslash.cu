@@ -10,6 +10,8 @@
 // TPS threads cooperate on one site, each taking 8/TPS of the hops, and combine
 // their partial sums with warp shuffles; more threads per site means more
 // independent loads in flight per SM.
+#include <string.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -267,6 +269,64 @@ __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   dslash_epilogue<T, V2, TPS, EPI>(k, d, i, sub, valid, vh);
 }
 
+// The half-lattice hop of NS systems that share one operator (the right-hand sides of a multi-RHS
+// shifted solve): every link is loaded and decoded once and applied to the NS input vectors, so the
+// link traffic per system drops by NS.  One thread per output site; per system the arithmetic (the
+// hop order, the forward and backward accumulators) and the epilogue are those of dslash_kernel with
+// one thread per site, so every system's output and partial sums equal its own launch's bit for bit.
+template <int LF, int NS, int EPI>
+__global__ void __launch_bounds__(128, NS <= 2 ? 4 : 3) dslash_msys_kernel(Geom g,
+                                                                          const __grid_constant__ PerSys<KArgs> pk) {
+  typedef typename LinkTraits<LF>::T T;
+  typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
+  const int vh = g.vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < vh;
+  const int p = pk.s[0].out_parity;
+  const void* links = pk.s[0].links;
+  const uint64_t pol = link_policy<LF>();
+  SiteHops<LF, 1> hops;
+  if (valid) hops.start(g, links, p, i, 0, pol);
+  pdl_wait();
+  pdl_trigger();
+  bool all_done = true;  // uniform: the flags only change between kernels
+#pragma unroll
+  for (int s = 0; s < NS; ++s) all_done = all_done && pk.s[s].done && *pk.s[s].done;
+  if (all_done) return;
+
+  Vec3<T> accf[NS], accb[NS], vn[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) accf[s] = accb[s] = vzero<T>();
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) vn[s] = ldg_vec(static_cast<const V2*>(pk.s[s].in), hops.nb[0], vh);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const Mat3<T> W = decode<LF>(hops.Wn, hops.sg[q]);
+      Vec3<T> v[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) v[s] = vn[s];
+      if (q + 1 < 8) {
+        hops.Wn = hops.link(links, p, i, 0, q + 1, vh, pol);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) vn[s] = ldg_vec(static_cast<const V2*>(pk.s[s].in), hops.nb[q + 1], vh);
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((q & 1) == 0) mv_acc(accf[s], W, v[s]);
+        else mdv_acc(accb[s], W, v[s]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    Vec3<T> d;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.c[c] = cmake(accf[s].c[c].re - accb[s].c[c].re, accf[s].c[c].im - accb[s].c[c].im);
+    dslash_epilogue<T, V2, 1, EPI>(pk.s[s], d, i, 0, valid, vh);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Batched half-Dslash over many lattices of different sizes in one persistent launch.  The work
 // is split into items of kBatchChunk output sites of one lattice (chunk_end holds the prefix
@@ -447,6 +507,66 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
     case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, st, a.pdl);
     case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, st, a.pdl);
     default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st, a.pdl);
+  }
+}
+
+template <int LF, int NS>
+static cudaError_t launch_msys_ns(const Geom& g, const PerSys<KArgs>& k, Epi epi, cudaStream_t st, bool pdl) {
+  const dim3 grid((unsigned)((g.vh + 127) / 128));
+  switch (epi) {
+    case Epi::Plain: return launch_k(pdl, dslash_msys_kernel<LF, NS, 0>, grid, dim3(128), st, g, k);
+    case Epi::AApply: return launch_k(pdl, dslash_msys_kernel<LF, NS, 1>, grid, dim3(128), st, g, k);
+    default: return launch_k(pdl, dslash_msys_kernel<LF, NS, 2>, grid, dim3(128), st, g, k);
+  }
+}
+
+template <int LF>
+static cudaError_t launch_msys_lf(const Geom& g, const PerSys<KArgs>& k, int S, Epi epi, cudaStream_t st, bool pdl) {
+  switch (S) {
+    case 2: return launch_msys_ns<LF, 2>(g, k, epi, st, pdl);
+    case 3: return launch_msys_ns<LF, 3>(g, k, epi, st, pdl);
+    default: return launch_msys_ns<LF, 4>(g, k, epi, st, pdl);
+  }
+}
+
+cudaError_t launch_dslash_msys(const Geom& g, const GaugeCopies& gc, const PerSys<DslashArgs>& a, int S,
+                               cudaStream_t st, int* nlaunch) {
+  if (S < 2 || S > kMaxRhs) return cudaErrorInvalidValue;
+  const DslashArgs& a0 = a.s[0];
+  PerSys<KArgs> k;
+  memset(&k, 0, sizeof(k));
+  const void* links = nullptr;
+  switch (a0.prec) {
+    case LQCD_FP32: links = gc.u32; break;
+    case LQCD_FP32_R12: links = gc.u12; break;
+    case LQCD_FP32_R8: links = gc.u8; break;
+    case LQCD_FP32_L16: links = gc.u16; break;
+    default: return cudaErrorInvalidValue;  // the FP32 Krylov modes only
+  }
+  for (int s = 0; s < S; ++s) {
+    const DslashArgs& x = a.s[s];
+    if (x.prec != a0.prec || x.epi != a0.epi || x.out_parity != a0.out_parity) return cudaErrorInvalidValue;
+    KArgs& y = k.s[s];
+    y.out = x.out;
+    y.in = x.in;
+    y.aux = x.aux;
+    y.bvec = x.bvec;
+    y.a = x.a;
+    y.a_dev = x.a_dev;
+    y.a_devf = x.a_devf;
+    y.out_parity = x.out_parity;
+    y.dot_out = x.dot_out;
+    y.done = x.done;
+    y.partials = x.partials;
+    y.ticket = x.ticket;
+    y.links = links;
+  }
+  if (nlaunch) *nlaunch += 1;
+  switch (a0.prec) {
+    case LQCD_FP32_R12: return launch_msys_lf<kL12>(g, k, S, a0.epi, st, a0.pdl);
+    case LQCD_FP32_R8: return launch_msys_lf<kL8>(g, k, S, a0.epi, st, a0.pdl);
+    case LQCD_FP32_L16: return launch_msys_lf<kL16>(g, k, S, a0.epi, st, a0.pdl);
+    default: return launch_msys_lf<kL32>(g, k, S, a0.epi, st, a0.pdl);
   }
 }
 

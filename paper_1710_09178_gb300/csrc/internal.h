@@ -21,6 +21,15 @@ __host__ __device__ inline bool vec_fp32(int prec) {
 }
 constexpr int kWindow = 10;  // iterations folded into one update of x_k, p_k
 
+// Right-hand sides of one multi-RHS shifted solve (mshift_cg_multi): the kernels of the solve take
+// the arguments of every system at once and run system blockIdx.y; the systems share the link loads
+// of the FP32 Dslash.
+constexpr int kMaxRhs = LQCD_MAX_RHS;
+template <typename A>
+struct PerSys {
+  A s[kMaxRhs];
+};
+
 struct SolverDev {
   double rr;       // |r|^2 of the current base residual
   double rr_b;     // copy of rr taken by the alpha step: the p-update kernel forms beta from it while
@@ -106,6 +115,7 @@ struct lqcd_ctx {
   int df_resid = 1;        // mixed modes: residuals in double-FP32 instead of FP64
   int dslash_tps = 0;
   lqcd::Workspace* ws = nullptr;
+  lqcd::Workspace* ws_extra[lqcd::kMaxRhs - 1] = {};  // systems 1 .. of multi-RHS solves (mshift_cg_multi)
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
   void* force_ws = nullptr;             // fermion-force buffers (force.cu)
   void* traj_ws = nullptr;              // trajectory buffers (trajectory.cu)
@@ -152,6 +162,10 @@ struct DslashArgs {
   bool pdl = false;              // programmatic dependent launch (inside captured solve graphs)
 };
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch);
+// the same hop on 2..kMaxRhs systems sharing the operator, each link loaded once (FP32 Krylov modes, one
+// thread per site): per system the results of launch_dslash with tps = 1, bit for bit
+cudaError_t launch_dslash_msys(const Geom& g, const GaugeCopies& gc, const PerSys<DslashArgs>& a, int S,
+                               cudaStream_t st, int* nlaunch);
 
 // dslash.cu: the batched half-Dslash (dslash_eo_batch).  All lattices of a call run in one
 // persistent launch whose descriptors (BatchTable) sit in device memory: each distinct set of
@@ -238,17 +252,21 @@ cudaError_t launch_split_df(const Geom& g, const double2* x, float2* hi, float2*
                             bool pdl);
 // epi: 0 plain, 1 A-apply (q = a x - D in, Re<x, q>), 2 residual
 cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl);
+cudaError_t launch_df_dslash_multi(const Geom& g, const PerSys<DfArgs>& a, int S, int epi, cudaStream_t st, bool pdl);
 cudaError_t launch_df_init(const Geom& g, const double2* b64, void* r, void* p, SolverDev* sd, const InitParams& ip,
                            double* partials, unsigned* ticket, cudaStream_t st);
-cudaError_t launch_df_r_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl);
-cudaError_t launch_df_p_update(const Geom& g, const DfUpdArgs& a, cudaStream_t st, bool pdl);
+cudaError_t launch_df_r_update(const Geom& g, const PerSys<DfUpdArgs>& a, int S, cudaStream_t st, bool pdl);
+cudaError_t launch_df_p_update(const Geom& g, const PerSys<DfUpdArgs>& a, int S, cudaStream_t st, bool pdl);
 int df_dslash_grid_blocks(const Geom& g);  // blocks (= partials) of one double-FP32 Dslash launch
-cudaError_t launch_df_flush(const Geom& g, const DfFlushArgs& a, cudaStream_t st, bool pdl);
+cudaError_t launch_df_flush(const Geom& g, const PerSys<DfFlushArgs>& a, int S, cudaStream_t st, bool pdl);
 cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st);
 
 // solver.cu
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
                double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats);
+int run_mshift_multi(lqcd_ctx* ctx, int S, const double* shifts, const double* residues, int n, double c0,
+                     const double* const* b_devs, double* const* const* x_devs, double* const* y_devs, double tol,
+                     int maxiter, int prec, lqcd_solve_stats* stats);
 void free_workspace(lqcd_ctx* ctx);
 // FP64 internal solutions x_k of the last mshift_cg call on this context, and its stream
 double2* const* workspace_solutions(lqcd_ctx* ctx);

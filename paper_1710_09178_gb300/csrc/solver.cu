@@ -126,8 +126,9 @@ __device__ __forceinline__ bool done_now(const SolverDev* sd) {
 
 // r -= alpha q; R[m] = r; |r|^2 partials.  Scalar block: the alpha step.
 template <typename T, int SF>
-__global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, RUpdArgs a) {
+__global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, const __grid_constant__ PerSys<RUpdArgs> args) {
   typedef typename KTraits<T>::V2 V2;
+  const RUpdArgs& a = args.s[blockIdx.y];  // system blockIdx.y
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
@@ -174,8 +175,9 @@ struct PUpdArgs {
 // p = r + beta p, one site per thread.  Scalar block: the beta step (stopping tests, window
 // coefficients, reliable-update decision, done flag).
 template <typename T>
-__global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, PUpdArgs a) {
+__global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, const __grid_constant__ PerSys<PUpdArgs> pa) {
   typedef typename KTraits<T>::V2 V2;
+  const PUpdArgs& a = pa.s[blockIdx.y];  // system blockIdx.y
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
@@ -218,7 +220,8 @@ struct FlushArgs {
 // Apply the pending window: p_k = P p_k0 + sum_i pi_i R_i;  x_k += X p_k0 + sum_i chi_i R_i.
 // At the first window of a solve p_k0 = b and x_k0 = 0 (nothing is read).
 template <typename T, int SF, bool XDF>
-__global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
+__global__ void __launch_bounds__(128) flush_kernel(Geom g, const __grid_constant__ PerSys<FlushArgs> pa) {
+  const FlushArgs& a = pa.s[blockIdx.y];  // system blockIdx.y
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
@@ -319,10 +322,10 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, FlushArgs a) {
 }
 
 // Per-shift recurrences of the pending window (one warp), right before the window update.
-__global__ void window_scalars_kernel(SolverDev* sd) {
+__global__ void window_scalars_kernel(const __grid_constant__ PerSys<SolverDev*> sds) {
   pdl_wait();
   pdl_trigger();
-  window_scalars(sd);
+  window_scalars(sds.s[blockIdx.y]);  // one block of 32 per system
 }
 
 // Precision schedule of the mixed modes.  The error that FP32 arithmetic (links, Krylov vectors)
@@ -336,15 +339,27 @@ __global__ void window_scalars_kernel(SolverDev* sd) {
 //
 // End of every window of the double-FP32 phase: the phase ends once |r|^2 <= switch2 (or the solve
 // is done, or the window budget is spent); in a captured graph this ends the phase's while loop.
-__global__ void loop_ctl_df_kernel(cudaGraphConditionalHandle handle, SolverDev* sd, int set_cond) {
+__global__ void loop_ctl_df_kernel(cudaGraphConditionalHandle handle, const __grid_constant__ PerSys<SolverDev*> sds,
+                                   int S, int set_cond) {
   if (threadIdx.x != 0) return;
-  if (!sd->halt1) {
-    const int wr = sd->windows_run + 1;
-    sd->windows_run = wr;
-    sd->windows_df += 1;
-    if (sd->done || sd->rr <= sd->switch2 || wr >= sd->max_windows) sd->halt1 = 1;
+  // a window ran while any system was still in the phase (the systems run in lock step); each system
+  // ends its own phase, the loop ends with the last
+  bool any = false;
+  for (int y = 0; y < S; ++y) any = any || !sds.s[y]->halt1;
+  unsigned running = 0u;
+  if (any) {
+    const int wr = sds.s[0]->windows_run + 1;
+    for (int y = 0; y < S; ++y) {
+      SolverDev* sd = sds.s[y];
+      sd->windows_run = wr;
+      if (!sd->halt1) {
+        sd->windows_df += 1;
+        if (sd->done || sd->rr <= sd->switch2 || wr >= sd->max_windows) sd->halt1 = 1;
+      }
+      running |= sd->halt1 ? 0u : 1u;
+    }
   }
-  if (set_cond) cudaGraphSetConditional(handle, sd->halt1 ? 0u : 1u);
+  if (set_cond) cudaGraphSetConditional(handle, running);
 }
 
 struct DemoteArgs {
@@ -361,7 +376,8 @@ struct DemoteArgs {
 // The change of phase, once (after the window that ended the double-FP32 phase): r, p and the active
 // shifts' p_k to the FP32 phase's storage, each the (hi, lo) pair rounded to FP32 (its hi part).
 template <int SF>
-__global__ void __launch_bounds__(256) demote_kernel(Geom g, DemoteArgs a) {
+__global__ void __launch_bounds__(256) demote_kernel(Geom g, const __grid_constant__ PerSys<DemoteArgs> pa) {
+  const DemoteArgs& a = pa.s[blockIdx.y];  // system blockIdx.y
   pdl_wait();
   pdl_trigger();
   const SolverDev* sd = a.sd;
@@ -376,8 +392,9 @@ __global__ void __launch_bounds__(256) demote_kernel(Geom g, DemoteArgs a) {
 }
 
 // after demote_kernel: mark the change done and start the reliable-update bookkeeping of the FP32 phase
-__global__ void demoted_kernel(SolverDev* sd) {
+__global__ void demoted_kernel(const __grid_constant__ PerSys<SolverDev*> sds) {
   if (threadIdx.x != 0) return;
+  SolverDev* sd = sds.s[blockIdx.y];
   if (sd->halt1 && !sd->demoted) {
     sd->demoted = 1;
     sd->iter_ru = sd->iter;
@@ -405,9 +422,12 @@ __global__ void ru_finish_kernel(Geom g, const double2* __restrict__ r64, void* 
 }
 
 // bookkeeping of a reliable update, one thread, after ru_finish_kernel
-__global__ void ru_close_kernel(SolverDev* sd, int* ru_count) {
+__global__ void ru_close_kernel(const __grid_constant__ PerSys<SolverDev*> sds, const __grid_constant__ PerSys<int*> counts) {
   pdl_wait();
   pdl_trigger();
+  if (threadIdx.x != 0) return;
+  SolverDev* sd = sds.s[blockIdx.y];
+  int* ru_count = counts.s[blockIdx.y];
   if (sd->ru_skip) return;
   double rr = sd->scal[0];
   if (!isfinite(rr)) {
@@ -423,11 +443,15 @@ __global__ void ru_close_kernel(SolverDev* sd, int* ru_count) {
 
 // End of a window inside the graph's while loop: continue while the solve is running.  The
 // window counter bounds the loop by itself, whatever state the other kernels left.
-__global__ void loop_ctl_kernel(cudaGraphConditionalHandle handle, SolverDev* sd) {
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle handle, const __grid_constant__ PerSys<SolverDev*> sds, int S) {
   if (threadIdx.x != 0) return;
-  int wr = sd->windows_run + 1;
-  sd->windows_run = wr;
-  unsigned cont = (!sd->done && wr < sd->max_windows) ? 1u : 0u;
+  const int wr = sds.s[0]->windows_run + 1;
+  unsigned cont = 0u;
+  for (int y = 0; y < S; ++y) {
+    SolverDev* sd = sds.s[y];
+    sd->windows_run = wr;
+    if (!sd->done && wr < sd->max_windows) cont = 1u;
+  }
   cudaGraphSetConditional(handle, cont);
 }
 
@@ -482,6 +506,7 @@ struct StatusWords {
 struct Workspace {
   int prec = -1;
   int n_cap = 0;
+  bool owns_stream = true;  // false for systems 1 .. S-1 of a multi-RHS solve (system 0's stream)
   int kprec = LQCD_FP32;  // Krylov vector precision (FP64 or FP32)
   int sfmt = kS32;        // shift-vector storage format
   size_t kbytes = 0, sbytes = 0, dbytes = 0;
@@ -532,8 +557,7 @@ static size_t vec_bytes(long long vh, int prec) {
 double2* const* workspace_solutions(lqcd_ctx* ctx) { return ctx->ws ? ctx->ws->xk : nullptr; }
 cudaStream_t workspace_stream(lqcd_ctx* ctx) { return ctx->ws ? ctx->ws->st : nullptr; }
 
-void free_workspace(lqcd_ctx* ctx) {
-  Workspace* w = ctx->ws;
+static void destroy_workspace(Workspace* w) {
   if (!w) return;
   for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
   void* bufs[] = {w->dfx_h, w->dfx_l, w->dft_h, w->dft_l, w->dfb_h, w->dfb_l,
@@ -552,8 +576,16 @@ void free_workspace(lqcd_ctx* ctx) {
   cudaEvent_t evs[] = {w->ev_in, w->ev_out, w->ev_t0, w->ev_t1, w->ev_batch[0], w->ev_batch[1]};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
-  if (w->st) cudaStreamDestroy(w->st);
+  if (w->st && w->owns_stream) cudaStreamDestroy(w->st);
   delete w;
+}
+
+void free_workspace(lqcd_ctx* ctx) {
+  for (int s = 0; s < kMaxRhs - 1; ++s) {
+    destroy_workspace(ctx->ws_extra[s]);
+    ctx->ws_extra[s] = nullptr;
+  }
+  destroy_workspace(ctx->ws);
   ctx->ws = nullptr;
 }
 
@@ -563,12 +595,11 @@ void free_workspace(lqcd_ctx* ctx) {
     if (_e != cudaSuccess) return cuda_check(ctx, _e, #call);    \
   } while (0)
 
-static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
-  Workspace* w = ctx->ws;
-  if (w && w->prec == prec && w->n_cap >= n) return LQCD_OK;
-  free_workspace(ctx);
-  w = new Workspace();
-  ctx->ws = w;
+// The buffers of one shifted-CG system (shared_st: run on that stream, e.g. system 0's, instead of
+// a stream of its own).  On failure *slot holds what was allocated so far (freed with the context).
+static int alloc_workspace(lqcd_ctx* ctx, int prec, int n, Workspace** slot, cudaStream_t shared_st) {
+  Workspace* w = new Workspace();
+  *slot = w;
   w->prec = prec;
   w->n_cap = n;
   w->kprec = (prec == LQCD_FP64 || prec == LQCD_DF64) ? prec : LQCD_FP32;
@@ -577,7 +608,12 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   w->kbytes = vec_bytes(vh, w->kprec);
   w->sbytes = vec_bytes(vh, (prec == LQCD_FP64 || prec == LQCD_DF64 || prec == LQCD_FP16FIX) ? prec : LQCD_FP32);
   w->dbytes = vec_bytes(vh, LQCD_FP64);
-  LQ_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+  if (shared_st) {
+    w->st = shared_st;
+    w->owns_stream = false;
+  } else {
+    LQ_CUDA(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+  }
   LQ_CUDA(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
   LQ_CUDA(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
   LQ_CUDA(cudaEventCreate(&w->ev_t0));
@@ -630,13 +666,43 @@ static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
   return LQCD_OK;
 }
 
+static int ensure_workspace(lqcd_ctx* ctx, int prec, int n) {
+  Workspace* w = ctx->ws;
+  if (w && w->prec == prec && w->n_cap >= n) return LQCD_OK;
+  free_workspace(ctx);
+  return alloc_workspace(ctx, prec, n, &ctx->ws, nullptr);
+}
+
+// system 0 (ctx->ws) and systems 1 .. S-1 (ctx->ws_extra, on system 0's stream); graphs captured with
+// the old buffers of systems 1 .. S-1 are dropped when those change
+static int ensure_workspaces(lqcd_ctx* ctx, int prec, int n, int S) {
+  int rc = ensure_workspace(ctx, prec, n);
+  if (rc != LQCD_OK) return rc;
+  for (int s = 1; s < S; ++s) {
+    Workspace*& e = ctx->ws_extra[s - 1];
+    if (e && e->prec == prec && e->n_cap >= n) continue;
+    destroy_workspace(e);
+    e = nullptr;
+    for (auto& kv : ctx->ws->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->ws->graphs.clear();
+    ctx->ws->graph_nodes.clear();
+    ctx->ws->graph_nodes_df.clear();
+    rc = alloc_workspace(ctx, prec, n, &e, ctx->ws->st);
+    if (rc != LQCD_OK) return rc;
+  }
+  return LQCD_OK;
+}
+
 struct Launcher {
   lqcd_ctx* ctx;
-  Workspace* w;
+  Workspace* w;  // system 0: the stream and the graph caches
   Geom g;
   int nlaunch = 0;
   bool pdl = false;      // launch with programmatic dependencies (captured graph bodies)
   bool chained = false;  // a kernel of this launcher precedes the next one in the stream
+  int S = 1;                      // systems of a multi-RHS solve (right-hand sides sharing the operator)
+  Workspace* more[kMaxRhs] = {};  // systems 1 .. S-1 (they share system 0's stream)
+  Workspace* sys(int s) const { return s == 0 ? w : more[s]; }
   // PDL for every kernel but the first of a captured body, whose predecessor is not ours
   bool next_pdl() {
     bool r = pdl && chained;
@@ -644,6 +710,19 @@ struct Launcher {
     return r;
   }
 };
+
+static PerSys<SolverDev*> solver_states(const Launcher& L) {
+  PerSys<SolverDev*> p;
+  memset(&p, 0, sizeof(p));
+  for (int s = 0; s < L.S; ++s) p.s[s] = L.sys(s)->sd;
+  return p;
+}
+
+// the solutions during the solve: (hi, lo) FP32 pairs (every mode but LQCD_FP64 with double-FP32
+// residuals) or FP64
+static double2* const* run_solutions(Workspace* w) {
+  return w->xdfmode ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
+}
 
 // the (hi, lo) vectors a double-FP32 iteration and window work on: those of the LQCD_DF64 solve,
 // or the double-FP32 phase of a mixed solve's precision schedule
@@ -655,68 +734,87 @@ struct DfBufs {
 };
 
 static DfBufs df_bufs(Workspace* w, bool phase) {
-  if (phase) return DfBufs{w->dr, w->dp, w->dq, w->dtmp, w->dring, w->dbytes, w->dpk,
-                           &w->sd->halt1};
+  if (phase) return DfBufs{w->dr, w->dp, w->dq, w->dtmp, w->dring, w->dbytes, w->dpk, &w->sd->halt1};
   return DfBufs{w->r, w->p, w->q, w->tmp, w->ring, w->sbytes, w->pk, nullptr};
 }
 
 // the four kernels of one base iteration
-static cudaError_t enqueue_iteration_df(Launcher& L, const DfBufs& B);
+static cudaError_t enqueue_iteration_df(Launcher& L, bool phase);
 
 static cudaError_t enqueue_iteration(Launcher& L) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
   cudaStream_t st = w->st;
-  const int* done = &w->sd->done;
-  if (w->kprec == LQCD_DF64) return enqueue_iteration_df(L, df_bufs(w, false));
-  DslashArgs d1;
-  d1.out = w->tmp;
-  d1.in = w->p;
-  d1.out_parity = 1;
-  d1.prec = w->prec == LQCD_FP16FIX ? LQCD_FP32 : w->prec;
-  d1.tps = ctx->dslash_tps;
-  d1.done = done;
-  d1.pdl = L.next_pdl();
-  cudaError_t e = launch_dslash(L.g, ctx->gauge, d1, st, &L.nlaunch);
-  if (e != cudaSuccess) return e;
-  DslashArgs d2 = d1;
-  d2.pdl = L.next_pdl();
-  d2.out = w->q;
-  d2.in = w->tmp;
-  d2.out_parity = 0;
-  d2.epi = Epi::AApply;
-  d2.aux = w->p;
-  d2.a_dev = &w->sd->a_diag;  // 4 m^2 + sigma_0 of the running solve
-  d2.a_devf = &w->sd->a_diag_f;
-  d2.partials = w->partials;  // no ticket: the r update sums the partials and runs the alpha step
-  e = launch_dslash(L.g, ctx->gauge, d2, st, &L.nlaunch);
-  if (e != cudaSuccess) return e;
+  if (w->kprec == LQCD_DF64) return enqueue_iteration_df(L, false);
+  const int S = L.S;
+  PerSys<DslashArgs> d1, d2;
+  PerSys<RUpdArgs> ra;
+  PerSys<PUpdArgs> pa;
+  memset(&ra, 0, sizeof(ra));
+  memset(&pa, 0, sizeof(pa));
+  const int dprec = w->prec == LQCD_FP16FIX ? LQCD_FP32 : w->prec;
+  const int tps = S == 1 ? ctx->dslash_tps : 1;  // the multi-system Dslash runs one thread per site
   const int nb = (L.g.vh + 255) / 256;  // streaming blocks; one more runs the scalar step
-  RUpdArgs ra;
-  ra.r = w->r;
-  ra.q = w->q;
-  ra.ring = w->ring;
-  ra.slot_bytes = w->sbytes;
-  ra.sd = w->sd;
-  ra.pq_partials = w->partials;
-  ra.n_pq = dslash_grid_blocks(L.g, d2.prec, d2.tps);
-  ra.rr_partials = w->partials_b;
-  PUpdArgs pa;
-  pa.r = w->r;
-  pa.p = w->p;
-  pa.sd = w->sd;
-  pa.rr_partials = w->partials_b;
-  pa.n_rr = nb;
-  const bool pr = L.next_pdl(), pp = L.next_pdl();
-  if (w->kprec == LQCD_FP64) {
-    e = launch_k(pr, r_update_kernel<double, kS64>, dim3(nb + 1), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, dim3(nb + 1), dim3(256), st, L.g, pa);
-  } else if (w->sfmt == kS16) {
-    e = launch_k(pr, r_update_kernel<float, kS16>, dim3(nb + 1), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb + 1), dim3(256), st, L.g, pa);
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    DslashArgs& a = d1.s[s];
+    a.out = y->tmp;
+    a.in = y->p;
+    a.out_parity = 1;
+    a.prec = dprec;
+    a.tps = tps;
+    a.done = &y->sd->done;
+    DslashArgs& b = d2.s[s];
+    b = a;
+    b.out = y->q;
+    b.in = y->tmp;
+    b.out_parity = 0;
+    b.epi = Epi::AApply;
+    b.aux = y->p;
+    b.a_dev = &y->sd->a_diag;  // 4 m^2 + sigma_0 of the running solve
+    b.a_devf = &y->sd->a_diag_f;
+    b.partials = y->partials;  // no ticket: the r update sums the partials and runs the alpha step
+    RUpdArgs& r = ra.s[s];
+    r.r = y->r;
+    r.q = y->q;
+    r.ring = y->ring;
+    r.slot_bytes = y->sbytes;
+    r.sd = y->sd;
+    r.pq_partials = y->partials;
+    r.n_pq = dslash_grid_blocks(L.g, dprec, tps);
+    r.rr_partials = y->partials_b;
+    PUpdArgs& u = pa.s[s];
+    u.r = y->r;
+    u.p = y->p;
+    u.sd = y->sd;
+    u.rr_partials = y->partials_b;
+    u.n_rr = nb;
+  }
+  cudaError_t e;
+  const bool p1 = L.next_pdl(), p2 = L.next_pdl();
+  for (int s = 0; s < S; ++s) {
+    d1.s[s].pdl = p1;
+    d2.s[s].pdl = p2;
+  }
+  if (S == 1) {
+    e = launch_dslash(L.g, ctx->gauge, d1.s[0], st, &L.nlaunch);
+    if (e == cudaSuccess) e = launch_dslash(L.g, ctx->gauge, d2.s[0], st, &L.nlaunch);
   } else {
-    e = launch_k(pr, r_update_kernel<float, kS32>, dim3(nb + 1), dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, dim3(nb + 1), dim3(256), st, L.g, pa);
+    e = launch_dslash_msys(L.g, ctx->gauge, d1, S, st, &L.nlaunch);
+    if (e == cudaSuccess) e = launch_dslash_msys(L.g, ctx->gauge, d2, S, st, &L.nlaunch);
+  }
+  if (e != cudaSuccess) return e;
+  const bool pr = L.next_pdl(), pp = L.next_pdl();
+  const dim3 grid(nb + 1, S);
+  if (w->kprec == LQCD_FP64) {
+    e = launch_k(pr, r_update_kernel<double, kS64>, grid, dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, grid, dim3(256), st, L.g, pa);
+  } else if (w->sfmt == kS16) {
+    e = launch_k(pr, r_update_kernel<float, kS16>, grid, dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, grid, dim3(256), st, L.g, pa);
+  } else {
+    e = launch_k(pr, r_update_kernel<float, kS32>, grid, dim3(256), st, L.g, ra);
+    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, grid, dim3(256), st, L.g, pa);
   }
   L.nlaunch += 2;
   return e;
@@ -724,109 +822,130 @@ static cudaError_t enqueue_iteration(Launcher& L) {
 
 // the four kernels of one base iteration of the double-FP32 solve (LQCD_DF64, or the double-FP32
 // phase of a mixed solve)
-static cudaError_t enqueue_iteration_df(Launcher& L, const DfBufs& B) {
+static cudaError_t enqueue_iteration_df(Launcher& L, bool phase) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
   cudaStream_t st = w->st;
+  const int S = L.S;
   const size_t n3 = 3 * (size_t)L.g.vh;
   auto hi = [](void* v) { return static_cast<float2*>(v); };
   auto lo = [n3](void* v) { return static_cast<float2*>(v) + n3; };
-  DfArgs d;
-  d.links_hi = ctx->gauge.u32;
-  d.links_lo = ctx->gauge.u32lo;
-  d.in_hi = hi(B.p);
-  d.in_lo = lo(B.p);
-  d.out_hi = hi(B.tmp);
-  d.out_lo = lo(B.tmp);
-  d.done = &w->sd->done;
-  d.halt = B.halt;
-  d.out_parity = 1;
-  cudaError_t e = launch_df_dslash(L.g, d, 0, st, L.next_pdl());
+  PerSys<DfArgs> d, a;
+  PerSys<DfUpdArgs> u;
+  memset(&u, 0, sizeof(u));
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    const DfBufs B = df_bufs(y, phase);
+    DfArgs& x = d.s[s];
+    x.links_hi = ctx->gauge.u32;
+    x.links_lo = ctx->gauge.u32lo;
+    x.in_hi = hi(B.p);
+    x.in_lo = lo(B.p);
+    x.out_hi = hi(B.tmp);
+    x.out_lo = lo(B.tmp);
+    x.done = &y->sd->done;
+    x.halt = B.halt;
+    x.out_parity = 1;
+    DfArgs& z = a.s[s];
+    z = x;
+    z.in_hi = hi(B.tmp);
+    z.in_lo = lo(B.tmp);
+    z.out_hi = hi(B.q);
+    z.out_lo = lo(B.q);
+    z.x_hi = hi(B.p);
+    z.x_lo = lo(B.p);
+    z.a_dev = &y->sd->a_diag;
+    z.a_devdf = &y->sd->a_diag_df;
+    z.partials = y->partials;  // no ticket: the r update sums the partials and runs the alpha step
+    z.out_parity = 0;
+    DfUpdArgs& v = u.s[s];
+    v.r = hi(B.r);
+    v.q = hi(B.q);
+    v.p = hi(B.p);
+    v.ring = B.ring;
+    v.slot_bytes = B.slot_bytes;
+    v.sd = y->sd;
+    v.pq_partials = y->partials;
+    v.n_pq = df_dslash_grid_blocks(L.g);
+    v.rr_partials = y->partials_b;
+    v.halt = B.halt;
+  }
+  cudaError_t e = launch_df_dslash_multi(L.g, d, S, 0, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  DfArgs a = d;
-  a.in_hi = hi(B.tmp);
-  a.in_lo = lo(B.tmp);
-  a.out_hi = hi(B.q);
-  a.out_lo = lo(B.q);
-  a.x_hi = hi(B.p);
-  a.x_lo = lo(B.p);
-  a.a_dev = &w->sd->a_diag;
-  a.a_devdf = &w->sd->a_diag_df;
-  a.partials = w->partials;  // no ticket: the r update sums the partials and runs the alpha step
-  a.out_parity = 0;
-  e = launch_df_dslash(L.g, a, 1, st, L.next_pdl());
+  e = launch_df_dslash_multi(L.g, a, S, 1, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  DfUpdArgs u;
-  u.r = hi(B.r);
-  u.q = hi(B.q);
-  u.p = hi(B.p);
-  u.ring = B.ring;
-  u.slot_bytes = B.slot_bytes;
-  u.sd = w->sd;
-  u.pq_partials = w->partials;
-  u.n_pq = df_dslash_grid_blocks(L.g);
-  u.rr_partials = w->partials_b;
-  u.halt = B.halt;
-  e = launch_df_r_update(L.g, u, st, L.next_pdl());
+  e = launch_df_r_update(L.g, u, S, st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  e = launch_df_p_update(L.g, u, st, L.next_pdl());
+  e = launch_df_p_update(L.g, u, S, st, L.next_pdl());
   L.nlaunch += 1;
   return e;
 }
 
 // the window end: per-shift recurrences, then the window update of every x_k, p_k (double-FP32 when
 // df_phase, i.e. in the first phase of the precision schedule)
-static cudaError_t enqueue_flush(Launcher& L, double2* const* xs, const double2* b64, int n, bool df_phase = false) {
+static cudaError_t enqueue_flush(Launcher& L, int n, bool df_phase = false) {
   Workspace* w = L.w;
-  cudaError_t e = launch_k(L.next_pdl(), window_scalars_kernel, dim3(1), dim3(32), w->st, w->sd);
+  const int S = L.S;
+  cudaError_t e =
+      launch_k(L.next_pdl(), window_scalars_kernel, dim3(1, S), dim3(32), w->st, solver_states(L));
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
   if (df_phase || w->sfmt == kSDF) {
-    const DfBufs B = df_bufs(w, df_phase);
-    DfFlushArgs df;
+    PerSys<DfFlushArgs> df;
     memset(&df, 0, sizeof(df));
-    df.ring = B.ring;
-    df.slot_bytes = B.slot_bytes;
-    for (int k = 0; k < n; ++k) {
-      df.pk[k] = static_cast<float2*>(B.pk[k]);
-      df.xk[k] = reinterpret_cast<float2*>(xs[k]);
+    for (int s = 0; s < S; ++s) {
+      Workspace* y = L.sys(s);
+      const DfBufs B = df_bufs(y, df_phase);
+      double2* const* xs = run_solutions(y);
+      DfFlushArgs& f = df.s[s];
+      f.ring = B.ring;
+      f.slot_bytes = B.slot_bytes;
+      for (int k = 0; k < n; ++k) {
+        f.pk[k] = static_cast<float2*>(B.pk[k]);
+        f.xk[k] = reinterpret_cast<float2*>(xs[k]);
+      }
+      f.b_hi = y->dfb_h;
+      f.b_lo = y->dfb_l;
+      f.sd = y->sd;
+      f.partials = y->partials;
+      f.ticket = y->tickets + 2;
     }
-    df.b_hi = w->dfb_h;
-    df.b_lo = w->dfb_l;
-    df.sd = w->sd;
-    df.partials = w->partials;
-    df.ticket = w->tickets + 2;
     L.nlaunch += 1;
-    return launch_df_flush(L.g, df, w->st, L.next_pdl());
+    return launch_df_flush(L.g, df, S, w->st, L.next_pdl());
   }
-  FlushArgs fa;
+  PerSys<FlushArgs> fa;
   memset(&fa, 0, sizeof(fa));
-  fa.ring = w->ring;
-  fa.slot_bytes = w->sbytes;
-  for (int k = 0; k < n; ++k) {
-    fa.pk[k] = w->pk[k];
-    fa.xk[k] = xs[k];
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    double2* const* xs = run_solutions(y);
+    FlushArgs& f = fa.s[s];
+    f.ring = y->ring;
+    f.slot_bytes = y->sbytes;
+    for (int k = 0; k < n; ++k) {
+      f.pk[k] = y->pk[k];
+      f.xk[k] = xs[k];
+    }
+    f.b64 = y->b64;
+    f.sd = y->sd;
+    f.partials = y->partials;
+    f.ticket = y->tickets + 2;
   }
-  fa.b64 = b64;
-  fa.sd = w->sd;
-  fa.partials = w->partials;
-  fa.ticket = w->tickets + 2;
-  int nb = (L.g.vh + 127) / 128;
+  const dim3 grid((L.g.vh + 127) / 128, S);
   const bool pdl = L.next_pdl();
   L.nlaunch += 1;
-  if (w->sfmt == kS64) return launch_k(pdl, flush_kernel<double, kS64, false>, dim3(nb), dim3(128), w->st, L.g, fa);
+  if (w->sfmt == kS64) return launch_k(pdl, flush_kernel<double, kS64, false>, grid, dim3(128), w->st, L.g, fa);
   if (w->sfmt == kS16) {
-    if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS16, true>, dim3(nb), dim3(128), w->st, L.g, fa);
-    return launch_k(pdl, flush_kernel<float, kS16, false>, dim3(nb), dim3(128), w->st, L.g, fa);
+    if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS16, true>, grid, dim3(128), w->st, L.g, fa);
+    return launch_k(pdl, flush_kernel<float, kS16, false>, grid, dim3(128), w->st, L.g, fa);
   }
-  if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS32, true>, dim3(nb), dim3(128), w->st, L.g, fa);
-  return launch_k(pdl, flush_kernel<float, kS32, false>, dim3(nb), dim3(128), w->st, L.g, fa);
+  if (w->xdfmode) return launch_k(pdl, flush_kernel<float, kS32, true>, grid, dim3(128), w->st, L.g, fa);
+  return launch_k(pdl, flush_kernel<float, kS32, false>, grid, dim3(128), w->st, L.g, fa);
 }
 
-// FP64 residual r64 = bvec - (A + sigma) x into r64, |r64|^2 into *dot (device)
+// FP64 residual r64 = bvec - (A + sigma) x into r64, |r64|^2 into *dot (device); one system
 static cudaError_t enqueue_resid64(Launcher& L, const double2* x, const double2* bvec, double sigma, double* dot,
                                    const int* done, const double* a_dev = nullptr) {
   Workspace* w = L.w;
@@ -856,120 +975,145 @@ static cudaError_t enqueue_resid64(Launcher& L, const double2* x, const double2*
   return launch_dslash(L.g, ctx->gauge, d2, w->st, &L.nlaunch);
 }
 
-// double-FP32 residual r_out = fl32(b - (A + sigma) x), |r_out|^2 into *dot (device); b is the
-// split copy of the solve's source.  Three kernels: split x, D_oe, D_eo with the residual epilogue.
-static cudaError_t enqueue_resid_df(Launcher& L, const double2* x, double sigma, const double* a_dev, float2* r_out,
-                                    double* dot, const int* done) {
+// one system's double-FP32 residual: r_out = fl32(b - (A + sigma) x), |r_out|^2 into *dot (device)
+struct ResidTarget {
+  const double2* x;  // the solution (as (hi, lo) pairs in xdfmode)
+  float2* r_out;
+  double* dot;
+  const int* done;   // kernels return at entry when set (may be null)
+};
+
+// Double-FP32 residuals of the L.S systems (b: each system's split copy of its source), in the
+// system's own buffers: split x (FP64 solutions only), D_oe, D_eo with the residual epilogue.  sd_adiag:
+// 4 m^2 + sigma is each system's running a_diag (the reliable update), else 4 m^2 + sigma split here.
+static cudaError_t enqueue_resid_df(Launcher& L, const ResidTarget* t, double sigma, bool sd_adiag) {
   Workspace* w = L.w;
   lqcd_ctx* ctx = L.ctx;
-  const float2* xh = w->dfx_h;
-  const float2* xl = w->dfx_l;
+  const int S = L.S;
   cudaError_t e = cudaSuccess;
-  if (w->xdfmode) {
-    // the solutions are already (hi, lo) pairs
-    xh = reinterpret_cast<const float2*>(x);
-    xl = xh + 3 * (size_t)L.g.vh;
-  } else {
-    e = launch_split_df(L.g, x, w->dfx_h, w->dfx_l, done, w->st, L.next_pdl());
-    L.nlaunch += 1;
-    if (e != cudaSuccess) return e;
+  PerSys<DfArgs> d, r;
+  const double a = 4.0 * ctx->mass * ctx->mass + sigma;
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    const float2* xh = y->dfx_h;
+    const float2* xl = y->dfx_l;
+    if (y->xdfmode) {
+      // the solutions are already (hi, lo) pairs
+      xh = reinterpret_cast<const float2*>(t[s].x);
+      xl = xh + 3 * (size_t)L.g.vh;
+    } else {
+      e = launch_split_df(L.g, t[s].x, y->dfx_h, y->dfx_l, t[s].done, w->st, L.next_pdl());
+      L.nlaunch += 1;
+      if (e != cudaSuccess) return e;
+    }
+    DfArgs& x = d.s[s];
+    x.links_hi = ctx->gauge.u32;
+    x.links_lo = ctx->gauge.u32lo;
+    x.in_hi = xh;
+    x.in_lo = xl;
+    x.out_hi = y->dft_h;
+    x.out_lo = y->dft_l;
+    x.done = t[s].done;
+    x.out_parity = 1;
+    DfArgs& z = r.s[s];
+    z = x;
+    z.in_hi = y->dft_h;
+    z.in_lo = y->dft_l;
+    z.out_hi = z.out_lo = nullptr;
+    z.out_parity = 0;
+    z.x_hi = xh;
+    z.x_lo = xl;
+    z.b_hi = y->dfb_h;
+    z.b_lo = y->dfb_l;
+    z.a = a;
+    if (sd_adiag) {
+      z.a_dev = &y->sd->a_diag;
+      z.a_devdf = &y->sd->a_diag_df;  // the reliable update's 4m^2 + sigma_0
+    } else {
+      const float ah = (float)a;
+      z.a_hi = ah;
+      z.a_lo = (float)(a - (double)ah);
+      z.a_split = 1;
+    }
+    z.r_out = t[s].r_out;
+    z.dot_out = t[s].dot;
+    z.partials = y->partials;
+    z.ticket = y->tickets + 3;
   }
-  DfArgs d;
-  d.links_hi = ctx->gauge.u32;
-  d.links_lo = ctx->gauge.u32lo;
-  d.in_hi = xh;
-  d.in_lo = xl;
-  d.out_hi = w->dft_h;
-  d.out_lo = w->dft_l;
-  d.done = done;
-  d.out_parity = 1;
-  e = launch_df_dslash(L.g, d, 0, w->st, L.next_pdl());
+  e = launch_df_dslash_multi(L.g, d, S, 0, w->st, L.next_pdl());
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  DfArgs r = d;
-  r.in_hi = w->dft_h;
-  r.in_lo = w->dft_l;
-  r.out_hi = r.out_lo = nullptr;
-  r.out_parity = 0;
-  r.x_hi = xh;
-  r.x_lo = xl;
-  r.b_hi = w->dfb_h;
-  r.b_lo = w->dfb_l;
-  r.a = 4.0 * ctx->mass * ctx->mass + sigma;
-  r.a_dev = a_dev;
-  if (a_dev == &w->sd->a_diag) {
-    r.a_devdf = &w->sd->a_diag_df;  // the reliable update's 4m^2 + sigma_0
-  } else if (!a_dev) {
-    const float ah = (float)r.a;
-    r.a_hi = ah;
-    r.a_lo = (float)(r.a - (double)ah);
-    r.a_split = 1;
-  }
-  r.r_out = r_out;
-  r.dot_out = dot;
-  r.partials = w->partials;
-  r.ticket = w->tickets + 3;
-  e = launch_df_dslash(L.g, r, 2, w->st, L.next_pdl());
+  e = launch_df_dslash_multi(L.g, r, S, 2, w->st, L.next_pdl());
   L.nlaunch += 1;
   return e;
 }
 
 // one window of the double-FP32 phase of the precision schedule, its phase test and the (guarded,
 // one-time) change to the FP32 phase
-static cudaError_t enqueue_df_window(Launcher& L, double2* const* xs, const double2* b64, int n,
-                                     cudaGraphConditionalHandle handle, int set_cond) {
+static cudaError_t enqueue_df_window(Launcher& L, int n, cudaGraphConditionalHandle handle, int set_cond) {
   Workspace* w = L.w;
-  const DfBufs B = df_bufs(w, true);
+  const int S = L.S;
   cudaError_t e;
   for (int it = 0; it < kWindow; ++it)
-    if ((e = enqueue_iteration_df(L, B)) != cudaSuccess) return e;
-  if ((e = enqueue_flush(L, xs, b64, n, true)) != cudaSuccess) return e;
-  loop_ctl_df_kernel<<<1, 32, 0, w->st>>>(handle, w->sd, set_cond);
+    if ((e = enqueue_iteration_df(L, true)) != cudaSuccess) return e;
+  if ((e = enqueue_flush(L, n, true)) != cudaSuccess) return e;
+  loop_ctl_df_kernel<<<1, 32, 0, w->st>>>(handle, solver_states(L), S, set_cond);
   L.nlaunch += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  DemoteArgs da;
+  PerSys<DemoteArgs> da;
   memset(&da, 0, sizeof(da));
-  da.r_df = static_cast<const float2*>(w->dr);
-  da.p_df = static_cast<const float2*>(w->dp);
-  da.r = w->r;
-  da.p = w->p;
-  for (int k = 0; k < n; ++k) {
-    da.pk_df[k] = static_cast<const float2*>(w->dpk[k]);
-    da.pk[k] = w->pk[k];
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    DemoteArgs& x = da.s[s];
+    x.r_df = static_cast<const float2*>(y->dr);
+    x.p_df = static_cast<const float2*>(y->dp);
+    x.r = y->r;
+    x.p = y->p;
+    for (int k = 0; k < n; ++k) {
+      x.pk_df[k] = static_cast<const float2*>(y->dpk[k]);
+      x.pk[k] = y->pk[k];
+    }
+    x.n = n;
+    x.sd = y->sd;
   }
-  da.n = n;
-  da.sd = w->sd;
-  const dim3 grid((L.g.vh + 255) / 256);
+  const dim3 grid((L.g.vh + 255) / 256, S);
   if (w->sfmt == kS16) e = launch_k(L.next_pdl(), demote_kernel<kS16>, grid, dim3(256), w->st, L.g, da);
   else e = launch_k(L.next_pdl(), demote_kernel<kS32>, grid, dim3(256), w->st, L.g, da);
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
-  demoted_kernel<<<1, 32, 0, w->st>>>(w->sd);
+  demoted_kernel<<<dim3(1, S), 32, 0, w->st>>>(solver_states(L));
   L.nlaunch += 1;
   return cudaGetLastError();
 }
 
 // iteration batch: windows x (kWindow iterations, flush, reliable update if due).  The reliable-update
 // kernels return at entry unless the beta step marked one as due (ru_skip == 0).
-static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2* b64, int n, int k0, double sigma0,
-                                 int windows, bool use_ru) {
+static cudaError_t enqueue_batch(Launcher& L, int n, int k0, double sigma0, int windows, bool use_ru) {
   cudaError_t e;
   Workspace* w = L.w;
+  const int S = L.S;
   for (int wdx = 0; wdx < windows; ++wdx) {
     for (int it = 0; it < kWindow; ++it)
       if ((e = enqueue_iteration(L)) != cudaSuccess) return e;
-    if ((e = enqueue_flush(L, xs, b64, n)) != cudaSuccess) return e;
+    if ((e = enqueue_flush(L, n)) != cudaSuccess) return e;
     if (use_ru && w->df) {
       // r = fl32(b - (A + sigma_0) x_0) in double-FP32 straight into the Krylov residual
-      if ((e = enqueue_resid_df(L, xs[k0], sigma0, &w->sd->a_diag, static_cast<float2*>(w->r), &w->sd->scal[0],
-                                &w->sd->ru_skip)) != cudaSuccess)
-        return e;
-      if ((e = launch_k(L.next_pdl(), ru_close_kernel, dim3(1), dim3(1), w->st, w->sd, w->ru_count)) != cudaSuccess)
+      ResidTarget t[kMaxRhs];
+      PerSys<int*> counts;
+      memset(&counts, 0, sizeof(counts));
+      for (int s = 0; s < S; ++s) {
+        Workspace* y = L.sys(s);
+        t[s] = ResidTarget{run_solutions(y)[k0], static_cast<float2*>(y->r), &y->sd->scal[0], &y->sd->ru_skip};
+        counts.s[s] = y->ru_count;
+      }
+      if ((e = enqueue_resid_df(L, t, sigma0, true)) != cudaSuccess) return e;
+      if ((e = launch_k(L.next_pdl(), ru_close_kernel, dim3(1, S), dim3(32), w->st, solver_states(L), counts)) !=
+          cudaSuccess)
         return e;
       L.nlaunch += 1;
     } else if (use_ru) {
-      // r64 = b - (A + sigma_0) x_0 in FP64 with FP64 links, then r <- r64 and |r|^2 <- |r64|^2
-      if ((e = enqueue_resid64(L, xs[k0], b64, sigma0, &w->sd->scal[0], &w->sd->ru_skip, &w->sd->a_diag)) !=
+      // one system: r64 = b - (A + sigma_0) x_0 in FP64 with FP64 links, then r <- r64, |r|^2 <- |r64|^2
+      if ((e = enqueue_resid64(L, w->xk[k0], w->b64, sigma0, &w->sd->scal[0], &w->sd->ru_skip, &w->sd->a_diag)) !=
           cudaSuccess)
         return e;
       int nb3 = (3 * L.g.vh + 255) / 256;
@@ -980,7 +1124,11 @@ static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2*
         e = launch_k(pf, ru_finish_kernel<double>, dim3(nb3), dim3(256), w->st, L.g, r64, w->r, sdc);
       else
         e = launch_k(pf, ru_finish_kernel<float>, dim3(nb3), dim3(256), w->st, L.g, r64, w->r, sdc);
-      if (e == cudaSuccess) e = launch_k(pc, ru_close_kernel, dim3(1), dim3(1), w->st, w->sd, w->ru_count);
+      PerSys<int*> counts;
+      memset(&counts, 0, sizeof(counts));
+      counts.s[0] = w->ru_count;
+      if (e == cudaSuccess)
+        e = launch_k(pc, ru_close_kernel, dim3(1, 1), dim3(32), w->st, solver_states(L), counts);
       L.nlaunch += 2;
       if (e != cudaSuccess) return e;
     }
@@ -988,11 +1136,17 @@ static cudaError_t enqueue_batch(Launcher& L, double2* const* xs, const double2*
   return cudaSuccess;
 }
 
-// Solve (A + shifts[k]) xs[k] = b64 for all k (FP64 internal vectors).
-static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts, int n, double tol,
-                      int maxiter, bool use_ru, int* iters, int* n_ru, int* status, int* iters_df) {
-  Workspace* w = ctx->ws;
-  Launcher L{ctx, w, make_geom(ctx), 0};
+// per-system results of solve_core
+struct CoreOut {
+  int iters = 0, n_ru = 0, status = LQCD_OK, iters_df = 0, shift_iters = 0;
+};
+
+// Solve (A + shifts[k]) x_k = b for all k, for each of the L.S systems (the sources in each
+// system's b64, the solutions in its run_solutions()).
+static int solve_core(Launcher& L, const double* shifts, int n, double tol, int maxiter, bool use_ru, CoreOut* out) {
+  lqcd_ctx* ctx = L.ctx;
+  Workspace* w = L.w;
+  const int S = L.S;
   int k0 = 0;
   for (int k = 1; k < n; ++k)
     if (shifts[k] < shifts[k0]) k0 = k;
@@ -1009,24 +1163,29 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
   ip.ru_interval = ctx->reliable_interval;
   ip.ru_delta = ctx->reliable_delta;
   ip.df_switch = sched ? ctx->df_switch : 0.0;
-  LQ_CUDA(cudaMemsetAsync(w->ru_count, 0, sizeof(int), w->st));
   int nb = (L.g.vh + 255) / 256;
-  if (w->kprec == LQCD_DF64)
-    LQ_CUDA(launch_df_init(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4, w->st));
-  else if (sched)
-    LQ_CUDA(launch_df_init(L.g, b64, w->dr, w->dp, w->sd, ip, w->partials, w->tickets + 4, w->st));
-  else if (w->kprec == LQCD_FP64)
-    init_kernel<double><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
-  else
-    init_kernel<float><<<nb, 256, 0, w->st>>>(L.g, b64, w->r, w->p, w->sd, ip, w->partials, w->tickets + 4);
-  L.nlaunch += 1;
-  LQ_CUDA(cudaGetLastError());
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    LQ_CUDA(cudaMemsetAsync(y->ru_count, 0, sizeof(int), w->st));
+    if (y->kprec == LQCD_DF64)
+      LQ_CUDA(launch_df_init(L.g, y->b64, y->r, y->p, y->sd, ip, y->partials, y->tickets + 4, w->st));
+    else if (sched)
+      LQ_CUDA(launch_df_init(L.g, y->b64, y->dr, y->dp, y->sd, ip, y->partials, y->tickets + 4, w->st));
+    else if (y->kprec == LQCD_FP64)
+      init_kernel<double><<<nb, 256, 0, w->st>>>(L.g, y->b64, y->r, y->p, y->sd, ip, y->partials, y->tickets + 4);
+    else
+      init_kernel<float><<<nb, 256, 0, w->st>>>(L.g, y->b64, y->r, y->p, y->sd, ip, y->partials, y->tickets + 4);
+    L.nlaunch += 1;
+    LQ_CUDA(cudaGetLastError());
+  }
 
   if (ctx->use_graph) {
-    // One graph per (source, solution set, shift count, base shift): a while-node repeats
+    // One graph per (source, solution set, shift count, base shift, systems): a while-node repeats
     // [kWindow iterations, window update, reliable update if due, loop control] until done; with the
     // precision schedule a first while-node repeats the double-FP32 windows until that phase ends.
-    auto key = std::make_tuple((const void*)b64, (const void*)xs[0], n * 4 + (use_ru ? 1 : 0) + (sched ? 2 : 0), k0);
+    // The buffers of systems 1 .. S-1 belong to the context (the graphs are dropped when they change).
+    auto key = std::make_tuple((const void*)w->b64, (const void*)run_solutions(w)[0],
+                               n * 4 + (use_ru ? 1 : 0) + (sched ? 2 : 0) + 256 * S, k0);
     auto it = w->graphs.find(key);
     if (it == w->graphs.end()) {
       // with programmatic dependent launch first; captured again without it if the driver
@@ -1054,11 +1213,13 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
           cp1.conditional.type = cudaGraphCondTypeWhile;
           cp1.conditional.size = 1;
           LQ_CUDA(cudaGraphAddNode(&prev, graph, nullptr, nullptr, 0, &cp1));
-          Launcher C1{ctx, w, L.g, 0};
+          Launcher C1 = L;
+          C1.nlaunch = 0;
           C1.pdl = pdl;
+          C1.chained = false;
           LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, cp1.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeThreadLocal));
-          e = enqueue_df_window(C1, xs, b64, n, h1, 1);
+          e = enqueue_df_window(C1, n, h1, 1);
           cudaGraph_t captured1;
           cudaError_t e1 = cudaStreamEndCapture(w->st, &captured1);
           if (e == cudaSuccess) e = e1;
@@ -1074,12 +1235,14 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
         cudaGraphNode_t cnode;
         LQ_CUDA(cudaGraphAddNode(&cnode, graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        Launcher C{ctx, w, L.g, 0};
+        Launcher C = L;
+        C.nlaunch = 0;
         C.pdl = pdl;
+        C.chained = false;
         LQ_CUDA(cudaStreamBeginCaptureToGraph(w->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        if (e == cudaSuccess) e = enqueue_batch(C, xs, b64, n, k0, sigma0, 1, use_ru);
+        if (e == cudaSuccess) e = enqueue_batch(C, n, k0, sigma0, 1, use_ru);
         if (e == cudaSuccess) {
-          loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, w->sd);
+          loop_ctl_kernel<<<1, 32, 0, w->st>>>(handle, solver_states(C), S);
           C.nlaunch += 1;
           e = cudaGetLastError();
         }
@@ -1097,14 +1260,24 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
       it = w->graphs.find(key);
     }
     LQ_CUDA(cudaGraphLaunch(it->second, w->st));
-    // windows_run, max_windows, windows_df
+    // windows_run, max_windows, windows_df (system 0 counts every window of both loops)
     int* wins = reinterpret_cast<int*>(&w->host_status[1]);
     LQ_CUDA(cudaMemcpyAsync(wins, &w->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
     LQ_CUDA(cudaStreamSynchronize(w->st));
-    // kernel nodes per window x windows run, in each phase
-    L.nlaunch += w->graph_nodes[key] * (wins[0] - wins[2]) + w->graph_nodes_df[key] * wins[2];
+    // kernel nodes per window x windows run, in each phase (a system that left the double-FP32 phase
+    // early idles through the phase's remaining windows)
+    int wdf = 0;
+    if (sched) {
+      for (int s = 0; s < S; ++s) {
+        int v = 0;
+        LQ_CUDA(cudaMemcpy(&v, &L.sys(s)->sd->windows_df, sizeof(int), cudaMemcpyDeviceToHost));
+        wdf = std::max(wdf, v);
+      }
+    }
+    L.nlaunch += w->graph_nodes[key] * (wins[0] - wdf) + w->graph_nodes_df[key] * wdf;
   } else {
-    // host-polled batches of windows (at most two in flight) until `finished` says so
+    // host-polled batches of windows (at most two in flight) until every system is done (or, in the
+    // double-FP32 phase, has left it)
     const int windows = std::max(1, ctx->batch / kWindow);
     const int per_batch = windows * kWindow;
     const int max_batches = (maxiter + per_batch - 1) / per_batch;
@@ -1114,22 +1287,27 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
       while (!finished) {
         if (launched < max_batches) {
           if (df_phase) {
-            for (int wdx = 0; wdx < windows; ++wdx) LQ_CUDA(enqueue_df_window(L, xs, b64, n, 0, 0));
+            for (int wdx = 0; wdx < windows; ++wdx) LQ_CUDA(enqueue_df_window(L, n, 0, 0));
           } else {
-            LQ_CUDA(enqueue_batch(L, xs, b64, n, k0, sigma0, windows, use_ru));
+            LQ_CUDA(enqueue_batch(L, n, k0, sigma0, windows, use_ru));
           }
           int slot = launched & 1;
-          LQ_CUDA(cudaMemcpyAsync(&w->host_status[slot], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost,
-                                  w->st));
+          for (int s = 0; s < S; ++s)
+            LQ_CUDA(cudaMemcpyAsync(&L.sys(s)->host_status[slot], &L.sys(s)->sd->iter, sizeof(StatusWords),
+                                    cudaMemcpyDeviceToHost, w->st));
           LQ_CUDA(cudaEventRecord(w->ev_batch[slot], w->st));
           ++launched;
         }
         if (launched - checked >= 2 || launched == max_batches) {
           int slot = checked & 1;
           LQ_CUDA(cudaEventSynchronize(w->ev_batch[slot]));
-          StatusWords sw = w->host_status[slot];
+          bool all = true;
+          for (int s = 0; s < S; ++s) {
+            const StatusWords sw = L.sys(s)->host_status[slot];
+            all = all && (sw.done || (df_phase && sw.halt1));
+          }
           ++checked;
-          if (sw.done || (df_phase && sw.halt1) || checked == max_batches) finished = true;
+          if (all || checked == max_batches) finished = true;
         }
       }
       return LQCD_OK;
@@ -1141,22 +1319,30 @@ static int solve_core(lqcd_ctx* ctx, const double2* b64, double2* const* xs, con
     int rc = run_batches(false);
     if (rc != LQCD_OK) return rc;
   }
-  // drain a batch still in flight and read the final state
-  LQ_CUDA(cudaMemcpyAsync(&w->host_status[0], &w->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
-  int ru_host = 0, wins_df[3] = {0, 0, 0};
-  LQ_CUDA(cudaMemcpyAsync(&ru_host, w->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
-  LQ_CUDA(cudaMemcpyAsync(&w->shift_iters_host, &w->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost, w->st));
-  LQ_CUDA(cudaMemcpyAsync(wins_df, &w->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
+  // drain a batch still in flight and read the final state of every system
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    LQ_CUDA(cudaMemcpyAsync(&y->host_status[0], &y->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
+  }
   LQ_CUDA(cudaStreamSynchronize(w->st));
-  StatusWords last = w->host_status[0];
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    int ru_host = 0, wins_df[3] = {0, 0, 0};
+    LQ_CUDA(cudaMemcpy(&ru_host, y->ru_count, sizeof(int), cudaMemcpyDeviceToHost));
+    LQ_CUDA(cudaMemcpy(&y->shift_iters_host, &y->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost));
+    LQ_CUDA(cudaMemcpy(wins_df, &y->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    const StatusWords last = y->host_status[0];
+    CoreOut& o = out[s];
+    o.iters = last.iter;
+    o.n_ru = ru_host;
+    o.shift_iters = y->shift_iters_host;
+    // iterations of the double-FP32 phase: the windows it ran, the last one possibly partial
+    o.iters_df = sched ? std::min(last.iter, kWindow * wins_df[2]) : 0;
+    if (last.status != LQCD_OK) o.status = last.status;
+    else if (!last.done || last.n_active > 0) o.status = LQCD_ERR_NOT_CONVERGED;
+    else o.status = LQCD_OK;
+  }
   ctx->launches += L.nlaunch;
-  *iters = last.iter;
-  *n_ru = ru_host;
-  // iterations of the double-FP32 phase: the windows it ran, the last one possibly partial
-  *iters_df = sched ? std::min(last.iter, kWindow * wins_df[2]) : 0;
-  if (last.status != LQCD_OK) *status = last.status;
-  else if (!last.done || last.n_active > 0) *status = LQCD_ERR_NOT_CONVERGED;
-  else *status = LQCD_OK;
   return LQCD_OK;
 }
 
@@ -1199,23 +1385,23 @@ __global__ void add_correction_kernel(int n3, double2* __restrict__ x, const voi
   x[i] = a;
 }
 
-// True residuals |b - (A + shifts[k]) x_k| / |b| for the listed shifts (double-FP32 in the modes
-// that keep x_k as (hi, lo) pairs, FP64 otherwise); when keep is not null each residual is also
-// stored in keep[k] (refinement precision) as a right-hand side.
-static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs, const double* shifts,
-                          const std::vector<int>& ks, double bnorm2, double* out, void* const* keep, int keep_f32) {
-  Workspace* w = ctx->ws;
+// True residuals |b - (A + shifts[k]) x_k| / |b| of one system (workspace w) for the listed shifts
+// (double-FP32 in the modes that keep x_k as (hi, lo) pairs, FP64 otherwise); when keep is not null
+// each residual is also stored in keep[k] (refinement precision) as a right-hand side.
+static int true_residuals(lqcd_ctx* ctx, Workspace* w, const double* shifts, const std::vector<int>& ks,
+                          double bnorm2, double* out, void* const* keep, int keep_f32) {
   Launcher L{ctx, w, make_geom(ctx), 0};
+  double2* const* xs = run_solutions(w);
   const int n3 = 3 * L.g.vh;
   for (size_t j = 0; j < ks.size(); ++j) {
     int k = ks[j];
     if (w->df) {
       // straight into the refinement right-hand side (FP32), else into a scratch vector
-      float2* dst = static_cast<float2*>(keep ? keep[k] : w->q);
-      LQ_CUDA(enqueue_resid_df(L, xs[k], shifts[k], nullptr, dst, &w->sd->scal[4 + j % kMaxShifts], nullptr));
+      ResidTarget t{xs[k], static_cast<float2*>(keep ? keep[k] : w->q), &w->sd->scal[4 + j % kMaxShifts], nullptr};
+      LQ_CUDA(enqueue_resid_df(L, &t, shifts[k], false));
       continue;
     }
-    LQ_CUDA(enqueue_resid64(L, xs[k], b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
+    LQ_CUDA(enqueue_resid64(L, xs[k], w->b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
     if (keep) {
       keep_residual_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->r64, keep[k], keep_f32);
       L.nlaunch += 1;
@@ -1229,115 +1415,132 @@ static int true_residuals(lqcd_ctx* ctx, const double2* b64, double2* const* xs,
   return LQCD_OK;
 }
 
-int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
-               double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats) {
-  int rc = ensure_workspace(ctx, prec, n);
+// The shifted CG of S right-hand sides b_devs[s] on one context (S = 1: mshift_cg; S > 1:
+// mshift_cg_multi).  Each system is solved exactly as on its own; the systems share the kernel
+// launches and, in the FP32 phase, every link load of the Dslash.
+int run_mshift_multi(lqcd_ctx* ctx, int S, const double* shifts, const double* residues, int n, double c0,
+                     const double* const* b_devs, double* const* const* x_devs, double* const* y_devs, double tol,
+                     int maxiter, int prec, lqcd_solve_stats* stats) {
+  int rc = ensure_workspaces(ctx, prec, n, S);
   if (rc != LQCD_OK) return rc;
   Workspace* w = ctx->ws;
   Geom g = make_geom(ctx);
+  Launcher L{ctx, w, g, 0};
+  L.S = S;
+  for (int s = 1; s < S; ++s) L.more[s] = ctx->ws_extra[s - 1];
   long long launches0 = ctx->launches;
   LQ_CUDA(cudaEventRecord(w->ev_in, ctx->stream));
   LQ_CUDA(cudaStreamWaitEvent(w->st, w->ev_in, 0));
   LQ_CUDA(cudaEventRecord(w->ev_t0, w->st));
-  LQ_CUDA(launch_pack_vector(g, w->b64, LQCD_FP64, reinterpret_cast<const double2*>(b_dev), w->st));
-  ctx->launches += 1;
-  if (w->df) {
-    LQ_CUDA(launch_split_df(g, w->b64, w->dfb_h, w->dfb_l, nullptr, w->st, false));
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    LQ_CUDA(launch_pack_vector(g, y->b64, LQCD_FP64, reinterpret_cast<const double2*>(b_devs[s]), w->st));
     ctx->launches += 1;
-  }
-
-  int iters = 0, n_ru = 0, st_main = LQCD_OK, iters_df = 0;
-  // The solutions live as (hi, lo) FP32 pairs through the solve, the checks and the refinement
-  // (every mode but LQCD_FP64) and become FP64 at the end; LQCD_DF64 needs no reliable updates.
-  const bool dfsolve = prec == LQCD_DF64;
-  double2* const* xs_run = w->xdfmode ? reinterpret_cast<double2* const*>(w->xdf) : w->xk;
-  rc = solve_core(ctx, w->b64, xs_run, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, &iters, &n_ru,
-                  &st_main, &iters_df);
-  if (rc != LQCD_OK) return rc;
-  LQ_CUDA(cudaMemcpyAsync(w->host_scal, &w->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
-  LQ_CUDA(cudaStreamSynchronize(w->st));
-  double bb = w->host_scal[0];
-
-  double tres[kMaxShifts];
-  for (int k = 0; k < n; ++k) tres[k] = 0.0;
-  int refine_iters = 0, refined = 0, rounds_done = 0, status = st_main;
-  if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
-    std::vector<int> all(n);
-    for (int k = 0; k < n; ++k) all[k] = k;
-    const bool refine = ctx->refine && st_main == LQCD_OK;
-    void* const* rhs = nullptr;
-    const int f32 = prec != LQCD_FP64;
-    if (refine) {
-      rc = mrhs_prepare(ctx, prec, n, &rhs);
-      if (rc != LQCD_OK) return rc;
-    }
-    rc = true_residuals(ctx, w->b64, xs_run, shifts, all, bb, tres, rhs, f32);
-    if (rc != LQCD_OK) return rc;
-    // Per-shift refinement, all shifts at once: (A + d_k) e_k = b - (A + d_k) x_k for every shift whose
-    // true residual is above tol, each reduced by 0.75 tol / residual (a 25 % margin for the FP32
-    // operator of the correction solve and the ~1e-12 |b| of the residual check), then x_k += e_k and
-    // a new check.
-    for (int round = 0; refine && round < 4; ++round) {
-      std::vector<int> todo;
-      double rel[kMaxShifts];
-      for (int k = 0; k < n; ++k) {
-        rel[k] = 1e300;  // systems already below tol are not iterated
-        if (tres[k] > tol) {
-          todo.push_back(k);
-          rel[k] = std::min(0.5, 0.75 * tol / tres[k]);
-        }
-      }
-      if (todo.empty()) break;
-      int it2 = 0, st2 = LQCD_OK;
-      rc = mrhs_solve(ctx, prec, n, shifts, rel, maxiter, w->st, &it2, &st2);
-      if (rc != LQCD_OK) return rc;
-      refine_iters += it2;
-      void* const* es = mrhs_solutions(ctx);
-      const int n3 = 3 * g.vh;
-      for (int k : todo) {
-        if (w->xdfmode)
-          add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(w->xdf[k]),
-                                                                         static_cast<const float2*>(es[k]));
-        else
-          add_correction_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->xk[k], es[k], f32);
-        ctx->launches += 1;
-      }
-      LQ_CUDA(cudaGetLastError());
-      if (round == 0) refined = (int)todo.size();
-      rounds_done = round + 1;
-      rc = true_residuals(ctx, w->b64, xs_run, shifts, todo, bb, tres, rhs, f32);
-      if (rc != LQCD_OK) return rc;
-      if (st2 == LQCD_ERR_NONFINITE) break;
-    }
-    if (status == LQCD_OK)
-      for (int k = 0; k < n; ++k)
-        if (!(tres[k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
-  }
-  if (w->xdfmode && bb != 0.0) {
-    for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, w->xdf[k], w->xk[k], w->st));
-    ctx->launches += n;
-  }
-  if (bb == 0.0) {
-    for (int k = 0; k < n; ++k) {
-      zero_kernel<<<(3 * g.vh + 255) / 256, 256, 0, w->st>>>(3 * g.vh, w->xk[k]);
+    if (y->df) {
+      LQ_CUDA(launch_split_df(g, y->b64, y->dfb_h, y->dfb_l, nullptr, w->st, false));
       ctx->launches += 1;
     }
   }
-  // outputs in the canonical layout
-  OutArgs oa;
-  memset(&oa, 0, sizeof(oa));
-  for (int k = 0; k < n; ++k) {
-    oa.xk[k] = w->xk[k];
-    oa.xout[k] = x_dev ? reinterpret_cast<double2*>(x_dev[k]) : nullptr;
-    oa.c[k] = residues ? residues[k] : 0.0;
+
+  // The solutions live as (hi, lo) FP32 pairs through the solve, the checks and the refinement
+  // (every mode but LQCD_FP64) and become FP64 at the end; LQCD_DF64 needs no reliable updates.
+  const bool dfsolve = prec == LQCD_DF64;
+  CoreOut core[kMaxRhs];
+  rc = solve_core(L, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, core);
+  if (rc != LQCD_OK) return rc;
+
+  int status_all = LQCD_OK;
+  int refine_iters[kMaxRhs] = {}, refined[kMaxRhs] = {}, rounds_done[kMaxRhs] = {};
+  double tres[kMaxRhs][kMaxShifts];
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    double2* const* xs_run = run_solutions(y);
+    LQ_CUDA(cudaMemcpyAsync(y->host_scal, &y->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
+    LQ_CUDA(cudaStreamSynchronize(w->st));
+    const double bb = y->host_scal[0];
+    const int st_main = core[s].status;
+    int status = st_main;
+    for (int k = 0; k < n; ++k) tres[s][k] = 0.0;
+    if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
+      std::vector<int> all(n);
+      for (int k = 0; k < n; ++k) all[k] = k;
+      const bool refine = ctx->refine && st_main == LQCD_OK;
+      void* const* rhs = nullptr;
+      const int f32 = prec != LQCD_FP64;
+      if (refine) {
+        rc = mrhs_prepare(ctx, prec, n, &rhs);
+        if (rc != LQCD_OK) return rc;
+      }
+      rc = true_residuals(ctx, y, shifts, all, bb, tres[s], rhs, f32);
+      if (rc != LQCD_OK) return rc;
+      // Per-shift refinement, all shifts of the system at once: (A + d_k) e_k = b - (A + d_k) x_k for every
+      // shift whose true residual is above tol, each reduced by 0.75 tol / residual (a 25 % margin for the
+      // FP32 operator of the correction solve and the ~1e-12 |b| of the residual check), then x_k += e_k
+      // and a new check.
+      for (int round = 0; refine && round < 4; ++round) {
+        std::vector<int> todo;
+        double rel[kMaxShifts];
+        for (int k = 0; k < n; ++k) {
+          rel[k] = 1e300;  // systems already below tol are not iterated
+          if (tres[s][k] > tol) {
+            todo.push_back(k);
+            rel[k] = std::min(0.5, 0.75 * tol / tres[s][k]);
+          }
+        }
+        if (todo.empty()) break;
+        int it2 = 0, st2 = LQCD_OK;
+        rc = mrhs_solve(ctx, prec, n, shifts, rel, maxiter, w->st, &it2, &st2);
+        if (rc != LQCD_OK) return rc;
+        refine_iters[s] += it2;
+        void* const* es = mrhs_solutions(ctx);
+        const int n3 = 3 * g.vh;
+        for (int k : todo) {
+          if (y->xdfmode)
+            add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(y->xdf[k]),
+                                                                           static_cast<const float2*>(es[k]));
+          else
+            add_correction_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, y->xk[k], es[k], f32);
+          ctx->launches += 1;
+        }
+        LQ_CUDA(cudaGetLastError());
+        if (round == 0) refined[s] = (int)todo.size();
+        rounds_done[s] = round + 1;
+        rc = true_residuals(ctx, y, shifts, todo, bb, tres[s], rhs, f32);
+        if (rc != LQCD_OK) return rc;
+        if (st2 == LQCD_ERR_NONFINITE) break;
+      }
+      if (status == LQCD_OK)
+        for (int k = 0; k < n; ++k)
+          if (!(tres[s][k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
+    }
+    if (y->xdfmode && bb != 0.0) {
+      for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, y->xdf[k], y->xk[k], w->st));
+      ctx->launches += n;
+    }
+    if (bb == 0.0) {
+      for (int k = 0; k < n; ++k) {
+        zero_kernel<<<(3 * g.vh + 255) / 256, 256, 0, w->st>>>(3 * g.vh, y->xk[k]);
+        ctx->launches += 1;
+      }
+    }
+    // outputs in the canonical layout
+    OutArgs oa;
+    memset(&oa, 0, sizeof(oa));
+    for (int k = 0; k < n; ++k) {
+      oa.xk[k] = y->xk[k];
+      oa.xout[k] = x_devs && x_devs[s] ? reinterpret_cast<double2*>(x_devs[s][k]) : nullptr;
+      oa.c[k] = residues ? residues[k] : 0.0;
+    }
+    oa.c0 = c0;
+    oa.b64 = y->b64;
+    oa.y = y_devs ? reinterpret_cast<double2*>(y_devs[s]) : nullptr;
+    oa.n = n;
+    outputs_kernel<<<(g.vh + 255) / 256, 256, 0, w->st>>>(g, oa);
+    ctx->launches += 1;
+    LQ_CUDA(cudaGetLastError());
+    core[s].status = status;
+    if (status_all == LQCD_OK && status != LQCD_OK) status_all = status;
   }
-  oa.c0 = c0;
-  oa.b64 = w->b64;
-  oa.y = reinterpret_cast<double2*>(y_dev);
-  oa.n = n;
-  outputs_kernel<<<(g.vh + 255) / 256, 256, 0, w->st>>>(g, oa);
-  ctx->launches += 1;
-  LQ_CUDA(cudaGetLastError());
   LQ_CUDA(cudaEventRecord(w->ev_t1, w->st));
   LQ_CUDA(cudaEventRecord(w->ev_out, w->st));
   LQ_CUDA(cudaStreamWaitEvent(ctx->stream, w->ev_out, 0));
@@ -1345,23 +1548,35 @@ int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int 
   float ms = 0;
   LQ_CUDA(cudaEventElapsedTime(&ms, w->ev_t0, w->ev_t1));
   if (stats) {
-    memset(stats, 0, sizeof(*stats));
-    stats->iterations = iters;
-    stats->reliable_updates = n_ru;
-    stats->refine_iterations = refine_iters;
-    stats->refined_shifts = refined;
-    stats->refine_rounds = rounds_done;
-    stats->kernel_launches = (int)(ctx->launches - launches0);
-    stats->n_shifts = n;
-    stats->shift_iterations = w->shift_iters_host;
-    stats->df_iterations = iters_df;
-    for (int k = 0; k < n; ++k) stats->true_residual[k] = tres[k];
-    stats->ms = ms;
+    for (int s = 0; s < S; ++s) {
+      lqcd_solve_stats& st = stats[s];
+      memset(&st, 0, sizeof(st));
+      st.iterations = core[s].iters;
+      st.reliable_updates = core[s].n_ru;
+      st.refine_iterations = refine_iters[s];
+      st.refined_shifts = refined[s];
+      st.refine_rounds = rounds_done[s];
+      st.kernel_launches = (int)(ctx->launches - launches0);
+      st.n_shifts = n;
+      st.shift_iterations = core[s].shift_iters;
+      st.df_iterations = core[s].iters_df;
+      for (int k = 0; k < n; ++k) st.true_residual[k] = tres[s][k];
+      st.ms = ms;
+    }
   }
-  if (status == LQCD_ERR_NONFINITE) return fail(ctx, status, "non-finite value in the shifted CG");
-  if (status == LQCD_ERR_NOT_CONVERGED) return fail(ctx, status, "shifted CG did not reach the requested residual");
-  if (status != LQCD_OK) return fail(ctx, status, "shifted CG failed");
+  if (status_all == LQCD_ERR_NONFINITE) return fail(ctx, status_all, "non-finite value in the shifted CG");
+  if (status_all == LQCD_ERR_NOT_CONVERGED)
+    return fail(ctx, status_all, "shifted CG did not reach the requested residual");
+  if (status_all != LQCD_OK) return fail(ctx, status_all, "shifted CG failed");
   return LQCD_OK;
+}
+
+int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,
+               double* const* x_dev, double* y_dev, double tol, int maxiter, int prec, lqcd_solve_stats* stats) {
+  const double* b[1] = {b_dev};
+  double* const* x[1] = {x_dev};
+  double* y[1] = {y_dev};
+  return run_mshift_multi(ctx, 1, shifts, residues, n, c0, b, x, y_dev ? y : nullptr, tol, maxiter, prec, stats);
 }
 
 }  // namespace lqcd

@@ -174,9 +174,17 @@ __device__ __forceinline__ void window_scalars(SolverDev* sd) {
   }
 #pragma unroll
   for (int i = 0; i < kWindow; ++i) pi[i] = chi[i] = 0.0;
+  // the window's base scalars: lane j loads iteration j's, all at once (no chain of dependent loads)
+  double al = 0.0, be = 0.0, rn = 0.0;
+  if (k < m) {
+    al = sd->alpha_h[k];
+    be = sd->beta_h[k];
+    rn = sd->rr_h[k];
+  }
   int shift_iters = 0;
   for (int j = 0; j < m; ++j) {
-    const double alpha = sd->alpha_h[j], beta = sd->beta_h[j], rr_new = sd->rr_h[j];
+    const double alpha = __shfl_sync(0xffffffffu, al, j), beta = __shfl_sync(0xffffffffu, be, j),
+                 rr_new = __shfl_sync(0xffffffffu, rn, j);
     shift_iters += __popc(__ballot_sync(0xffffffffu, act != 0));
     if (act) {
       const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + sk * alpha);

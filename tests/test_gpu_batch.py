@@ -179,3 +179,37 @@ def test_dslash_batch_of_many_lattices_in_one_launch_and_under_capture():
         lq.dslash_eo(ctx, single, vin, 1 - p, lq.FP32)
         torch.cuda.synchronize()
         assert torch.equal(single, vout)
+
+
+def test_batch_of_multi_rhs_problems_equals_single_solves():
+    # one problem per lattice with its four sources solved together (mshift_cg_multi), the problems
+    # run concurrently by mshift_cg_batch: every source's solutions and y equal its stand-alone
+    # mshift_cg solve bit for bit
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    lattices = [((4, 4, 4, 4), 0.1), ((10, 6, 4, 6), 0.05), ((8, 8, 8, 4), 0.02), ((12, 12, 12, 4), 0.05)]
+    problems = []
+    for li, (dims, mass) in enumerate(lattices):
+        ctx, U = make_context(dims, mass, gauge_seed=150 + li)
+        c0, res, poles, _ = rational.zolotarev_inv_sqrt(12, 4 * mass ** 2, 16 + 4 * mass ** 2)
+        bs = [to_dev(inputs.gaussian_vector(dims, 160 + 4 * li + f)) for f in range(4)]
+        xss = [[torch.empty_like(b) for _ in poles] for b in bs]
+        ys = [torch.empty_like(b) for b in bs]
+        problems.append(dict(ctx=ctx, shifts=poles, residues=res, c0=c0, bs=bs, xss=xss, ys=ys, tol=1e-10,
+                             prec=lq.FP32))
+    rc, st, stats = lq.mshift_cg_batch(problems, nthreads=4)
+    torch.cuda.synchronize()
+    assert rc == 0 and all(s == 0 for s in st)
+    for p, sts in zip(problems, stats):
+        assert len(sts) == 4
+        for f in range(4):
+            xs = [torch.empty_like(p["bs"][f]) for _ in p["shifts"]]
+            y = torch.empty_like(p["bs"][f])
+            rc1, st1 = lq.mshift_cg(p["ctx"], p["shifts"], p["residues"], p["c0"], p["bs"][f], xs, y, tol=1e-10,
+                                    prec=lq.FP32)
+            torch.cuda.synchronize()
+            assert rc1 == 0 and st1["iterations"] == sts[f]["iterations"]
+            assert all(torch.equal(a, c) for a, c in zip(xs, p["xss"][f]))
+            assert torch.equal(y, p["ys"][f])
