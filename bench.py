@@ -226,6 +226,23 @@ def time_dslash(lq, torch, ctx, prec_name, prec, reps, flush_buf):
     return statistics.mean(ms), statistics.median(ms)
 
 
+def fp64_peak_tflops(torch, n=4096, reps=5):
+    """FP64 matrix-multiply rate (cuBLAS DGEMM, 2 n^3 flops per product), best of reps."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
 STREAM_FIELDS = 8  # 8 x 75.5 MB of FP32 links: each field is ~528 MB of traffic old when it is read again
 
 
@@ -715,7 +732,8 @@ def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
     `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
     then 6 replays of the graph: 592 launches),
-    `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch."""
+    `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch,
+    `multi` = the same for four sources solved together (mshift_cg_multi)."""
     import torch
 
     import __graft_entry__
@@ -736,6 +754,15 @@ def run_profile_target(kind, prec_name):
         vin.view(torch.float32 if prec != lq.FP64 else torch.float64).normal_()
         for r in range(8):
             lq.dslash_eo(ctx, vout, vin, r & 1, prec)
+    elif kind == "multi":
+        # four sources solved together (mshift_cg_multi), graphs off
+        ctx.set_option(lq.OPT_USE_GRAPH, 0)
+        bs = [torch.from_numpy(inputs.gaussian_vector(DIMS, VEC_SEED + 100 * s)).cuda() for s in range(4)]
+        c0, res, poles, _ = lq.rational_coeffs(-0.5, 4 * MASS * MASS, 16 + 4 * MASS * MASS, NPOLES)
+        rc, sts = lq.mshift_cg_multi(ctx, poles, res, c0, bs, None, None, tol=TOL, prec=prec)
+        print(json.dumps({"profile": "multi", "rc": rc, "iterations": [s["iterations"] for s in sts],
+                          "refine_iterations": [s["refine_iterations"] for s in sts],
+                          "launches": ctx.launch_count()}))
     else:
         ctx.set_option(lq.OPT_USE_GRAPH, 0)
         b = torch.from_numpy(inputs.gaussian_vector(DIMS, VEC_SEED)).cuda()
@@ -757,7 +784,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
-    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve"], help="run a small fixed workload for ncu and exit")
+    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve", "multi"],
+                    help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
     ap.add_argument("--traj-steps", type=int, default=TRAJ_STEPS, help="Omelyan steps per trajectory for --rhmc")
@@ -889,6 +917,12 @@ def main():
         gbs = DSLASH_BYTES_PER_SITE[name] * vh / (mean_ms * 1e-3) / 1e9
         dsl[name] = {"ms": mean_ms, "median_ms": med_ms, "algorithmic_GBps": gbs, "frac_of_hbm": gbs / peak,
                      "gflops": DSLASH_FLOPS_PER_SITE * vh / (mean_ms * 1e-3) / 1e9}
+    if "fp64" in dsl:
+        # the FP64 Dslash against GB300's FP64 rate, measured here with cuBLAS DGEMM (the FP64 pipe's
+        # ceiling for plain FP64 arithmetic)
+        f64 = fp64_peak_tflops(torch)
+        dsl["fp64"]["fp64_peak_tflops_dgemm"] = f64
+        dsl["fp64"]["frac_of_fp64_peak"] = dsl["fp64"]["gflops"] / 1e3 / f64
     traffic = profiled_traffic(WORKLOAD)
     d32 = dsl["fp32"]
     sctx = make_stream_contexts(lq, torch, Ud, STREAM_FIELDS)

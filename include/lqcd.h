@@ -197,7 +197,8 @@ int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, in
  *   - Size limit: V/2 <= 170661 sites for LQCD_FP64 and <= 341322 for the FP32 modes
  *     (e.g. 32^3 x 8 fits in every precision, 40^3 x 8 in the FP32 modes), whatever
  *     LQCD_OPT_DSLASH_TPS is set to; larger lattices get LQCD_ERR_ARG with a message
- *     naming the limit.
+ *     naming the limit.  It runs the context's threads per site in 128-thread blocks in
+ *     linear order (LQCD_OPT_DSLASH_BS and LQCD_OPT_DSLASH_ORDER do not apply).
  *   - The first call on each device looks up the array's device address (with that device
  *     current) and caches it; make that first call before any stream capture.
  *   - Every call uses the same array: calls that may overlap on the GPU (other streams,
@@ -226,7 +227,7 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
 #define LQCD_OPT_USE_GRAPH 4         /* 1 = one CUDA graph per solve whose conditional while-node repeats a
                                         10-iteration window until the device says done (default);
                                         0 = plain launches, host polls a device flag per batch */
-#define LQCD_OPT_DSLASH_TPS 5        /* threads per output site in the FP32 Dslash (1, 2, 4 or 8; 0 = tuned) */
+#define LQCD_OPT_DSLASH_TPS 5        /* threads per output site in the FP32 Dslash (1, 2, 4 or 8; 0 = default 1) */
 #define LQCD_OPT_RELIABLE_DELTA 6    /* a reliable update is also due once |r| drops below delta times its
                                         largest value since the last one (default 0.01) */
 #define LQCD_OPT_PDL 7               /* 1 = kernels inside the captured solve graphs use programmatic dependent
@@ -243,6 +244,10 @@ int lqcd_neighbour_table(lqcd_ctx* ctx, int* fwd_dev, int* bwd_dev, int* sign_de
                                         shifted solutions by about eps_32 |r_j|, and they get no reliable
                                         update of their own: starting in double-FP32 leaves them far closer
                                         to the tolerance and shortens the per-shift refinement */
+#define LQCD_OPT_DSLASH_BS 10        /* threads per block of the FP32 Dslash: 64 or 128 (0 = 128) */
+#define LQCD_OPT_DSLASH_ORDER 11     /* block-to-site order of the FP32 Dslash: 0 linear (default), 1 the two halves
+                                        of the site range interleaved (blocks running together stream from two
+                                        distant regions of the vectors and link blocks) */
 int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
 
 /*
@@ -359,12 +364,15 @@ typedef struct {
 int mshift_cg_batch(lqcd_batch_problem* problems, int nprob, int nthreads);
 
 /*
- * lqcd_autotune - time the half-Dslash of precision prec (LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8
- * or LQCD_FP32_L16) with 1, 2,
- * 4 and 8 threads per output site on this context's lattice and gauge field, keep the fastest
- * (as LQCD_OPT_DSLASH_TPS) and store it in *best_tps (may be NULL).  Allocates and frees two
- * temporary vectors; synchronises the context stream.
+ * lqcd_autotune_shape - time the half-Dslash of precision prec (LQCD_FP32, LQCD_FP32_R12, LQCD_FP32_R8
+ * or LQCD_FP32_L16) on this context's lattice and gauge field for every launch shape: 1, 2, 4 or 8
+ * threads per output site, 64 or 128 threads per block, linear or interleaved block-to-site order
+ * (LQCD_OPT_DSLASH_ORDER); keep the fastest (as LQCD_OPT_DSLASH_TPS, LQCD_OPT_DSLASH_BS,
+ * LQCD_OPT_DSLASH_ORDER) and store it in *best_tps, *best_bs, *best_order (each may be NULL).
+ * Allocates and frees two temporary vectors; synchronises the context stream.
+ * lqcd_autotune is the same with only *best_tps reported.
  */
+int lqcd_autotune_shape(lqcd_ctx* ctx, int prec, int* best_tps, int* best_bs, int* best_order);
 int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps);
 
 /* Parameters of rhmc_trajectory. */

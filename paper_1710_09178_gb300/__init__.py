@@ -48,6 +48,8 @@ OPT_RELIABLE_DELTA = 6
 OPT_PDL = 7
 OPT_DF_RESID = 8
 OPT_DF_SWITCH = 9
+OPT_DSLASH_BS = 10
+OPT_DSLASH_ORDER = 11
 
 MAX_SHIFTS = 32
 MAX_BATCH = 128
@@ -58,7 +60,7 @@ EXPORTED = [
     "lqcd_pack_vector", "lqcd_unpack_vector", "dslash_eo", "lqcd_apply_A", "lqcd_neighbour_table",
     "lqcd_set_option", "mshift_cg", "lqcd_rational_coeffs", "lqcd_launch_count", "lqcd_apply_A_noalloc",
     "fermion_force", "rhmc_trajectory", "mshift_cg_batch", "lqcd_autotune",
-    "lqcd_share_gauge", "dslash_eo_batch", "lqcd_bounds_word", "mshift_cg_multi",
+    "lqcd_share_gauge", "dslash_eo_batch", "lqcd_bounds_word", "mshift_cg_multi", "lqcd_autotune_shape",
 ]
 
 
@@ -194,6 +196,8 @@ def _bind(path):
         "rhmc_trajectory": (i, [vp, ctypes.POINTER(RhmcParams), vp, vp, vp, d, ctypes.POINTER(TrajResult)]),
         "mshift_cg_batch": (i, [ctypes.POINTER(BatchProblem), i, i]),
         "lqcd_autotune": (i, [vp, i, ctypes.POINTER(ctypes.c_int)]),
+        "lqcd_autotune_shape": (i, [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
         "lqcd_share_gauge": (i, [vp, vp]),
         "dslash_eo_batch": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), i, i]),
         "lqcd_bounds_word": (i, [vp, ctypes.POINTER(ctypes.c_uint)]),
@@ -313,10 +317,19 @@ class Context:
         return self.check(self.lib.lqcd_set_option(self.handle, int(key), float(value)))
 
     def autotune(self, prec=FP32):
-        """Pick the fastest Dslash threads-per-site on this lattice (lqcd_autotune); returns it."""
+        """Pick the fastest Dslash launch shape on this lattice (lqcd_autotune); returns the threads
+        per site (the block size and order chosen are set too: autotune_shape reports them)."""
         best = ctypes.c_int(0)
         self.check(self.lib.lqcd_autotune(self.handle, int(prec), ctypes.byref(best)))
         return best.value
+
+    def autotune_shape(self, prec=FP32):
+        """Pick the fastest Dslash launch shape on this lattice (lqcd_autotune_shape); returns
+        (threads per site, threads per block, block-to-site order)."""
+        t, b, o = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self.check(self.lib.lqcd_autotune_shape(self.handle, int(prec), ctypes.byref(t), ctypes.byref(b),
+                                                ctypes.byref(o)))
+        return t.value, b.value, o.value
 
     def launch_count(self):
         """Kernels the library has launched on this context (graph nodes counted)."""

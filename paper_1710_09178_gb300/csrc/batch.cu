@@ -10,10 +10,11 @@
 // several solves of one lattice read them, so concurrency recovers both the idle SMs and the
 // link reuse of a multi-right-hand-side kernel.
 //
-// Autotuning.  lqcd_autotune times the FP32 (or 12-real) half-Dslash with 1, 2, 4 and 8 threads
-// per output site on the context's own lattice and keeps the fastest: one thread per site wins
-// at 32^3 x 8, more threads per site win on small lattices where one thread per site leaves
-// most SMs idle.
+// Autotuning.  lqcd_autotune_shape times the FP32 (or compressed-link) half-Dslash on the context's
+// own lattice for every launch shape -- 1, 2, 4 or 8 threads per output site, 64 or 128 threads per
+// block, linear or interleaved block-to-site order -- and keeps the fastest: one thread per site in
+// 128-thread blocks wins at 32^3 x 8, more threads per site and smaller blocks win on small lattices
+// where one thread per site leaves most SMs idle.
 #include <atomic>
 #include <string>
 #include <thread>
@@ -24,7 +25,7 @@
 
 using namespace lqcd;
 
-extern "C" int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps) {
+extern "C" int lqcd_autotune_shape(lqcd_ctx* ctx, int prec, int* best_tps, int* best_bs, int* best_order) {
   if (!ctx) return LQCD_ERR_ARG;
   if (!vec_fp32(prec)) return fail(ctx, LQCD_ERR_ARG, "lqcd_autotune: FP32-vector modes only");
   if (!ctx->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_autotune: no gauge field loaded");
@@ -32,45 +33,55 @@ extern "C" int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps) {
   size_t vb = 24 * (size_t)ctx->Vh;
   void *in = nullptr, *out = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   int rc = LQCD_OK;
   float best_ms = 1e30f;
-  int best = 1;
-  const int tps_list[4] = {1, 2, 4, 8};
+  int best[3] = {1, 128, 0};
+  const int tps_list[4] = {1, 2, 4, 8}, bs_list[2] = {128, 64}, order_list[2] = {0, 1};
   if ((e = cudaMalloc(&in, vb)) != cudaSuccess || (e = cudaMalloc(&out, vb)) != cudaSuccess ||
       (e = cudaMemsetAsync(in, 0, vb, ctx->stream)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
       (e = cudaEventCreate(&e1)) != cudaSuccess) {
     rc = cuda_check(ctx, e, "lqcd_autotune setup");
   }
+  // every (threads per site, threads per block, block-to-site order): 4 warm-up launches, then the
+  // event time of 20 back-to-back launches alternating the parity
   for (int t = 0; t < 4 && rc == LQCD_OK; ++t) {
-    DslashArgs a;
-    a.out = out;
-    a.in = in;
-    a.prec = prec;
-    a.tps = tps_list[t];
-    int nl = 0;
-    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
-      a.out_parity = r & 1;
-      e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
-    }
-    const int reps = 20;
-    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-      a.out_parity = r & 1;
-      e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = cuda_check(ctx, e, "lqcd_autotune");
-      break;
-    }
-    ctx->launches += nl;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = tps_list[t];
+    for (int bi = 0; bi < 2 && rc == LQCD_OK; ++bi) {
+      for (int oi = 0; oi < 2 && rc == LQCD_OK; ++oi) {
+        DslashArgs a;
+        a.out = out;
+        a.in = in;
+        a.prec = prec;
+        a.tps = tps_list[t];
+        a.bs = bs_list[bi];
+        a.order = order_list[oi];
+        int nl = 0;
+        for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+          a.out_parity = r & 1;
+          e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
+        }
+        const int reps = 20;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+          a.out_parity = r & 1;
+          e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          rc = cuda_check(ctx, e, "lqcd_autotune");
+          break;
+        }
+        ctx->launches += nl;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best[0] = tps_list[t];
+          best[1] = bs_list[bi];
+          best[2] = order_list[oi];
+        }
+      }
     }
   }
   if (in) cudaFree(in);
@@ -78,8 +89,17 @@ extern "C" int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (rc != LQCD_OK) return rc;
-  if (best_tps) *best_tps = best;
-  return lqcd_set_option(ctx, LQCD_OPT_DSLASH_TPS, best);
+  if (best_tps) *best_tps = best[0];
+  if (best_bs) *best_bs = best[1];
+  if (best_order) *best_order = best[2];
+  rc = lqcd_set_option(ctx, LQCD_OPT_DSLASH_TPS, best[0]);
+  if (rc == LQCD_OK) rc = lqcd_set_option(ctx, LQCD_OPT_DSLASH_BS, best[1]);
+  if (rc == LQCD_OK) rc = lqcd_set_option(ctx, LQCD_OPT_DSLASH_ORDER, best[2]);
+  return rc;
+}
+
+extern "C" int lqcd_autotune(lqcd_ctx* ctx, int prec, int* best_tps) {
+  return lqcd_autotune_shape(ctx, prec, best_tps, nullptr, nullptr);
 }
 
 extern "C" int mshift_cg_batch(lqcd_batch_problem* probs, int nprob, int nthreads) {

@@ -46,7 +46,7 @@ static bool prec_valid(int prec) {
 static int ensure_scratch(lqcd_ctx* ctx) {
   if (ctx->scalars) return LQCD_OK;
   cudaError_t e;
-  size_t nparts = (size_t)dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8) + 64;
+  size_t nparts = (size_t)dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8, 64) + 64;
   if ((e = cudaMalloc(&ctx->partials, sizeof(double) * nparts)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
   if ((e = cudaMalloc(&ctx->tickets, sizeof(unsigned) * 8)) != cudaSuccess) return cuda_check(ctx, e, "cudaMalloc");
   if ((e = cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 8, ctx->stream)) != cudaSuccess)
@@ -233,6 +233,8 @@ int dslash_eo(lqcd_ctx* ctx, void* out_dev, const void* in_dev, int out_parity, 
   a.out_parity = out_parity;
   a.prec = prec;
   a.tps = ctx->dslash_tps;
+  a.bs = ctx->dslash_bs;
+  a.order = ctx->dslash_order;
   int nl = 0;
   cudaError_t e = launch_dslash(make_geom(ctx), ctx->gauge, a, ctx->stream, &nl);
   ctx->launches += nl;
@@ -379,6 +381,8 @@ int lqcd_apply_A(lqcd_ctx* ctx, void* q_dev, const void* p_dev, double sigma, in
   a.out_parity = 1;
   a.prec = prec;
   a.tps = ctx->dslash_tps;
+  a.bs = ctx->dslash_bs;
+  a.order = ctx->dslash_order;
   int nl = 0;
   cudaError_t e = launch_dslash(g, ctx->gauge, a, ctx->stream, &nl);
   if (e != cudaSuccess) return cuda_check(ctx, e, "apply_A");
@@ -437,6 +441,14 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value) {
     case LQCD_OPT_DSLASH_TPS:
       if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return fail(ctx, LQCD_ERR_ARG, "tps must be 0,1,2,4,8");
       ctx->dslash_tps = v;
+      break;
+    case LQCD_OPT_DSLASH_BS:
+      if (v != 0 && v != 64 && v != 128) return fail(ctx, LQCD_ERR_ARG, "block size must be 0, 64 or 128");
+      ctx->dslash_bs = v;
+      break;
+    case LQCD_OPT_DSLASH_ORDER:
+      if (v != 0 && v != 1) return fail(ctx, LQCD_ERR_ARG, "site order must be 0 or 1");
+      ctx->dslash_order = v;
       break;
     default: return fail(ctx, LQCD_ERR_ARG, "unknown option");
   }

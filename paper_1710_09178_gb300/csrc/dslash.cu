@@ -36,6 +36,7 @@ struct KArgs {
   double* partials;
   unsigned* ticket;
   const void* links;
+  int order;  // block-to-site order (site_block)
 };
 
 template <int LF>
@@ -231,12 +232,24 @@ __device__ __forceinline__ uint64_t link_policy() {
   return (LF == kL64) ? policy_evict_first() : policy_evict_last();
 }
 
+// The chunk of output sites block blockIdx.x works on.  order 0: chunk b = block b (lexicographic
+// within the parity, the order of the stored vectors); order 1: the two halves of the site range
+// interleaved, even blocks taking the first half and odd blocks the second, so that blocks that run
+// at the same time stream from two distant regions of the lattice (and of every link block).  A
+// bijection on [0, gridDim.x); the per-block partial sums stay indexed by blockIdx.x.
+__device__ __forceinline__ int site_block(int order) {
+  const int b = blockIdx.x;
+  if (!order) return b;
+  const int h = (gridDim.x + 1) >> 1;
+  return (b & 1) ? h + (b >> 1) : (b >> 1);
+}
+
 template <int LF, int TPS, int EPI>
 __global__ void __launch_bounds__(128, 7) dslash_kernel(Geom g, KArgs k) {
   typedef typename LinkTraits<LF>::T T;
   typedef typename std::conditional<LF == kL64, double2, float2>::type V2;
   const int vh = g.vh;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gt = site_block(k.order) * blockDim.x + threadIdx.x;
   const int i = gt / TPS;
   const int sub = gt % TPS;
   const bool valid = i < vh;
@@ -464,9 +477,8 @@ static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream
 }
 
 template <int LF>
-static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cudaStream_t st, bool pdl) {
-  const int bs = 128;
-  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);  // FP64 is arithmetic-bound
+static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, int bs, cudaStream_t st, bool pdl) {
+  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, 128, pdl);  // FP64 is arithmetic-bound
   switch (tps) {
     case 1: return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);
     case 2: return launch_tps<LF, 2>(g, k, epi, st, bs, pdl);
@@ -478,10 +490,11 @@ static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, cu
 static int default_tps(int) { return 1; }  // fastest on GB300 at 16^3x8 and 32^3x8 (sweep over 1, 2, 4, 8)
 
 // blocks of one Dslash launch (= partials it writes): the FP64 kernel always runs 1 thread per site
-int dslash_grid_blocks(const Geom& g, int prec, int tps) {
+int dslash_grid_blocks(const Geom& g, int prec, int tps, int bs) {
   if (tps <= 0 || prec == LQCD_FP64) tps = default_tps(prec);
+  if (bs <= 0 || prec == LQCD_FP64) bs = 128;
   long long threads = (long long)g.vh * tps;
-  return (int)((threads + 127) / 128);
+  return (int)((threads + bs - 1) / bs);
 }
 
 cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs& a, cudaStream_t st, int* nlaunch) {
@@ -500,13 +513,16 @@ cudaError_t launch_dslash(const Geom& g, const GaugeCopies& gc, const DslashArgs
   k.ticket = a.ticket;
   int tps = a.tps > 0 ? a.tps : default_tps(a.prec);
   if (tps != 1 && tps != 2 && tps != 4 && tps != 8) return cudaErrorInvalidValue;
+  const int bs = a.bs > 0 ? a.bs : 128;
+  if (bs != 64 && bs != 128) return cudaErrorInvalidValue;
+  k.order = (a.prec == LQCD_FP64) ? 0 : a.order;
   if (nlaunch) *nlaunch += 1;
   switch (a.prec) {
-    case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, st, a.pdl);
-    case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, st, a.pdl);
-    case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, st, a.pdl);
-    case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, st, a.pdl);
-    default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, st, a.pdl);
+    case LQCD_FP64: k.links = gc.u64; return launch_lf<kL64>(g, k, a.epi, tps, bs, st, a.pdl);
+    case LQCD_FP32_R12: k.links = gc.u12; return launch_lf<kL12>(g, k, a.epi, tps, bs, st, a.pdl);
+    case LQCD_FP32_R8: k.links = gc.u8; return launch_lf<kL8>(g, k, a.epi, tps, bs, st, a.pdl);
+    case LQCD_FP32_L16: k.links = gc.u16; return launch_lf<kL16>(g, k, a.epi, tps, bs, st, a.pdl);
+    default: k.links = gc.u32; return launch_lf<kL32>(g, k, a.epi, tps, bs, st, a.pdl);
   }
 }
 

@@ -249,6 +249,8 @@ extern "C" int fermion_force(lqcd_ctx* ctx, const double* shifts, const double* 
       d.in = fw->x32[k];
       d.prec = LQCD_FP32;
       d.tps = ctx->dslash_tps;
+      d.bs = ctx->dslash_bs;
+      d.order = ctx->dslash_order;
       fa.x[k] = fw->x32[k];
     }
     if ((e = launch_dslash(g, ctx->gauge, d, st, &nl)) != cudaSuccess) return cuda_check(ctx, e, "fermion_force");

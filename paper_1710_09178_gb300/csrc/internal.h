@@ -114,6 +114,8 @@ struct lqcd_ctx {
   int use_pdl = 1;         // programmatic dependent launch inside captured graphs
   int df_resid = 1;        // mixed modes: residuals in double-FP32 instead of FP64
   int dslash_tps = 0;
+  int dslash_bs = 0;     // FP32 Dslash threads per block (64 or 128; 0 = 128)
+  int dslash_order = 0;  // FP32 Dslash block-to-site order (0 linear, 1 halves interleaved)
   lqcd::Workspace* ws = nullptr;
   lqcd::Workspace* ws_extra[lqcd::kMaxRhs - 1] = {};  // systems 1 .. of multi-RHS solves (mshift_cg_multi)
   lqcd::MrhsWorkspace* mrhs = nullptr;  // multi-right-hand-side refinement buffers
@@ -148,6 +150,8 @@ struct DslashArgs {
   int out_parity = 0;
   int prec = LQCD_FP32;       // link copy / vector precision
   int tps = 0;                // threads per site (FP32 paths), 0 = default
+  int bs = 0;                 // threads per block of the FP32 paths: 64 or 128 (0 = 128)
+  int order = 0;              // block-to-site order of the FP32 paths: 0 linear, 1 the two halves interleaved
   // AApply: out = a * aux - D in, dot = Re<aux, out>;  Resid: out = bvec - (a * aux - D in), dot = |out|^2
   Epi epi = Epi::Plain;
   double a = 0;
@@ -196,7 +200,7 @@ int batch_items(int vh);
 cudaError_t launch_dslash_batch(const BatchArgs& a, int prec, unsigned* head, int n_sm, cudaStream_t st);
 cudaError_t launch_dslash_batch_table(const BatchTable* dev_table, int n_items, int prec, unsigned* head, int n_sm,
                                       cudaStream_t st);
-int dslash_grid_blocks(const Geom& g, int prec, int tps);
+int dslash_grid_blocks(const Geom& g, int prec, int tps, int bs = 0);
 
 // df64.cu: residuals b - (A + sigma) x in double-FP32 arithmetic
 struct DfArgs {

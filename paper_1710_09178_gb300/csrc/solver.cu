@@ -656,7 +656,7 @@ static int alloc_workspace(lqcd_ctx* ctx, int prec, int n, Workspace** slot, cud
   LQ_CUDA(cudaMemsetAsync(w->sd, 0, sizeof(SolverDev), w->st));
   LQ_CUDA(cudaMalloc(&w->ru_count, sizeof(int)));
   // one partial per block of the widest reduction kernel
-  int nparts = std::max(dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8), (int)((vh + 127) / 128)) + 64;
+  int nparts = std::max(dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8, 64), (int)((vh + 127) / 128)) + 64;
   LQ_CUDA(cudaMalloc(&w->partials, 2 * sizeof(double) * nparts));
   w->partials_b = w->partials + nparts;
   LQ_CUDA(cudaMalloc(&w->tickets, sizeof(unsigned) * 16));
@@ -753,7 +753,10 @@ static cudaError_t enqueue_iteration(Launcher& L) {
   memset(&ra, 0, sizeof(ra));
   memset(&pa, 0, sizeof(pa));
   const int dprec = w->prec == LQCD_FP16FIX ? LQCD_FP32 : w->prec;
-  const int tps = S == 1 ? ctx->dslash_tps : 1;  // the multi-system Dslash runs one thread per site
+  // the multi-system Dslash runs one thread per site in 128-thread blocks, in linear order
+  const int tps = S == 1 ? ctx->dslash_tps : 1;
+  const int bs = S == 1 ? ctx->dslash_bs : 128;
+  const int order = S == 1 ? ctx->dslash_order : 0;
   const int nb = (L.g.vh + 255) / 256;  // streaming blocks; one more runs the scalar step
   for (int s = 0; s < S; ++s) {
     Workspace* y = L.sys(s);
@@ -763,6 +766,8 @@ static cudaError_t enqueue_iteration(Launcher& L) {
     a.out_parity = 1;
     a.prec = dprec;
     a.tps = tps;
+    a.bs = bs;
+    a.order = order;
     a.done = &y->sd->done;
     DslashArgs& b = d2.s[s];
     b = a;
@@ -781,7 +786,7 @@ static cudaError_t enqueue_iteration(Launcher& L) {
     r.slot_bytes = y->sbytes;
     r.sd = y->sd;
     r.pq_partials = y->partials;
-    r.n_pq = dslash_grid_blocks(L.g, dprec, tps);
+    r.n_pq = dslash_grid_blocks(L.g, dprec, tps, bs);
     r.rr_partials = y->partials_b;
     PUpdArgs& u = pa.s[s];
     u.r = y->r;

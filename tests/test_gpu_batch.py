@@ -73,9 +73,45 @@ def test_autotune_keeps_parity(dims):
     ctx, U = make_context(dims, 0.05, gauge_seed=70)
     best = ctx.autotune(lq.FP32)
     assert best in (1, 2, 4, 8)
+    tps, bs, order = ctx.autotune_shape(lq.FP32)
+    assert tps in (1, 2, 4, 8) and bs in (64, 128) and order in (0, 1)
     psi = inputs.gaussian_vector(dims, 71)
     for p in (0, 1):
         assert rel_max(gpu_dslash(ctx, psi, p, lq.FP32), staggered.dslash_eo(U, psi, dims, p)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", [1, 2, 4, 5])  # FP32, 12-real, 8-real, 16-bit links
+def test_every_launch_shape_matches_oracle(prec):
+    # threads per site x threads per block x block-to-site order: the half-Dslash against the oracle
+    # (element by element, ragged 10x6x4x6 lattice: V/2 = 720 sites, not a multiple of any block), the
+    # A-apply's dot product, and a converged mixed solve certified by the oracle's FP64 true residual
+    import itertools
+
+    import paper_1710_09178_gb300 as lq
+    from gpu_util import gpu_apply_A, gpu_mshift
+    from oracle import linkcomp, rational, solvers
+
+    dims, mass = (10, 6, 4, 6), 0.05
+    ctx, U = make_context(dims, mass, gauge_seed=72)
+    Ur = linkcomp.decode_l16(linkcomp.encode_l16(U.reshape(-1, 3, 3))).reshape(U.shape) if prec == 5 else U
+    psi = inputs.gaussian_vector(dims, 73)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(8, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    tol = 1e-4 if prec == 4 else 2e-6
+    for tps, bs, order in itertools.product((1, 2, 4, 8), (64, 128), (0, 1)):
+        ctx.set_option(lq.OPT_DSLASH_TPS, tps)
+        ctx.set_option(lq.OPT_DSLASH_BS, bs)
+        ctx.set_option(lq.OPT_DSLASH_ORDER, order)
+        for p in (0, 1):
+            got = gpu_dslash(ctx, psi, p, prec)
+            assert rel_max(got, staggered.dslash_eo(Ur, psi, dims, p)) < tol, (tps, bs, order, p)
+        q, pq = gpu_apply_A(ctx, psi, 0.2, prec)
+        ref = staggered.A_apply(Ur, psi, mass, dims, 0.2)
+        assert abs(pq - np.real(np.vdot(psi, ref))) <= tol * abs(pq), (tps, bs, order)
+        if (tps, bs, order) in ((8, 64, 1), (2, 128, 1)):
+            rc, st, xs, _ = gpu_mshift(ctx, psi, poles, prec=prec)
+            assert rc == 0
+            tr = solvers.true_residuals(lambda v, s: staggered.A_apply(U, v, mass, dims, s), psi, xs, poles)
+            assert np.all(tr <= 1e-10)
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 4, 5])  # FP64, FP32, 12-real, 8-real, 16-bit links
