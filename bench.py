@@ -733,6 +733,7 @@ def run_profile_target(kind, prec_name):
     `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
     then 6 replays of the graph: 592 launches),
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch,
+    `solve_graph` = two solves with CUDA graphs on (the second is the timed configuration),
     `multi` = the same for four sources solved together (mshift_cg_multi)."""
     import torch
 
@@ -754,6 +755,17 @@ def run_profile_target(kind, prec_name):
         vin.view(torch.float32 if prec != lq.FP64 else torch.float64).normal_()
         for r in range(8):
             lq.dslash_eo(ctx, vout, vin, r & 1, prec)
+    elif kind == "solve_graph":
+        # two solves with CUDA graphs on (the first captures the graph): the second one's kernel nodes
+        # are what the timed solve runs
+        b = torch.from_numpy(inputs.gaussian_vector(DIMS, VEC_SEED)).cuda()
+        c0, res, poles, _ = lq.rational_coeffs(-0.5, 4 * MASS * MASS, 16 + 4 * MASS * MASS, NPOLES)
+        xs = [torch.empty_like(b) for _ in range(NPOLES)]
+        y = torch.empty_like(b)
+        for _ in range(2):
+            rc, st = lq.mshift_cg(ctx, poles, res, c0, b, xs, y, tol=TOL, prec=prec)
+        print(json.dumps({"profile": "solve_graph", "rc": rc, "iterations": st["iterations"],
+                          "refine_iterations": st["refine_iterations"], "launches_per_solve": st["kernel_launches"]}))
     elif kind == "multi":
         # four sources solved together (mshift_cg_multi), graphs off
         ctx.set_option(lq.OPT_USE_GRAPH, 0)
@@ -784,7 +796,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
-    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve", "multi"],
+    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve", "solve_graph", "multi"],
                     help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")

@@ -98,7 +98,7 @@ int lqcd_destroy(lqcd_ctx* ctx) {
   traj_release(ctx);
   if (ctx->gauge.owned) {
     void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16,
-                 ctx->gauge.u32lo, ctx->gauge.lo16};
+                 ctx->gauge.u32lo};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -139,7 +139,7 @@ int lqcd_share_gauge(lqcd_ctx* ctx, const lqcd_ctx* src) {
   if (!src->gauge.loaded) return fail(ctx, LQCD_ERR_STATE, "lqcd_share_gauge: source has no gauge field");
   if (ctx->gauge.owned) {
     void* g[] = {ctx->gauge.u64, ctx->gauge.u32, ctx->gauge.u12, ctx->gauge.u8, ctx->gauge.u16,
-                 ctx->gauge.u32lo, ctx->gauge.lo16};
+                 ctx->gauge.u32lo};
     for (void* b : g)
       if (b) cudaFree(b);
   }
@@ -169,8 +169,6 @@ int lqcd_set_gauge(lqcd_ctx* ctx, const double* U_dev) {
     return cuda_check(ctx, e, "cudaMalloc(gauge l16)");
   if (!gc.u32lo && (e = cudaMalloc(&gc.u32lo, 2 * 4 * 18 * vh * sizeof(float))) != cudaSuccess)
     return cuda_check(ctx, e, "cudaMalloc(gauge fp32 rounding errors)");
-  if (!gc.lo16 && (e = cudaMalloc(&gc.lo16, 2 * 4 * 18 * vh * sizeof(short))) != cudaSuccess)
-    return cuda_check(ctx, e, "cudaMalloc(gauge 16-bit rounding errors)");
   e = launch_pack_gauge(g, reinterpret_cast<const double2*>(U_dev), gc, ctx->stream);
   ctx->launches += 1;
   if (e != cudaSuccess) return cuda_check(ctx, e, "pack_gauge");

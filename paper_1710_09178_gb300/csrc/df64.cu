@@ -48,41 +48,6 @@ __device__ __forceinline__ double block_sum_df(float s, float c) {
 
 __device__ __forceinline__ float2 split64(double a) { return split_hi_lo(a); }
 
-__device__ __forceinline__ int ld_stream(const int* p, uint64_t pol) {
-  int r;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
-  return r;
-}
-
-// the two int16 halves of a 32-bit word (low half first, as stored)
-__device__ __forceinline__ float lo_half(int w) { return (float)((w << 16) >> 16); }
-__device__ __forceinline__ float hi_half(int w) { return (float)(w >> 16); }
-
-// the int16 rounding-error copy of a link (GaugeCopies::lo16, the layout of the FP32 copy with int16
-// entries): entries q * 2^-40
-__device__ __forceinline__ Mat3<float> load_link_lo16(const short* __restrict__ U, int p, int mu, int i, int vh,
-                                                      uint64_t pol) {
-  const short* blk = U + (size_t)(p * 4 + mu) * 18 * vh;
-  const int2* s4 = reinterpret_cast<const int2*>(blk);              // 4 entries (8 bytes) per site and group
-  const int* s2 = reinterpret_cast<const int*>(blk + 16 * (size_t)vh);  // the last 2 entries (4 bytes)
-  const float sc = 9.094947017729282e-13f;  // 2^-40, exact in FP32
-  const int2 a = ld_stream(s4 + i, pol), b = ld_stream(s4 + vh + i, pol), c = ld_stream(s4 + 2 * vh + i, pol),
-             d = ld_stream(s4 + 3 * vh + i, pol);
-  const int e = ld_stream(s2 + i, pol);
-  Mat3<float> M;
-  M.e[0][0] = cmake(sc * lo_half(a.x), sc * hi_half(a.x));
-  M.e[0][1] = cmake(sc * lo_half(a.y), sc * hi_half(a.y));
-  M.e[0][2] = cmake(sc * lo_half(b.x), sc * hi_half(b.x));
-  M.e[1][0] = cmake(sc * lo_half(b.y), sc * hi_half(b.y));
-  M.e[1][1] = cmake(sc * lo_half(c.x), sc * hi_half(c.x));
-  M.e[1][2] = cmake(sc * lo_half(c.y), sc * hi_half(c.y));
-  M.e[2][0] = cmake(sc * lo_half(d.x), sc * hi_half(d.x));
-  M.e[2][1] = cmake(sc * lo_half(d.y), sc * hi_half(d.y));
-  M.e[2][2] = cmake(sc * lo_half(e), sc * hi_half(e));
-  return M;
-}
-
-
 // x (FP64) -> (hi, lo) FP32 pairs
 __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __restrict__ x, float2* __restrict__ hi,
                                                         float2* __restrict__ lo, const int* done) {
@@ -100,7 +65,7 @@ __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __
 // EPI 0: out = D in (hi, lo);  EPI 1: out = a x - D in and Re<x, out> (the A-apply; inside the
 // solve, without a ticket, the sum stays as per-block (hi, lo) partials for the r update);
 // EPI 2: r_out = fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
-template <int EPI, bool LO16>
+template <int EPI>
 __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_constant__ PerSys<DfArgs> pk) {
   const DfArgs& k = pk.s[blockIdx.y];  // system blockIdx.y
   const int vh = g.vh;
@@ -124,8 +89,7 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_
       const int lp = fwd ? p : 1 - p;
       const int li = fwd ? i : j;
       const Mat3<float> Uh = load_link32(k.links_hi, lp, mu, li, vh, pol_hi);
-      const Mat3<float> Ul = LO16 ? load_link_lo16(k.links_lo16, lp, mu, li, vh, pol_lo)
-                                  : load_link32(k.links_lo, lp, mu, li, vh, pol_lo);
+      const Mat3<float> Ul = load_link32(k.links_lo, lp, mu, li, vh, pol_lo);
       const Vec3<float> vh3 = ldg_vec(k.in_hi, j, vh), vl3 = ldg_vec(k.in_lo, j, vh);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -231,14 +195,9 @@ int df_dslash_grid_blocks(const Geom& g) { return (g.vh + 127) / 128; }
 
 cudaError_t launch_df_dslash_multi(const Geom& g, const PerSys<DfArgs>& a, int S, int epi, cudaStream_t st, bool pdl) {
   const dim3 grid((unsigned)df_dslash_grid_blocks(g), (unsigned)S);
-  if (a.s[0].links_lo16) {  // the 16-bit rounding-error links (the double-FP32 phase of the mixed solves)
-    if (epi == 2) return launch_k(pdl, df_dslash_kernel<2, true>, grid, dim3(128), st, g, a);
-    if (epi == 1) return launch_k(pdl, df_dslash_kernel<1, true>, grid, dim3(128), st, g, a);
-    return launch_k(pdl, df_dslash_kernel<0, true>, grid, dim3(128), st, g, a);
-  }
-  if (epi == 2) return launch_k(pdl, df_dslash_kernel<2, false>, grid, dim3(128), st, g, a);
-  if (epi == 1) return launch_k(pdl, df_dslash_kernel<1, false>, grid, dim3(128), st, g, a);
-  return launch_k(pdl, df_dslash_kernel<0, false>, grid, dim3(128), st, g, a);
+  if (epi == 2) return launch_k(pdl, df_dslash_kernel<2>, grid, dim3(128), st, g, a);
+  if (epi == 1) return launch_k(pdl, df_dslash_kernel<1>, grid, dim3(128), st, g, a);
+  return launch_k(pdl, df_dslash_kernel<0>, grid, dim3(128), st, g, a);
 }
 
 cudaError_t launch_df_dslash(const Geom& g, const DfArgs& a, int epi, cudaStream_t st, bool pdl) {

@@ -87,8 +87,6 @@ struct GaugeCopies {
   float4* u8 = nullptr;    // [2][4][2][Vh] float4, 8-real form, no sign
   char* u16 = nullptr;     // [2][4] { int4 [Vh]; int2 [Vh] }, int16 codes of rows 0-1, no sign
   float* u32lo = nullptr;  // as u32: fl32(1/2 eta bc U - u32), the FP32 rounding errors (double-FP32 residuals)
-  short* lo16 = nullptr;   // as u32, int16 codes rint(2^40 (1/2 eta bc U - u32)) of those errors (the double-FP32
-                           // phase of the mixed solves: the link pair to ~5e-13 in 108 instead of 144 bytes)
   bool loaded = false;
   bool owned = true;       // false when borrowed from another context (lqcd_share_gauge)
 };
@@ -208,7 +206,6 @@ int dslash_grid_blocks(const Geom& g, int prec, int tps, int bs = 0);
 struct DfArgs {
   const float* links_hi = nullptr;  // GaugeCopies::u32
   const float* links_lo = nullptr;  // GaugeCopies::u32lo
-  const short* links_lo16 = nullptr;  // GaugeCopies::lo16: used instead of links_lo when set
   const float2* in_hi = nullptr;    // input vector (other parity) as (hi, lo)
   const float2* in_lo = nullptr;
   float2* out_hi = nullptr;         // plain: D in as (hi, lo)

@@ -27,7 +27,7 @@ __device__ __forceinline__ int pack_codes(double re, double im) {
 // One thread per (site, mu): canonical complex128 [V][4][3][3] -> five internal copies.
 __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2* __restrict__ u64,
                                   float* __restrict__ u32, float4* __restrict__ u12, float4* __restrict__ u8,
-                                  char* __restrict__ u16, float* __restrict__ u32lo, short* __restrict__ lo16) {
+                                  char* __restrict__ u16, float* __restrict__ u32lo) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long V = 2LL * g.vh;
   if (t >= 4 * V) return;
@@ -69,21 +69,6 @@ __global__ void pack_gauge_kernel(Geom g, const double2* __restrict__ U, double2
       f4[(size_t)q * vh + i] = make_float4(lo(e[2 * q].x), lo(e[2 * q].y), lo(e[2 * q + 1].x), lo(e[2 * q + 1].y));
     f2[i] = make_float2(lo(e[8].x), lo(e[8].y));
   }
-  if (lo16) {
-    // the same rounding errors (|d| <= 2^-25: the links carry the 1/2) as int16 fixed point, step 2^-40
-    short* blk = lo16 + (size_t)(p * 4 + mu) * 18 * vh;
-    short4* s4 = reinterpret_cast<short4*>(blk);
-    short2* s2 = reinterpret_cast<short2*>(blk + 16 * (size_t)vh);
-    float hs = (float)half_sign;
-    auto q = [&](double v) {
-      const double d = (half_sign * v - (double)(hs * (float)v)) * 1099511627776.0;  // 2^40
-      return (short)fmax(-32767.0, fmin(32767.0, rint(d)));
-    };
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      s4[(size_t)k * vh + i] = make_short4(q(e[2 * k].x), q(e[2 * k].y), q(e[2 * k + 1].x), q(e[2 * k + 1].y));
-    s2[i] = make_short2(q(e[8].x), q(e[8].y));
-  }
   if (u12) {
     float4* blk = u12 + (size_t)(p * 4 + mu) * 3 * vh;
 #pragma unroll
@@ -117,7 +102,7 @@ cudaError_t launch_pack_gauge(const Geom& g, const double2* U, GaugeCopies& gc, 
   long long n = 8LL * g.vh;  // 4 V threads
   int bs = 256;
   long long nb = (n + bs - 1) / bs;
-  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12, gc.u8, gc.u16, gc.u32lo, gc.lo16);
+  pack_gauge_kernel<<<(unsigned)nb, bs, 0, st>>>(g, U, gc.u64, gc.u32, gc.u12, gc.u8, gc.u16, gc.u32lo);
   return cudaGetLastError();
 }
 

@@ -844,10 +844,6 @@ static cudaError_t enqueue_iteration_df(Launcher& L, bool phase) {
     DfArgs& x = d.s[s];
     x.links_hi = ctx->gauge.u32;
     x.links_lo = ctx->gauge.u32lo;
-    // the mixed solves' double-FP32 phase needs the links to ~5e-13, not to the last of the 48 bits
-    // (its errors enter the solutions scaled by |r| / |b| <= 1 and its end is at 1e-3): the 16-bit copy
-    // of the FP32 rounding errors; LQCD_DF64 solves and all residual checks keep the FP32 copy
-    if (phase) x.links_lo16 = ctx->gauge.lo16;
     x.in_hi = hi(B.p);
     x.in_lo = lo(B.p);
     x.out_hi = hi(B.tmp);
