@@ -35,6 +35,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# hardware work queues for the concurrent solve graphs of the batch workload (the CUDA runtime default
+# of 8 serialises the streams of more than 8 concurrent solves onto 8 queues); read when the process
+# creates its CUDA context, a per-process setting
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "multishift-CG time/solve to 1e-10, mixed vs FP64 at 32^3x8; Dslash % HBM peak"
 WORKLOAD = "32^3x8"
@@ -488,7 +492,7 @@ C4_VOLUMES = [(8, 8, 8, 8), (12, 12, 12, 4), (16, 16, 16, 4), (16, 16, 16, 8)]
 C4_MASSES = [0.02, 0.05, 0.1]
 
 
-def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=32, autotune=True):
+def run_batch(lq, torch, n_lat=64, n_pf=4, npoles=12, nthreads=16, autotune=True):
     """64 independent lattices (sizes and masses drawn uniformly, seed 7), 4 Gaussian pseudofermions
     each, 12-pole x^{-1/2} shifted CG to 1e-10 in FP32 mode: sequential vs mshift_cg_batch."""
     from paper_1710_09178_gb300 import inputs

@@ -707,16 +707,39 @@ __device__ __forceinline__ bool publish_partial(double* partials, unsigned* tick
   return last;
 }
 
-// One warp: the sum of n double-FP32 partials p[0..n) in a fixed order (each lane accumulates
-// p[lane], p[lane + 32], ... with TwoSum, then a shuffle tree), on the FP32 pipes.  The value is
+// One warp: the sum of n double-FP32 partials p[0..n) in a fixed order, on the FP32 pipes.  Lane l
+// keeps four TwoSum accumulators, accumulator j taking p[l + 32 (4 i + j)]: each round issues four
+// independent loads before it adds, so the lane waits for one L2 round trip per four partials
+// instead of one per partial; the four are combined in order, then a shuffle tree.  The value is
 // that of lane 0; the other lanes may differ in the last bits.
 __device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
   const int lane = threadIdx.x & 31;
-  float s = 0.f, c = 0.f;
-  for (int b = lane; b < n; b += 32) {
-    const float2 x = __ldcg(p + b);
-    df_add(s, c, x.x, x.y);
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
+  int b = lane;
+  for (; b + 96 < n; b += 128) {
+    const float2 x0 = __ldcg(p + b), x1 = __ldcg(p + b + 32), x2 = __ldcg(p + b + 64), x3 = __ldcg(p + b + 96);
+    df_add(s0, c0, x0.x, x0.y);
+    df_add(s1, c1, x1.x, x1.y);
+    df_add(s2, c2, x2.x, x2.y);
+    df_add(s3, c3, x3.x, x3.y);
   }
+  // fewer than four rounds left (b + 96 >= n)
+  if (b < n) {
+    const float2 x = __ldcg(p + b);
+    df_add(s0, c0, x.x, x.y);
+  }
+  if (b + 32 < n) {
+    const float2 x = __ldcg(p + b + 32);
+    df_add(s1, c1, x.x, x.y);
+  }
+  if (b + 64 < n) {
+    const float2 x = __ldcg(p + b + 64);
+    df_add(s2, c2, x.x, x.y);
+  }
+  float s = s0, c = c0;
+  df_add(s, c, s1, c1);
+  df_add(s, c, s2, c2);
+  df_add(s, c, s3, c3);
   float2 v = df_norm(s, c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -749,9 +772,21 @@ __device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, 
     if constexpr (DF) {
       v = warp_sum_df(reinterpret_cast<const float2*>(partials), n);
     } else {
-      v = 0.0;
-      for (int b = threadIdx.x; b < n; b += 32) v += __ldcg(partials + b);
-      v = warp_sum(v);
+      // four independent FP64 accumulators per lane (loads of four rounds in flight), combined in order
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int b = threadIdx.x;
+      for (; b + 96 < n; b += 128) {
+        const double x0 = __ldcg(partials + b), x1 = __ldcg(partials + b + 32), x2 = __ldcg(partials + b + 64),
+                     x3 = __ldcg(partials + b + 96);
+        v0 += x0;
+        v1 += x1;
+        v2 += x2;
+        v3 += x3;
+      }
+      if (b < n) v0 += __ldcg(partials + b);
+      if (b + 32 < n) v1 += __ldcg(partials + b + 32);
+      if (b + 64 < n) v2 += __ldcg(partials + b + 64);
+      v = warp_sum(((v0 + v1) + v2) + v3);
     }
     if (threadIdx.x == 0) {
       const double q = SUM_OVER_X ? v / *x : *x / v;
