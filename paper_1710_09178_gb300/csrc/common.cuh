@@ -752,49 +752,103 @@ __device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
 }
 
 // Every block of the kernel that follows the one that wrote the n partials (one per block, no
-// ticket): warp 0 sums them in a fixed order, and thread 0 forms ratio = *x / sum (SUM_OVER_X
-// false) or sum / *x (true) with its FP32 and (hi, lo) copies.  The result reaches every thread
-// through shared memory, the same bits in every block; the FP64 work stays in one warp per block
-// (GB300's FP64 pipe is 1/64 of the FP32 rate).  DF: the partials are double-FP32 pairs (hi, lo)
-// in the 8 bytes of each entry, added on the FP32 pipes (warp_sum_df; the FP32 and double-FP32
-// solves), else FP64 values added in FP64.
+// ticket) sums them and forms ratio = *x / sum (SUM_OVER_X false) or sum / *x (true) with its FP32
+// and (hi, lo) copies.  All threads of the block take part so that every load is in flight at once
+// (one L2 round trip instead of a chain of them): thread t adds the entries t, t + T, t + 2T, ...
+// (T = blockDim.x) in that order, the warps combine their threads' sums in a fixed shuffle tree,
+// and warp 0 combines the warps' sums in the same tree; thread 0 divides (FP64, once per block).
+// The order depends only on n and blockDim.x, so every block of a launch gets the same bits.  DF:
+// the partials are double-FP32 pairs (hi, lo) in the 8 bytes of each entry, added with TwoSum on
+// the FP32 pipes (the FP32 and double-FP32 solves; GB300's FP64 pipe is 1/64 of the FP32 rate),
+// else FP64 values added in FP64.
+// x: the numerator (denominator) value, loaded by the caller together with its other loads, so
+// that the division waits for no further round trip to memory.  skip: this thread read a stop
+// flag (the solve is done, or its phase is over).  The flag may be set by another block of the
+// same launch while the block reads it, so the threads may disagree; the first barrier ORs their
+// readings (stop, the same in every thread) and a stopped block returns before any other barrier.
+// The partials are loaded whatever the flag says (they are always in bounds), so that no load
+// waits for the flag.
 struct PartialsRatio {
   double sum, ratio;
   float ratio_f;
   float2 ratio_df;
+  int stop;
 };
 
+// (hi, lo) pair combined over the 32 lanes of a warp in a fixed tree; valid in lane 0
+__device__ __forceinline__ float2 warp_tree_df(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, v.x, o), ol = __shfl_down_sync(0xffffffffu, v.y, o);
+    float s = v.x, c = v.y;
+    df_add(s, c, oh, ol);
+    v = df_norm(s, c);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_tree64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <bool SUM_OVER_X, bool DF>
-__device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, int n, const double* x) {
+__device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, int n, double x, bool skip = false) {
   __shared__ PartialsRatio res;
-  if (threadIdx.x < 32) {
-    double v;
-    if constexpr (DF) {
-      v = warp_sum_df(reinterpret_cast<const float2*>(partials), n);
-    } else {
-      // four independent FP64 accumulators per lane (loads of four rounds in flight), combined in order
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-      int b = threadIdx.x;
-      for (; b + 96 < n; b += 128) {
-        const double x0 = __ldcg(partials + b), x1 = __ldcg(partials + b + 32), x2 = __ldcg(partials + b + 64),
-                     x3 = __ldcg(partials + b + 96);
-        v0 += x0;
-        v1 += x1;
-        v2 += x2;
-        v3 += x3;
-      }
-      if (b < n) v0 += __ldcg(partials + b);
-      if (b + 32 < n) v1 += __ldcg(partials + b + 32);
-      if (b + 64 < n) v2 += __ldcg(partials + b + 64);
-      v = warp_sum(((v0 + v1) + v2) + v3);
+  __shared__ double wsum[32];
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
+  constexpr int kLoads = 4;  // loads per thread issued before the adds of a round
+  if constexpr (DF) {
+    const float2* p = reinterpret_cast<const float2*>(partials);
+    float s = 0.f, c = 0.f;
+    for (int b = t; b < n; b += kLoads * nt) {
+      float2 v[kLoads];
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) v[j] = (b + j * nt < n) ? __ldcg(p + b + j * nt) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) df_add(s, c, v[j].x, v[j].y);
     }
-    if (threadIdx.x == 0) {
-      const double q = SUM_OVER_X ? v / *x : *x / v;
-      res.sum = v;
-      res.ratio = q;
-      res.ratio_df = split_hi_lo(q);
-      res.ratio_f = res.ratio_df.x;
+    const float2 w = warp_tree_df(df_norm(s, c));
+    if (lane == 0) reinterpret_cast<float2*>(wsum)[warp] = w;
+    if (__syncthreads_or(skip)) {
+      PartialsRatio r{};
+      r.stop = 1;
+      return r;
     }
+    if (warp == 0) {
+      const float2 u = warp_tree_df(lane < nw ? reinterpret_cast<const float2*>(wsum)[lane] : make_float2(0.f, 0.f));
+      if (lane == 0) wsum[0] = (double)u.x + (double)u.y;
+    }
+  } else {
+    double s = 0.0;
+    for (int b = t; b < n; b += kLoads * nt) {
+      double v[kLoads];
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) v[j] = (b + j * nt < n) ? __ldcg(partials + b + j * nt) : 0.0;
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) s += v[j];
+    }
+    const double w = warp_tree64(s);
+    if (lane == 0) wsum[warp] = w;
+    if (__syncthreads_or(skip)) {
+      PartialsRatio r{};
+      r.stop = 1;
+      return r;
+    }
+    if (warp == 0) {
+      const double u = warp_tree64(lane < nw ? wsum[lane] : 0.0);
+      if (lane == 0) wsum[0] = u;
+    }
+  }
+  if (t == 0) {
+    const double v = wsum[0];
+    const double q = SUM_OVER_X ? v / x : x / v;
+    res.sum = v;
+    res.ratio = q;
+    res.ratio_df = split_hi_lo(q);
+    res.ratio_f = res.ratio_df.x;
+    res.stop = 0;
   }
   __syncthreads();
   return res;

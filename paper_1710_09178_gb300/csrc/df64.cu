@@ -242,14 +242,29 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __gri
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
-  if (*reinterpret_cast<const volatile int*>(&sd->done)) return;  // the scalar block may set it meanwhile
-  if (a.halt && *a.halt) return;
+  // the scalar block may set done meanwhile: partials_ratio settles the block on one reading
+  const int dn = *reinterpret_cast<const volatile int*>(&sd->done), ht = a.halt ? *a.halt : 0;  // both in flight
+  const bool skip = (dn | ht) != 0;
   const int m = sd->m;
+  const double rr = sd->rr;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
-  const bool mine = !scalar_block && i < vh && m < kWindow;
-  const PartialsRatio pa = partials_ratio<false, true>(a.pq_partials, a.n_pq, &sd->rr);
+  const bool site = !scalar_block && i < vh;
+  float2 rv[4][3];  // r hi, r lo, q hi, q lo: issued before the partials are summed
+  if (site) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
+      rv[0][c] = a.r[o];
+      rv[1][c] = a.r[ol];
+      rv[2][c] = a.q[o];
+      rv[3][c] = a.q[ol];
+    }
+  }
+  const PartialsRatio pa = partials_ratio<false, true>(a.pq_partials, a.n_pq, rr, skip);
+  if (pa.stop) return;  // the same in every thread of the block
+  const bool mine = site && m < kWindow;
   if (scalar_block) {
     solver_alpha_step(sd, pa);
     return;
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __gri
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
-      const float2 rh = a.r[o], rl = a.r[ol], qh = a.q[o], ql = a.q[ol];
+      const float2 rh = rv[0][c], rl = rv[1][c], qh = rv[2][c], ql = rv[3][c];
       float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
       df_mac(rs, rc, -al.x, -al.y, qh.x, ql.x);
       df_mac(is, ic, -al.x, -al.y, qh.y, ql.y);
@@ -286,22 +301,36 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, const __gri
   pdl_wait();
   pdl_trigger();
   SolverDev* sd = a.sd;
-  if (*reinterpret_cast<const volatile int*>(&sd->done)) return;
-  if (a.halt && *a.halt) return;
+  const int dn = *reinterpret_cast<const volatile int*>(&sd->done), ht = a.halt ? *a.halt : 0;  // both in flight
+  const bool skip = (dn | ht) != 0;
+  const double rr_b = sd->rr_b;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
-  const PartialsRatio pb = partials_ratio<true, true>(a.rr_partials, (int)gridDim.x - 1, &sd->rr_b);
+  const bool mine = !scalar_block && i < vh;
+  float2 rv[4][3];  // r hi, r lo, p hi, p lo: issued before the partials are summed
+  if (mine) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
+      rv[0][c] = a.r[o];
+      rv[1][c] = a.r[ol];
+      rv[2][c] = a.p[o];
+      rv[3][c] = a.p[ol];
+    }
+  }
+  const PartialsRatio pb = partials_ratio<true, true>(a.rr_partials, (int)gridDim.x - 1, rr_b, skip);
+  if (pb.stop) return;  // the same in every thread of the block
   if (scalar_block) {
     solver_beta_step(sd, pb);
     return;
   }
-  if (i >= vh) return;
+  if (!mine) return;
   const float2 be = pb.ratio_df;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const size_t o = (size_t)c * vh + i, ol = o + 3 * (size_t)vh;
-    const float2 rh = a.r[o], rl = a.r[ol], ph = a.p[o], pl = a.p[ol];
+    const float2 rh = rv[0][c], rl = rv[1][c], ph = rv[2][c], pl = rv[3][c];
     float rs = rh.x, rc = rl.x, is = rh.y, ic = rl.y;
     df_mac(rs, rc, be.x, be.y, ph.x, pl.x);
     df_mac(is, ic, be.x, be.y, ph.y, pl.y);
@@ -404,6 +433,7 @@ __global__ void __launch_bounds__(128) df_flush_kernel(Geom g, const __grid_cons
       sd->wactive[t] = sd->active[t];
     }
     if (t == 0) {
+      advance_window_scalars(sd, m);
       sd->m = 0;
       sd->first = 0;
     }

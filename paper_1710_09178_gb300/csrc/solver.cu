@@ -120,7 +120,8 @@ struct RUpdArgs {
 // Every block derives alpha (beta) from the same partials in the same order, so all blocks use
 // the bits the step stores.
 __device__ __forceinline__ bool done_now(const SolverDev* sd) {
-  // the scalar block of the running kernel may set the flag concurrently; either value is fine
+  // the scalar block of the running kernel may set the flag concurrently: either value is fine
+  // for the block, which settles on one reading for all its threads (partials_ratio's stop)
   return *reinterpret_cast<const volatile int*>(&sd->done) != 0;
 }
 
@@ -132,18 +133,23 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, const __grid_c
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
-  if (done_now(sd)) return;
+  // every load of the block is issued before any of them is used: the flags, |r|^2, the site's
+  // vectors (they do not depend on alpha) and, in partials_ratio, the partials
+  const bool skip = done_now(sd);
   const int m = sd->m;
+  const double rr = sd->rr;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
-  const bool mine = !scalar_block && i < g.vh && m < kWindow;
+  const bool site = !scalar_block && i < g.vh;
   Vec3<T> r, q;
-  if (mine) {  // issued before the partials are summed: they do not depend on alpha
+  if (site) {
     r = load_vec(static_cast<const V2*>(a.r), i, g.vh);
     q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
   }
   // Re<p, q> and alpha = |r|^2 / Re<p, q>
-  const PartialsRatio pa = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, &sd->rr);
+  const PartialsRatio pa = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, rr, skip);
+  if (pa.stop) return;  // the same in every thread of the block
+  const bool mine = site && m < kWindow;
   if (scalar_block) {
     solver_alpha_step(sd, pa);
     return;
@@ -181,7 +187,8 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, const __grid_c
   SolverDev* sd = a.sd;
   pdl_wait();
   pdl_trigger();
-  if (done_now(sd)) return;
+  const bool skip = done_now(sd);
+  const double rr_b = sd->rr_b;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
   const bool mine = !scalar_block && i < g.vh;
@@ -191,7 +198,8 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, const __grid_c
     p = load_vec(static_cast<const V2*>(a.p), i, g.vh);
   }
   // |r_new|^2 and beta = |r_new|^2 / |r|^2
-  const PartialsRatio pb = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, &sd->rr_b);
+  const PartialsRatio pb = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, rr_b, skip);
+  if (pb.stop) return;  // the same in every thread of the block
   if (scalar_block) {
     solver_beta_step(sd, pb);
     return;
@@ -315,17 +323,19 @@ __global__ void __launch_bounds__(128) flush_kernel(Geom g, const __grid_constan
       sd->wactive[t] = sd->active[t];
     }
     if (t == 0) {
+      advance_window_scalars(sd, m);
       sd->m = 0;
       sd->first = 0;
     }
   }
 }
 
-// Per-shift recurrences of the pending window (one warp), right before the window update.
+// Per-shift recurrences of the pending window, right before the window update: block (k, s) is
+// shift k of system s.
 __global__ void window_scalars_kernel(const __grid_constant__ PerSys<SolverDev*> sds) {
   pdl_wait();
   pdl_trigger();
-  window_scalars(sds.s[blockIdx.y]);  // one block of 32 per system
+  window_scalars_shift(sds.s[blockIdx.y], blockIdx.x);
 }
 
 // Precision schedule of the mixed modes.  The error that FP32 arithmetic (links, Krylov vectors)
@@ -895,7 +905,7 @@ static cudaError_t enqueue_flush(Launcher& L, int n, bool df_phase = false) {
   Workspace* w = L.w;
   const int S = L.S;
   cudaError_t e =
-      launch_k(L.next_pdl(), window_scalars_kernel, dim3(1, S), dim3(32), w->st, solver_states(L));
+      launch_k(L.next_pdl(), window_scalars_kernel, dim3(n, S), dim3(32), w->st, solver_states(L));
   L.nlaunch += 1;
   if (e != cudaSuccess) return e;
   if (df_phase || w->sfmt == kSDF) {

@@ -9,7 +9,7 @@
 //   beta step (needs (r,r) new): beta = (r,r)_new/(r,r);  beta_k = beta (zeta_k'/zeta_k)^2;
 //       p_k = zeta_k' r_new + beta_k p_k;  stop shift k once zeta_k'^2 (r,r)_new <= tol^2 (b,b);
 //       and decide whether a reliable update is due at the end of the window
-// (the zeta_k parts of both steps are deferred to the window end, window_scalars())
+// (the zeta_k parts of both steps are deferred to the window end, window_scalars_shift())
 // The x_k and p_k updates are not applied vector by vector: they are folded into
 // the coefficients of the pending window,
 //   p_k = P p_k0 + sum_i pi_i R_i,   x_k = x_k0 + X p_k0 + sum_i chi_i R_i,
@@ -85,7 +85,7 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
 // The base iteration needs only alpha and beta; the per-shift recurrences (zeta_k, the window
 // coefficients, the stopping tests of the shifts) depend on nothing but the sequence of alpha and
 // beta.  So the two steps below store the base scalars of the iteration and decide the base
-// stopping test, and window_scalars() replays the per-shift recurrences of the whole window once,
+// stopping test, and window_scalars_shift() replays the per-shift recurrences of the whole window once,
 // before the window update, with the same operations in the same order as an iteration-by-iteration
 // evaluation.  The base shift stops last: for s_k >= 0, |zeta_k| <= 1 (zeta_k is the inverse of the
 // base residual polynomial at -s_k), and zeta_0 = 1 exactly, so "every shift has stopped" is "the
@@ -146,8 +146,11 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRa
   sd->ru_skip = (done || !due) ? 1 : 0;
 }
 
-// Per-shift recurrences of the pending window's m iterations, replayed from alpha_h, beta_h, rr_h;
-// one warp, lane k owns shift k.  Iteration j (alpha = alpha_h[j], beta = beta_h[j]):
+// Per-shift recurrences of the pending window's m iterations for shift k, replayed from alpha_h,
+// beta_h, rr_h; one warp per shift (one block per shift, so the shifts' FP64 chains run on
+// different SMs: GB300's FP64 pipe is narrow), lane i owns the window coefficients pi_i, chi_i of
+// the shift and every lane evaluates the shift's scalar chain (the same bits in every lane).
+// Iteration j (alpha = alpha_h[j], beta = beta_h[j]):
 //   alpha part:  den = alpha beta_prev (zeta_prev - zeta) + zeta_prev alpha_prev (1 + s_k alpha)
 //                q = zeta_prev alpha_prev / den,  zeta' = zeta q,  alpha_k = alpha q
 //                x_k += alpha_k p_k    ->  X += alpha_k P,  chi_i += alpha_k pi_i  (i < j)
@@ -155,84 +158,75 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRa
 //                p_k = zeta' r_j+1 + beta_k p_k  ->  P *= beta_k, pi_i *= beta_k (i < j), pi_j = zeta'
 //                shift k stops once zeta'^2 |r_j+1|^2 <= tol^2 |b|^2 (then takes no later residual)
 // (zeta' = zeta zeta_prev alpha_prev / den, formed as zeta q: one FP64 division.)
-__device__ __forceinline__ void window_scalars(SolverDev* sd) {
+// The statistics are integer atomics (the same totals in any order): the shift's active iterations
+// go to shift_iters, and a shift that stops takes itself off n_active.  alpha_prev and beta_prev are
+// read here and advanced by the window update that follows (its last block), so no block of this
+// launch sees another's write.
+__device__ __forceinline__ void window_scalars_shift(SolverDev* sd, int k) {
   if (threadIdx.x >= 32) return;
-  const int k = threadIdx.x;
+  const int lane = threadIdx.x;
   const int n = sd->n, m = sd->m;
+  if (k >= n || !sd->active[k]) return;  // uniform: a stopped shift keeps its state
   const double stop2 = sd->stop2;
   double ap = sd->alpha_prev, bp = sd->beta_prev;
-  const bool mine = k < n;
-  const int act0 = mine ? sd->active[k] : 0;
-  int act = act0;
-  double z = 1.0, zp = 1.0, sk = 0.0, P = 0.0, X = 0.0, pi[kWindow], chi[kWindow];
-  if (act) {
-    z = sd->zeta[k];
-    zp = sd->zeta_prev[k];
-    sk = sd->s[k];
-    P = sd->P[k];
-    X = sd->X[k];
-  }
-#pragma unroll
-  for (int i = 0; i < kWindow; ++i) pi[i] = chi[i] = 0.0;
+  double z = sd->zeta[k], zp = sd->zeta_prev[k];
+  const double sk = sd->s[k];
+  double P = sd->P[k], X = sd->X[k];
+  double pi = 0.0, chi = 0.0;  // slot lane of the window
   // the window's base scalars: lane j loads iteration j's, all at once (no chain of dependent loads)
   double al = 0.0, be = 0.0, rn = 0.0;
-  if (k < m) {
-    al = sd->alpha_h[k];
-    be = sd->beta_h[k];
-    rn = sd->rr_h[k];
+  if (lane < m) {
+    al = sd->alpha_h[lane];
+    be = sd->beta_h[lane];
+    rn = sd->rr_h[lane];
   }
-  int shift_iters = 0;
+  bool act = true;
+  int iters = 0;
   for (int j = 0; j < m; ++j) {
     const double alpha = __shfl_sync(0xffffffffu, al, j), beta = __shfl_sync(0xffffffffu, be, j),
                  rr_new = __shfl_sync(0xffffffffu, rn, j);
-    shift_iters += __popc(__ballot_sync(0xffffffffu, act != 0));
-    if (act) {
+    if (act) {  // uniform over the warp
+      ++iters;
       const double den = alpha * bp * (zp - z) + zp * ap * (1.0 + sk * alpha);
       const double q = zp * ap / den;
       const double zn = z * q;
       const double ak = alpha * q;
       X = X + ak * P;
-#pragma unroll
-      for (int i = 0; i < kWindow; ++i)
-        if (i < j) chi[i] = chi[i] + ak * pi[i];
+      if (lane < j) chi = chi + ak * pi;
       const double bk = beta * q * q;
       P = P * bk;
       const bool stop = zn * zn * rr_new <= stop2;
-#pragma unroll
-      for (int i = 0; i < kWindow; ++i) {
-        if (i < j) pi[i] = pi[i] * bk;
-        else if (i == j) pi[i] = zn;
-        else if (stop) pi[i] = 0.0;
-        if (i == j || (i > j && stop)) chi[i] = 0.0;
-      }
+      if (lane < j) pi = pi * bk;
+      else if (lane == j) pi = zn;
+      else if (stop) pi = 0.0;
+      if (lane == j || (lane > j && stop)) chi = 0.0;
       zp = z;
       z = zn;
-      if (stop) act = 0;
+      if (stop) act = false;
     }
     ap = alpha;
     bp = beta;
   }
-  if (act0) {
+  if (lane < m) {
+    sd->pi[k][lane] = pi;
+    sd->chi[k][lane] = chi;
+  }
+  if (lane == 0) {
     sd->zeta[k] = z;
     sd->zeta_prev[k] = zp;
     sd->P[k] = P;
     sd->X[k] = X;
-#pragma unroll
-    for (int i = 0; i < kWindow; ++i) {
-      if (i < m) {
-        sd->pi[k][i] = pi[i];
-        sd->chi[k][i] = chi[i];
-      }
-    }
-    sd->active[k] = act;
+    sd->active[k] = act ? 1 : 0;
+    atomicAdd(&sd->shift_iters, iters);
+    if (!act) atomicSub(&sd->n_active, 1);
   }
-  const int n_active = __popc(__ballot_sync(0xffffffffu, act != 0));
-  if (k == 0) {
-    sd->alpha_prev = ap;
-    sd->beta_prev = bp;
-    sd->n_active = n_active;
-    sd->shift_iters += shift_iters;
-  }
+}
+
+// The window update's last block, after the replay above: the base alpha and beta of the window's
+// last iteration become the "previous" ones of the next window's first iteration.
+__device__ __forceinline__ void advance_window_scalars(SolverDev* sd, int m) {
+  sd->alpha_prev = sd->alpha_h[m - 1];
+  sd->beta_prev = sd->beta_h[m - 1];
 }
 
 }  // namespace lqcd
