@@ -752,15 +752,16 @@ __device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
 }
 
 // Every block of the kernel that follows the one that wrote the n partials (one per block, no
-// ticket) sums them and forms ratio = *x / sum (SUM_OVER_X false) or sum / *x (true) with its FP32
-// and (hi, lo) copies.  All threads of the block take part so that every load is in flight at once
-// (one L2 round trip instead of a chain of them): thread t adds the entries t, t + T, t + 2T, ...
-// (T = blockDim.x) in that order, the warps combine their threads' sums in a fixed shuffle tree,
-// and warp 0 combines the warps' sums in the same tree; thread 0 divides (FP64, once per block).
-// The order depends only on n and blockDim.x, so every block of a launch gets the same bits.  DF:
-// the partials are double-FP32 pairs (hi, lo) in the 8 bytes of each entry, added with TwoSum on
-// the FP32 pipes (the FP32 and double-FP32 solves; GB300's FP64 pipe is 1/64 of the FP32 rate),
-// else FP64 values added in FP64.
+// ticket) sums them and forms ratio = x / sum (SUM_OVER_X false) or sum / x (true) with its FP32
+// and (hi, lo) copies.  The order of the sum is fixed by n alone, whatever the block size: 128
+// virtual lanes, lane v adding the entries v, v + 128, v + 256, ... in that order, a shuffle tree
+// over each group of 32 lanes, and the four groups' sums combined in the same tree; so kernels of
+// any block size (a multiple of 64) that sum the same partials get the same bits.  Thread t takes
+// the virtual lanes t, t + blockDim.x, ... below 128 (two at 64 threads, none above 127 at 256), and
+// issues all its loads of a round before it adds (one L2 round trip for up to 8 entries per lane);
+// thread 0 divides (FP64, once per block).  DF: the partials are double-FP32 pairs (hi, lo) in the 8
+// bytes of each entry, added with TwoSum on the FP32 pipes (the FP32 and double-FP32 solves; GB300's
+// FP64 pipe is 1/64 of the FP32 rate), else FP64 values added in FP64.
 // x: the numerator (denominator) value, loaded by the caller together with its other loads, so
 // that the division waits for no further round trip to memory.  skip: this thread read a stop
 // flag (the solve is done, or its phase is over).  The flag may be set by another block of the
@@ -793,56 +794,63 @@ __device__ __forceinline__ double warp_tree64(double v) {
   return v;
 }
 
+constexpr int kSumLanes = 128;  // virtual lanes of partials_ratio's fixed summation order
+
 template <bool SUM_OVER_X, bool DF>
 __device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, int n, double x, bool skip = false) {
   __shared__ PartialsRatio res;
-  __shared__ double wsum[32];
-  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
-  constexpr int kLoads = 4;  // loads per thread issued before the adds of a round
+  __shared__ double gsum[kSumLanes / 32];
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
+  constexpr int kLoads = 8;  // entries per virtual lane loaded before the adds of a round
   if constexpr (DF) {
     const float2* p = reinterpret_cast<const float2*>(partials);
-    float s = 0.f, c = 0.f;
-    for (int b = t; b < n; b += kLoads * nt) {
-      float2 v[kLoads];
+    for (int v = t; v < kSumLanes; v += nt) {  // the same trip count in every lane of a warp
+      float s = 0.f, c = 0.f;
+      for (int b = v; b < n; b += kLoads * kSumLanes) {
+        float2 e[kLoads];
 #pragma unroll
-      for (int j = 0; j < kLoads; ++j) v[j] = (b + j * nt < n) ? __ldcg(p + b + j * nt) : make_float2(0.f, 0.f);
+        for (int j = 0; j < kLoads; ++j)
+          e[j] = (b + j * kSumLanes < n) ? __ldcg(p + b + j * kSumLanes) : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < kLoads; ++j) df_add(s, c, v[j].x, v[j].y);
+        for (int j = 0; j < kLoads; ++j) df_add(s, c, e[j].x, e[j].y);
+      }
+      const float2 w = warp_tree_df(df_norm(s, c));
+      if (lane == 0) reinterpret_cast<float2*>(gsum)[v >> 5] = w;
     }
-    const float2 w = warp_tree_df(df_norm(s, c));
-    if (lane == 0) reinterpret_cast<float2*>(wsum)[warp] = w;
     if (__syncthreads_or(skip)) {
       PartialsRatio r{};
       r.stop = 1;
       return r;
     }
-    if (warp == 0) {
-      const float2 u = warp_tree_df(lane < nw ? reinterpret_cast<const float2*>(wsum)[lane] : make_float2(0.f, 0.f));
-      if (lane == 0) wsum[0] = (double)u.x + (double)u.y;
+    if (t < 32) {
+      const float2 u = warp_tree_df(t < kSumLanes / 32 ? reinterpret_cast<const float2*>(gsum)[t] : make_float2(0.f, 0.f));
+      if (t == 0) gsum[0] = (double)u.x + (double)u.y;
     }
   } else {
-    double s = 0.0;
-    for (int b = t; b < n; b += kLoads * nt) {
-      double v[kLoads];
+    for (int v = t; v < kSumLanes; v += nt) {
+      double s = 0.0;
+      for (int b = v; b < n; b += kLoads * kSumLanes) {
+        double e[kLoads];
 #pragma unroll
-      for (int j = 0; j < kLoads; ++j) v[j] = (b + j * nt < n) ? __ldcg(partials + b + j * nt) : 0.0;
+        for (int j = 0; j < kLoads; ++j) e[j] = (b + j * kSumLanes < n) ? __ldcg(partials + b + j * kSumLanes) : 0.0;
 #pragma unroll
-      for (int j = 0; j < kLoads; ++j) s += v[j];
+        for (int j = 0; j < kLoads; ++j) s += e[j];
+      }
+      const double w = warp_tree64(s);
+      if (lane == 0) gsum[v >> 5] = w;
     }
-    const double w = warp_tree64(s);
-    if (lane == 0) wsum[warp] = w;
     if (__syncthreads_or(skip)) {
       PartialsRatio r{};
       r.stop = 1;
       return r;
     }
-    if (warp == 0) {
-      const double u = warp_tree64(lane < nw ? wsum[lane] : 0.0);
-      if (lane == 0) wsum[0] = u;
+    if (t < 32) {
+      const double u = warp_tree64(t < kSumLanes / 32 ? gsum[t] : 0.0);
+      if (t == 0) gsum[0] = u;
     }
   }
   if (t == 0) {
-    const double v = wsum[0];
+    const double v = gsum[0];
     const double q = SUM_OVER_X ? v / x : x / v;
     res.sum = v;
     res.ratio = q;

@@ -62,9 +62,89 @@ __global__ void __launch_bounds__(256) split_df_kernel(int n3, const double2* __
   lo[i] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
 }
 
+// One hop of the site's double-FP32 half Dslash onto its accumulators (s, c) of the real and
+// imaginary parts of each colour: fwd: out_a += U_ab v_b, else out_a -= conj(U_ba) v_b, with
+// U = Uh + Ul and v = vh + vl.
+__device__ __forceinline__ void df_hop(float (&sr)[3], float (&cr)[3], float (&si)[3], float (&ci)[3],
+                                       const Mat3<float>& Uh, const Mat3<float>& Ul, const Vec3<float>& vh3,
+                                       const Vec3<float>& vl3, bool fwd) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2 xv = make_float2(vh3.c[b].re, vh3.c[b].im), xl = make_float2(vl3.c[b].re, vl3.c[b].im);
+      if (fwd) {
+        const Cplx<float> uh = Uh.e[a][b], ul = Ul.e[a][b];
+        df_mac(sr[a], cr[a], uh.re, ul.re, xv.x, xl.x);
+        df_mac(sr[a], cr[a], -uh.im, -ul.im, xv.y, xl.y);
+        df_mac(si[a], ci[a], uh.re, ul.re, xv.y, xl.y);
+        df_mac(si[a], ci[a], uh.im, ul.im, xv.x, xl.x);
+      } else {
+        const Cplx<float> uh = Uh.e[b][a], ul = Ul.e[b][a];
+        df_mac(sr[a], cr[a], -uh.re, -ul.re, xv.x, xl.x);
+        df_mac(sr[a], cr[a], -uh.im, -ul.im, xv.y, xl.y);
+        df_mac(si[a], ci[a], -uh.re, -ul.re, xv.y, xl.y);
+        df_mac(si[a], ci[a], uh.im, ul.im, xv.x, xl.x);
+      }
+    }
+  }
+}
+
+// hop h of output site s (index i): the neighbour's index and the link's parity and index
+struct DfHopSite {
+  int j, lp, li, mu;
+  bool fwd;
+};
+__device__ __forceinline__ DfHopSite df_hop_site(const Geom& g, const Site& s, int p, int i, int h) {
+  DfHopSite o;
+  o.mu = h >> 1;
+  o.fwd = (h & 1) == 0;
+  o.j = neighbour_half(g, o.fwd ? neighbour_fwd(g, s, o.mu) : neighbour_bwd(g, s, o.mu));
+  o.lp = o.fwd ? p : 1 - p;
+  o.li = o.fwd ? i : o.j;
+  return o;
+}
+
+__device__ __forceinline__ float2 df_a(const DfArgs& k) {
+  return k.a_split ? make_float2(k.a_hi, k.a_lo) : (k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a));
+}
+
+// EPI 0 output of site i: D in as (hi, lo)
+__device__ __forceinline__ void df_store_plain(const DfArgs& k, int i, int vh, const float (&sr)[3],
+                                               const float (&cr)[3], const float (&si)[3], const float (&ci)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 re = df_norm(sr[a], cr[a]), im = df_norm(si[a], ci[a]);
+    k.out_hi[(size_t)a * vh + i] = make_float2(re.x, im.x);
+    k.out_lo[(size_t)a * vh + i] = make_float2(re.y, im.y);
+  }
+}
+
+// EPI 2 at site i: r = fl32(b - a x + D in), stored when r_out is set; returns the site's |r|^2 (FP32)
+__device__ __forceinline__ float df_resid_site(const DfArgs& k, int i, int vh, const float (&sr)[3],
+                                               const float (&cr)[3], const float (&si)[3], const float (&ci)[3]) {
+  const float2 asp = df_a(k);
+  const float ah = asp.x, al = asp.y;
+  float dsite = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const size_t o = (size_t)a * vh + i;
+    const float2 bh = k.b_hi[o], bl = k.b_lo[o], xh = k.x_hi[o], xl = k.x_lo[o];
+    float rs = bh.x, rc = bl.x, is = bh.y, ic = bl.y;
+    df_mac(rs, rc, -ah, -al, xh.x, xl.x);
+    df_mac(is, ic, -ah, -al, xh.y, xl.y);
+    df_add(rs, rc, sr[a], cr[a]);
+    df_add(is, ic, si[a], ci[a]);
+    const float rr = __fadd_rn(rs, rc), ri = __fadd_rn(is, ic);
+    if (k.r_out) k.r_out[o] = make_float2(rr, ri);
+    dsite += rr * rr + ri * ri;
+  }
+  return dsite;
+}
+
 // EPI 0: out = D in (hi, lo);  EPI 1: out = a x - D in and Re<x, out> (the A-apply; inside the
 // solve, without a ticket, the sum stays as per-block (hi, lo) partials for the r update);
-// EPI 2: r_out = fl32(b - (a x - D in)) and |r_out|^2 (FP64 sum).
+// EPI 2: r_out = fl32(b - (a x - D in)) (unless r_out is null) and |r_out|^2 (FP64 sum).
 template <int EPI>
 __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_constant__ PerSys<DfArgs> pk) {
   const DfArgs& k = pk.s[blockIdx.y];  // system blockIdx.y
@@ -83,53 +163,20 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_
     const uint64_t pol_lo = policy_evict_first();  // rounding errors, read only by the checks
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
-      const int mu = h >> 1;
-      const bool fwd = (h & 1) == 0;
-      const int j = neighbour_half(g, fwd ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu));
-      const int lp = fwd ? p : 1 - p;
-      const int li = fwd ? i : j;
-      const Mat3<float> Uh = load_link32(k.links_hi, lp, mu, li, vh, pol_hi);
-      const Mat3<float> Ul = load_link32(k.links_lo, lp, mu, li, vh, pol_lo);
-      const Vec3<float> vh3 = ldg_vec(k.in_hi, j, vh), vl3 = ldg_vec(k.in_lo, j, vh);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const float2 xv = make_float2(vh3.c[b].re, vh3.c[b].im), xl = make_float2(vl3.c[b].re, vl3.c[b].im);
-          if (fwd) {
-            // out_a += U_ab v_b
-            const Cplx<float> uh = Uh.e[a][b], ul = Ul.e[a][b];
-            df_mac(sr[a], cr[a], uh.re, ul.re, xv.x, xl.x);
-            df_mac(sr[a], cr[a], -uh.im, -ul.im, xv.y, xl.y);
-            df_mac(si[a], ci[a], uh.re, ul.re, xv.y, xl.y);
-            df_mac(si[a], ci[a], uh.im, ul.im, xv.x, xl.x);
-          } else {
-            // out_a -= conj(U_ba) v_b
-            const Cplx<float> uh = Uh.e[b][a], ul = Ul.e[b][a];
-            df_mac(sr[a], cr[a], -uh.re, -ul.re, xv.x, xl.x);
-            df_mac(sr[a], cr[a], -uh.im, -ul.im, xv.y, xl.y);
-            df_mac(si[a], ci[a], -uh.re, -ul.re, xv.y, xl.y);
-            df_mac(si[a], ci[a], uh.im, ul.im, xv.x, xl.x);
-          }
-        }
-      }
+      const DfHopSite o = df_hop_site(g, s, p, i, h);
+      const Mat3<float> Uh = load_link32(k.links_hi, o.lp, o.mu, o.li, vh, pol_hi);
+      const Mat3<float> Ul = load_link32(k.links_lo, o.lp, o.mu, o.li, vh, pol_lo);
+      const Vec3<float> vh3 = ldg_vec(k.in_hi, o.j, vh), vl3 = ldg_vec(k.in_lo, o.j, vh);
+      df_hop(sr, cr, si, ci, Uh, Ul, vh3, vl3, o.fwd);
     }
   }
   if constexpr (EPI == 0) {
-    if (valid) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float2 re = df_norm(sr[a], cr[a]), im = df_norm(si[a], ci[a]);
-        k.out_hi[(size_t)a * vh + i] = make_float2(re.x, im.x);
-        k.out_lo[(size_t)a * vh + i] = make_float2(re.y, im.y);
-      }
-    }
+    if (valid) df_store_plain(k, i, vh, sr, cr, si, ci);
   } else if constexpr (EPI == 1) {
     // q = a x - D in (x = the own-site vector, p of the solve), Re<x, q> in double-FP32
     float ds = 0.f, dc = 0.f;
     if (valid) {
-      const float2 asp = k.a_split ? make_float2(k.a_hi, k.a_lo)
-                                   : (k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a));
+      const float2 asp = df_a(k);
       const float ah = asp.x, al = asp.y;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -157,26 +204,7 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_
       if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
     }
   } else {
-    float dsite = 0.f;
-    if (valid) {
-      const float2 asp = k.a_split ? make_float2(k.a_hi, k.a_lo)
-                                   : (k.a_devdf ? *k.a_devdf : split64(k.a_dev ? *k.a_dev : k.a));
-      const float ah = asp.x, al = asp.y;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const size_t o = (size_t)a * vh + i;
-        const float2 bh = k.b_hi[o], bl = k.b_lo[o], xh = k.x_hi[o], xl = k.x_lo[o];
-        // r = b - a x + D in
-        float rs = bh.x, rc = bl.x, is = bh.y, ic = bl.y;
-        df_mac(rs, rc, -ah, -al, xh.x, xl.x);
-        df_mac(is, ic, -ah, -al, xh.y, xl.y);
-        df_add(rs, rc, sr[a], cr[a]);
-        df_add(is, ic, si[a], ci[a]);
-        const float rr = __fadd_rn(rs, rc), ri = __fadd_rn(is, ic);
-        k.r_out[o] = make_float2(rr, ri);
-        dsite += rr * rr + ri * ri;
-      }
-    }
+    const float dsite = valid ? df_resid_site(k, i, vh, sr, cr, si, ci) : 0.f;
     const double bs = block_sum_mixed(dsite);
     if (publish_partial(k.partials, k.ticket, bs)) {
       const double tot = gather_partials(k.partials, k.ticket);

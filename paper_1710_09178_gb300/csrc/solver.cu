@@ -533,6 +533,7 @@ struct Workspace {
   // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
   bool df = false;
   float2 *dfx_h = nullptr, *dfx_l = nullptr, *dft_h = nullptr, *dft_l = nullptr, *dfb_h = nullptr, *dfb_l = nullptr;
+
   // precision schedule of the mixed modes: the double-FP32 phase's Krylov, window and shift vectors
   // ((hi, lo) pairs, 48 bytes per site); the solutions are shared with the FP32 phase
   bool sched = false;
@@ -819,19 +820,17 @@ static cudaError_t enqueue_iteration(Launcher& L) {
     if (e == cudaSuccess) e = launch_dslash_msys(L.g, ctx->gauge, d2, S, st, &L.nlaunch);
   }
   if (e != cudaSuccess) return e;
-  const bool pr = L.next_pdl(), pp = L.next_pdl();
+  const bool pr = L.next_pdl();
   const dim3 grid(nb + 1, S);
-  if (w->kprec == LQCD_FP64) {
-    e = launch_k(pr, r_update_kernel<double, kS64>, grid, dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<double>, grid, dim3(256), st, L.g, pa);
-  } else if (w->sfmt == kS16) {
-    e = launch_k(pr, r_update_kernel<float, kS16>, grid, dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, grid, dim3(256), st, L.g, pa);
-  } else {
-    e = launch_k(pr, r_update_kernel<float, kS32>, grid, dim3(256), st, L.g, ra);
-    if (e == cudaSuccess) e = launch_k(pp, p_update_kernel<float>, grid, dim3(256), st, L.g, pa);
-  }
-  L.nlaunch += 2;
+  if (w->kprec == LQCD_FP64) e = launch_k(pr, r_update_kernel<double, kS64>, grid, dim3(256), st, L.g, ra);
+  else if (w->sfmt == kS16) e = launch_k(pr, r_update_kernel<float, kS16>, grid, dim3(256), st, L.g, ra);
+  else e = launch_k(pr, r_update_kernel<float, kS32>, grid, dim3(256), st, L.g, ra);
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  const bool pp = L.next_pdl();
+  if (w->kprec == LQCD_FP64) e = launch_k(pp, p_update_kernel<double>, grid, dim3(256), st, L.g, pa);
+  else e = launch_k(pp, p_update_kernel<float>, grid, dim3(256), st, L.g, pa);
+  L.nlaunch += 1;
   return e;
 }
 
@@ -1411,8 +1410,8 @@ static int true_residuals(lqcd_ctx* ctx, Workspace* w, const double* shifts, con
   for (size_t j = 0; j < ks.size(); ++j) {
     int k = ks[j];
     if (w->df) {
-      // straight into the refinement right-hand side (FP32), else into a scratch vector
-      ResidTarget t{xs[k], static_cast<float2*>(keep ? keep[k] : w->q), &w->sd->scal[4 + j % kMaxShifts], nullptr};
+      // straight into the refinement right-hand side (FP32); with no keep the residual is not stored
+      ResidTarget t{xs[k], keep ? static_cast<float2*>(keep[k]) : nullptr, &w->sd->scal[4 + j % kMaxShifts], nullptr};
       LQ_CUDA(enqueue_resid_df(L, &t, shifts[k], false));
       continue;
     }
