@@ -280,10 +280,14 @@ cudaStream_t workspace_stream(lqcd_ctx* ctx);
 void force_release(lqcd_ctx* ctx);
 void traj_release(lqcd_ctx* ctx);
 
-// mrhs.cu: many shifted systems (A + sigma_j) e_j = r_j solved together (per-shift refinement)
+// mrhs.cu: many shifted systems (A + sigma_j) e_j = r_j solved together (per-shift refinement), up to
+// kMrhsSlots of them: every shift of up to kMaxRhs right-hand sides of 16 shifts
+constexpr int kMrhsSlots = 64;
 int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out);
+// sys_iters (may be null): per system j, the iterations it ran until it met its target (0: it was not
+// iterated; a system still short of it at maxiter gets *iters)
 int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter, cudaStream_t st,
-               int* iters, int* status);
+               int* iters, int* status, int* sys_iters = nullptr);
 void* const* mrhs_solutions(lqcd_ctx* ctx);
 void mrhs_release(lqcd_ctx* ctx);
 

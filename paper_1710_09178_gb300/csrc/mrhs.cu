@@ -21,7 +21,8 @@
 
 namespace lqcd {
 
-constexpr int kMrhsMax = kMaxShifts;
+constexpr int kMrhsMax = kMrhsSlots;
+static_assert(kMrhsMax <= 128, "one lane per system in a 128-thread block");
 // systems per link load in the multi-RHS Dslash: 4 accumulators per thread keep the kernel at
 // 8 resident blocks per SM; on GB300 that beats more link reuse (16 systems: +40 % solve time,
 // 8: +9 %, 2: +4 %, 1: +15 % at 32^3 x 8), the links being L2-resident anyway
@@ -38,6 +39,7 @@ struct MrhsDev {
   float af[kMrhsMax];  // the same in FP32 (no FP64 conversion inside the FP32 kernels)
   float alpha_f[kMrhsMax], beta_f[kMrhsMax];  // FP32 copies written by the scalar steps
   double rr[kMrhsMax], stop2[kMrhsMax], alpha[kMrhsMax], beta[kMrhsMax];
+  int it_sys[kMrhsMax];  // the iteration count at which system j met its target (0: not yet, or never iterated)
 };
 
 struct MrhsVecs {
@@ -280,6 +282,7 @@ __global__ void __launch_bounds__(128) mrhs_update_kernel(Geom g, MrhsVecs vv, M
     md->beta_f[sj] = (float)beta;
     md->rr[sj] = v;
     keep[pos] = !(v <= md->stop2[sj]);
+    if (!keep[pos]) md->it_sys[sj] = md->iter + 1;  // thread 0 advances iter after the barrier below
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(128) mrhs_init_kernel(Geom g, MrhsVecs vv, Mrh
       md->af[sj] = (float)in.a[sj];
       md->alpha[sj] = md->beta[sj] = 0.0;
       md->alpha_f[sj] = md->beta_f[sj] = 0.f;
+      md->it_sys[sj] = 0;
     }
   }
   __syncthreads();
@@ -490,7 +494,9 @@ static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, cons
 // Solve (A + sigma_j) e_j = r_j (r_j already in the workspace's r buffers) until
 // |r_j| <= rel_j |r_j(0)| for every j, or maxiter.  Returns iterations in *iters.
 int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter,
-               cudaStream_t st, int* iters, int* status) {
+               cudaStream_t st, int* iters, int* status, int* sys_iters) {
+  if (m < 1 || m > kMrhsMax) return fail(ctx, LQCD_ERR_ARG, "mrhs: too many systems");
+  int it_sys[kMrhsMax];
   MrhsWorkspace* mw = ctx->mrhs;
   Geom g = make_geom(ctx);
   const int groups = (m + kMrhsGroup - 1) / kMrhsGroup;
@@ -526,6 +532,12 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
     ctx->launches += nl;
     *iters = hs[0];
     *status = hs[3];
+    if (sys_iters) {
+      if ((e = cudaMemcpyAsync(it_sys, mw->md->it_sys, sizeof(int) * m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_check(ctx, e, "mrhs readback");
+      for (int j = 0; j < m; ++j) sys_iters[j] = it_sys[j];
+    }
     return LQCD_OK;
   }
   if (!mw->graph || mw->graph_m != m || mw->graph_prec != prec) {
@@ -588,10 +600,15 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
   int passes = 0;
   if ((e = cudaMemcpyAsync(&passes, &mw->md->passes, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_check(ctx, e, "mrhs readback");
+  if (sys_iters &&
+      (e = cudaMemcpyAsync(it_sys, mw->md->it_sys, sizeof(int) * m, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_check(ctx, e, "mrhs readback");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_check(ctx, e, "mrhs sync");
   ctx->launches += nl + (long long)passes * mw->nodes_per_pass;
   *iters = hs[0];
   *status = hs[3] != LQCD_OK ? hs[3] : LQCD_OK;
+  if (sys_iters)
+    for (int j = 0; j < m; ++j) sys_iters[j] = it_sys[j];
   return LQCD_OK;
 }
 

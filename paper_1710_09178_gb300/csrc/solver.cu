@@ -1429,6 +1429,112 @@ static int true_residuals(lqcd_ctx* ctx, Workspace* w, const double* shifts, con
   return LQCD_OK;
 }
 
+// The true residuals of several systems' solutions (held as (hi, lo) pairs) at once: for every shift k,
+// one double-FP32 residual launch pair over the systems that list k (kernels over gridDim.y, each
+// system with its own arithmetic and buffers, so each residual is the bits of its own check), then
+// one wait for all.  ks[s]: the shifts of system s; keep (may be null): the residual of (s, k) goes
+// to keep[s * n + k], the refinement's right-hand side.
+static int true_residuals_joint(lqcd_ctx* ctx, const Launcher& L, const double* shifts, int n,
+                                const std::vector<int>* ks, const double* bb, double (*out)[kMaxShifts],
+                                void* const* keep) {
+  Workspace* w = L.w;
+  for (int k = 0; k < n; ++k) {
+    Launcher Lk{ctx, nullptr, L.g, 0};
+    ResidTarget t[kMaxRhs];
+    int cnt = 0;
+    for (int s = 0; s < L.S; ++s) {
+      if (std::find(ks[s].begin(), ks[s].end(), k) == ks[s].end()) continue;
+      Workspace* y = L.sys(s);
+      if (cnt == 0) Lk.w = y;  // every system runs on system 0's stream
+      else Lk.more[cnt] = y;
+      t[cnt] = ResidTarget{run_solutions(y)[k], keep ? static_cast<float2*>(keep[s * n + k]) : nullptr,
+                           &y->sd->scal[4 + k], nullptr};
+      ++cnt;
+    }
+    if (cnt == 0) continue;
+    Lk.S = cnt;
+    LQ_CUDA(enqueue_resid_df(Lk, t, shifts[k], false));
+    ctx->launches += Lk.nlaunch;
+  }
+  for (int s = 0; s < L.S; ++s) {
+    Workspace* y = L.sys(s);
+    LQ_CUDA(cudaMemcpyAsync(y->host_scal, &y->sd->scal[4], sizeof(double) * n, cudaMemcpyDeviceToHost, w->st));
+  }
+  LQ_CUDA(cudaStreamSynchronize(w->st));
+  for (int s = 0; s < L.S; ++s)
+    for (int k : ks[s]) out[s][k] = sqrt(L.sys(s)->host_scal[k] / bb[s]);
+  return LQCD_OK;
+}
+
+// Certification and refinement of S > 1 systems together (solutions as (hi, lo) pairs, S n <=
+// kMrhsSlots): the checks as above, and per round one multi-RHS correction solve for every failing
+// (system, shift) pair, slot s n + k.  Each pair's correction is computed as in a solve of its own
+// system alone (its CG, its scalars and its sums do not depend on the other slots), so the results
+// are the same bits as system by system, with one wait per step instead of one per system; the
+// refinement iterations reported for a system are those its own slots ran.  One difference: a
+// non-finite correction in any slot ends the refinement of every system.
+static int post_solve_joint(lqcd_ctx* ctx, const Launcher& L, int prec, const double* shifts, int n, double tol,
+                            int maxiter, const int* st_main, const double* bb, double (*tres)[kMaxShifts],
+                            int* refine_iters, int* refined, int* rounds_done) {
+  const int S = L.S;
+  Workspace* w = L.w;
+  bool refine[kMaxRhs], refine_any = false;
+  for (int s = 0; s < S; ++s) {
+    refine[s] = ctx->refine && st_main[s] == LQCD_OK;
+    refine_any = refine_any || refine[s];
+  }
+  void* const* rhs = nullptr;
+  int rc;
+  if (refine_any && (rc = mrhs_prepare(ctx, prec, S * n, &rhs)) != LQCD_OK) return rc;
+  std::vector<int> ks[kMaxRhs];
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < n; ++k) ks[s].push_back(k);
+  if ((rc = true_residuals_joint(ctx, L, shifts, n, ks, bb, tres, rhs)) != LQCD_OK) return rc;
+  double sig[kMrhsSlots], rel[kMrhsSlots];
+  int its[kMrhsSlots];
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < n; ++k) sig[s * n + k] = shifts[k];
+  const int n3 = 3 * L.g.vh;
+  for (int round = 0; refine_any && round < 4; ++round) {
+    bool any = false;
+    for (int s = 0; s < S; ++s) {
+      ks[s].clear();
+      for (int k = 0; k < n; ++k) {
+        const int j = s * n + k;
+        rel[j] = 1e300;  // slots already below tol are not iterated
+        if (refine[s] && tres[s][k] > tol) {
+          ks[s].push_back(k);
+          rel[j] = std::min(0.5, 0.75 * tol / tres[s][k]);
+          any = true;
+        }
+      }
+    }
+    if (!any) break;
+    int it2 = 0, st2 = LQCD_OK;
+    if ((rc = mrhs_solve(ctx, prec, S * n, sig, rel, maxiter, w->st, &it2, &st2, its)) != LQCD_OK) return rc;
+    void* const* es = mrhs_solutions(ctx);
+    for (int s = 0; s < S; ++s) {
+      if (ks[s].empty()) continue;
+      Workspace* y = L.sys(s);
+      int mx = 0;
+      for (int k : ks[s]) {
+        const int j = s * n + k;
+        mx = std::max(mx, its[j] > 0 ? its[j] : it2);
+        add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(y->xdf[k]),
+                                                                       static_cast<const float2*>(es[j]));
+        ctx->launches += 1;
+      }
+      refine_iters[s] += mx;
+      if (round == 0) refined[s] = (int)ks[s].size();
+      rounds_done[s] = round + 1;
+    }
+    LQ_CUDA(cudaGetLastError());
+    if ((rc = true_residuals_joint(ctx, L, shifts, n, ks, bb, tres, rhs)) != LQCD_OK) return rc;
+    if (st2 == LQCD_ERR_NONFINITE) break;
+  }
+  return LQCD_OK;
+}
+
 // The shifted CG of S right-hand sides b_devs[s] on one context (S = 1: mshift_cg; S > 1:
 // mshift_cg_multi).  Each system is solved exactly as on its own; the systems share the kernel
 // launches and, in the FP32 phase, every link load of the Dslash.
@@ -1466,16 +1572,36 @@ int run_mshift_multi(lqcd_ctx* ctx, int S, const double* shifts, const double* r
   int status_all = LQCD_OK;
   int refine_iters[kMaxRhs] = {}, refined[kMaxRhs] = {}, rounds_done[kMaxRhs] = {};
   double tres[kMaxRhs][kMaxShifts];
+  // |b|^2 of every system, one wait
+  double bbs[kMaxRhs];
+  int st_mains[kMaxRhs];
   for (int s = 0; s < S; ++s) {
     Workspace* y = L.sys(s);
-    double2* const* xs_run = run_solutions(y);
-    LQ_CUDA(cudaMemcpyAsync(y->host_scal, &y->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
-    LQ_CUDA(cudaStreamSynchronize(w->st));
-    const double bb = y->host_scal[0];
-    const int st_main = core[s].status;
-    int status = st_main;
+    LQ_CUDA(cudaMemcpyAsync(&y->host_scal[kMaxShifts + 3], &y->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
+    st_mains[s] = core[s].status;
     for (int k = 0; k < n; ++k) tres[s][k] = 0.0;
-    if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
+  }
+  LQ_CUDA(cudaStreamSynchronize(w->st));
+  bool joint = S > 1 && S * n <= kMrhsSlots;  // every system with a nonzero, finite source in double-FP32
+  for (int s = 0; s < S; ++s) {
+    bbs[s] = L.sys(s)->host_scal[kMaxShifts + 3];
+    joint = joint && L.sys(s)->xdfmode && bbs[s] > 0.0 && st_mains[s] != LQCD_ERR_NONFINITE;
+  }
+  if (joint) {
+    rc = post_solve_joint(ctx, L, prec, shifts, n, tol, maxiter, st_mains, bbs, tres, refine_iters, refined,
+                          rounds_done);
+    if (rc != LQCD_OK) return rc;
+  }
+  for (int s = 0; s < S; ++s) {
+    Workspace* y = L.sys(s);
+    const double bb = bbs[s];
+    const int st_main = st_mains[s];
+    int status = st_main;
+    if (joint) {
+      if (status == LQCD_OK)
+        for (int k = 0; k < n; ++k)
+          if (!(tres[s][k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
+    } else if (bb > 0.0 && st_main != LQCD_ERR_NONFINITE) {
       std::vector<int> all(n);
       for (int k = 0; k < n; ++k) all[k] = k;
       const bool refine = ctx->refine && st_main == LQCD_OK;

@@ -3,8 +3,9 @@ pseudofermions of one gauge field in the batched workload; the paper solves one 
 
 Bars: every system's solutions, y and statistics equal those of mshift_cg on that source alone,
 bit for bit (the systems run the same arithmetic; they only share kernel launches and, in the FP32
-iterations, the link loads of the Dslash), in every FP32 Krylov mode, with and without the
-double-FP32 first phase and with and without CUDA graphs; the oracle's FP64 true residual of every
+iterations, the link loads of the Dslash; after the solve their checks and refinement run jointly
+when every (system, shift) pair fits the refinement's 64 slots, else system by system: 4 x 17), in
+every FP32 Krylov mode, with and without the double-FP32 first phase and with and without CUDA graphs; the oracle's FP64 true residual of every
 returned x_k is at most tol; unsupported modes and bad arguments are refused.
 """
 import numpy as np
@@ -44,7 +45,7 @@ KEYS = ("iterations", "reliable_updates", "refine_iterations", "refined_shifts",
 
 
 @pytest.mark.parametrize("dims,mass,npoles,nrhs", [((10, 6, 4, 6), 0.05, 12, 2), ((16, 16, 16, 8), 0.05, 14, 4),
-                                                   ((8, 8, 8, 4), 0.02, 12, 3)])
+                                                   ((8, 8, 8, 4), 0.02, 12, 3), ((8, 8, 8, 4), 0.02, 17, 4)])
 @pytest.mark.parametrize("prec", [FP32, FP32_R12, FP16FIX, FP32_L16])
 def test_multi_equals_single_solves(dims, mass, npoles, nrhs, prec):
     import paper_1710_09178_gb300 as lq
