@@ -51,6 +51,13 @@ GAUGE_SEED, VEC_SEED = 5, 6
 DSLASH_BYTES_PER_SITE = {"fp32": 8 * 72 + 24 + 24, "fp32_r12": 8 * 48 + 24 + 24, "fp32_r8": 8 * 32 + 24 + 24,
                          "fp32_l16": 8 * 24 + 24 + 24, "fp64": 8 * 144 + 48 + 48}
 DSLASH_FLOPS_PER_SITE = 570
+# The double-FP32 half Dslash (the checks and the first phase of the mixed solve): per output site 8 hops x
+# 9 link entries x 4 real products, each one compensated multiply-add of 12 FP32 operations (product,
+# its exact error and the two cross terms: 4; TwoSum into the running sum: 6; the compensation: 2), and
+# 6 final renormalisations of 2; bytes, counted as for the FP32 Dslash (each crossing HBM once): 8 link
+# pairs (hi, lo: 2 x 72), the input pair (2 x 24, re-read from L2 by the neighbours) and the output pair
+DF_OPS_PER_SITE = 8 * 9 * 4 * 12 + 6 * 2
+DF_BYTES_PER_SITE = 8 * 144 + 48 + 48
 
 
 def env_int(name, default):
@@ -69,23 +76,23 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=("dslash.cu", "common.cuh")):
     h = hashlib.sha256()
-    for f in ("dslash.cu", "common.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1710_09178_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_key):
-    """DRAM bytes per launch of the FP32 Dslash from the committed ncu record
-    (profiles/dslash_fp32_32c8.json), if it was captured on this kernel source."""
-    p = os.path.join(ROOT, "profiles", "dslash_fp32_32c8.json")
+def profiled_traffic(workload_key, record="dslash_fp32_32c8.json", files=("dslash.cu", "common.cuh")):
+    """DRAM bytes per launch of a kernel from its committed ncu record (profiles/<record>: the FP32
+    Dslash by default), if it was captured on this kernel source."""
+    p = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash(files):
         return None
     return float(rec["dram_bytes_per_launch"])
 
@@ -326,6 +333,44 @@ def time_dslash_graph(lq, torch, Ud, prec, reps, n_fields=STREAM_FIELDS):
         torch.cuda.synchronize()
         for c, _, _ in sctx:
             c.close()
+
+
+def time_df_dslash_graph(lq, torch, Ud, reps=64):
+    """The double-FP32 half Dslash (dslash_eo with LQCD_DF64 vectors) at the bench workload: reps
+    launches in one CUDA graph, alternating parities; its 151 MB of hi + lo links exceed L2.  Returns ms
+    per launch (median of 5 replays), or None where the capture is refused."""
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    c = lq.Context(DIMS, MASS, stream=s.cuda_stream)
+    try:
+        c.set_gauge(Ud)
+        vin, vout = c.new_vector(lq.DF64), c.new_vector(lq.DF64)
+        vin.view(torch.float32).normal_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for i in range(4):
+                lq.dslash_eo(c, vout, vin, i & 1, lq.DF64)
+            s.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+                for i in range(reps):
+                    lq.dslash_eo(c, vout, vin, i & 1, lq.DF64)
+            graph.replay()
+            ms = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                graph.replay()
+                e1.record(s)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1) / reps)
+        return statistics.median(ms)
+    except (RuntimeError, lq.LqcdError):
+        return None
+    finally:
+        torch.cuda.synchronize()
+        c.close()
 
 
 def cpu_oracle_solves(U, b, coeffs):
@@ -735,7 +780,7 @@ def run_formats(lq, torch, dims_list=((32, 32, 32, 8), (48, 48, 48, 12)), reps=2
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
     `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
-    then 6 replays of the graph: 592 launches),
+    then 6 replays of the graph: 592 launches), `df_dslash` = 8 double-FP32 half-Dslash launches,
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch,
     `solve_graph` = two solves with CUDA graphs on (the second is the timed configuration),
     `multi` = the same for four sources solved together (mshift_cg_multi)."""
@@ -753,6 +798,12 @@ def run_profile_target(kind, prec_name):
     if kind == "dslash_graph":
         ms = time_dslash_graph(lq, torch, torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda(), prec, 96)
         print(json.dumps({"profile": "dslash_graph", "ms_per_launch": ms}))
+    elif kind == "df_dslash":
+        vin = ctx.new_vector(lq.DF64)
+        vout = ctx.new_vector(lq.DF64)
+        vin.view(torch.float32).normal_()
+        for r in range(8):
+            lq.dslash_eo(ctx, vout, vin, r & 1, lq.DF64)
     elif kind == "dslash":
         vin = ctx.new_vector(prec)
         vout = ctx.new_vector(prec)
@@ -800,7 +851,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
-    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "solve", "solve_graph", "multi"],
+    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "df_dslash", "solve", "solve_graph", "multi"],
                     help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
@@ -966,6 +1017,25 @@ def main():
                 "bytes_per_launch": bpl, "ms_per_launch": r_ms, "timing": r_timing,
                 "stream_launches": streamed, "isolated_launch": isolated}
 
+    # ---- the double-FP32 Dslash: the largest share of the mixed solve's time (its first phase and
+    # every true-residual check), bound by FP32 instruction issue; peak = SMs x 128 FP32 lanes x the
+    # maximum SM clock (2070 MHz), one operation per lane and cycle (an FMA counts as one) ----------
+    roofline_df = None
+    if not args.quick:
+        df_ms = time_df_dslash_graph(lq, torch, Ud)
+        if df_ms is not None:
+            n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+            alu_peak = n_sm * 128 * 2070e6 / 1e12  # T FP32 operations per second
+            ops = DF_OPS_PER_SITE * vh / (df_ms * 1e-3) / 1e12
+            df_gbs = DF_BYTES_PER_SITE * vh / (df_ms * 1e-3) / 1e9
+            roofline_df = {"bound": "alu", "achieved": ops, "peak": alu_peak, "unit": "T FP32 op/s", "frac": ops / alu_peak,
+                           "traffic": profiled_traffic(WORKLOAD, "df_dslash_32c8.json", ("df64.cu", "common.cuh")),
+                           "kernel": "df_dslash_kernel<plain> (double-FP32 links and vectors)",
+                           "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2070 MHz",
+                           "ops_per_site": DF_OPS_PER_SITE, "bytes_per_launch": DF_BYTES_PER_SITE * vh,
+                           "ms_per_launch": df_ms, "algorithmic_GBps": df_gbs, "frac_of_hbm": df_gbs / peak,
+                           "timing": "64 launches (alternating parities) in one CUDA graph, median of 5 replays"}
+
     # ---- end to end through the C ABI with host buffers ------------------------------------
     c0, res, poles, _ = coeffs
     b_host = torch.from_numpy(b).pin_memory()
@@ -1043,6 +1113,7 @@ def main():
         "modes": extra,
         "dslash": dsl,
         "roofline": roofline,
+        "roofline_df": roofline_df,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/solve", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "rhmc_trajectory": traj,
