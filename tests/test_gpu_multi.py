@@ -149,3 +149,39 @@ def test_multi_rejects_bad_arguments():
     ctx.set_option(lq.OPT_DF_RESID, 1)
     rc, _ = lq.mshift_cg_multi(ctx, [0.1], [1.0], 0.0, [b1, b2], prec=FP32, raise_on_error=False)
     assert rc == 0
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_multi_joint_and_fallback_post_solve(refine):
+    # After the solve the systems' checks and refinement run jointly; a zero source among them sends
+    # the call down the system-by-system path.  Either way, with and without refinement, every system
+    # equals its own mshift_cg bit for bit.
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (8, 8, 8, 4), 0.02
+    ctx, U = make_context(dims, mass, gauge_seed=37)
+    ctx.set_option(lq.OPT_REFINE, refine)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(12, 4 * mass ** 2, 16 + 4 * mass ** 2)
+    b1, b2 = to_dev(inputs.gaussian_vector(dims, 90)), to_dev(inputs.gaussian_vector(dims, 91))
+    for bs in ([b1, b2], [b1, torch.zeros_like(b1), b2]):
+        single = []
+        for b in bs:
+            xs1 = [torch.empty_like(b) for _ in poles]
+            y1 = torch.empty_like(b)
+            rc1, st1 = lq.mshift_cg(ctx, poles, res, c0, b, xs1, y1, tol=1e-10, prec=FP32, raise_on_error=False)
+            single.append((rc1, st1, xs1, y1))
+        xs = [[torch.empty_like(b) for _ in poles] for b in bs]
+        ys = [torch.empty_like(b) for b in bs]
+        rc, sts = lq.mshift_cg_multi(ctx, poles, res, c0, bs, xs, ys, tol=1e-10, prec=FP32, raise_on_error=False)
+        torch.cuda.synchronize()
+        assert rc == next((x[0] for x in single if x[0] != 0), 0)  # the first system that is not OK
+        if refine:
+            assert rc == 0
+        for s in range(len(bs)):
+            for k in KEYS:
+                assert sts[s][k] == single[s][1][k], (len(bs), s, k)
+            for a, c in zip(xs[s], single[s][2]):
+                assert torch.equal(a, c)
+            assert torch.equal(ys[s], single[s][3])
