@@ -533,6 +533,11 @@ struct Workspace {
   // double-FP32 residuals (mixed modes): x, D_oe x and b as (hi, lo) pairs
   bool df = false;
   float2 *dfx_h = nullptr, *dfx_l = nullptr, *dft_h = nullptr, *dft_l = nullptr, *dfb_h = nullptr, *dfb_l = nullptr;
+  // the certification's residual slots 1 .. kMaxRhs-1 (slot 0 uses dft, partials and ticket 3): D_oe x_k,
+  // per-block partials (nparts each) and tickets 5 ..
+  float2 *cdft_h[kMaxRhs - 1] = {}, *cdft_l[kMaxRhs - 1] = {};
+  double* cpartials = nullptr;
+  int nparts = 0;
 
   // precision schedule of the mixed modes: the double-FP32 phase's Krylov, window and shift vectors
   // ((hi, lo) pairs, 48 bytes per site); the solutions are shared with the FP32 phase
@@ -573,9 +578,13 @@ static void destroy_workspace(Workspace* w) {
   for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
   void* bufs[] = {w->dfx_h, w->dfx_l, w->dft_h, w->dft_l, w->dfb_h, w->dfb_l,
                   w->r, w->p, w->q, w->tmp, w->ring, w->b64, w->r64, w->tmp64, w->e64, w->rb64, w->sd,
-                  w->ru_count, w->partials, w->tickets, w->dr, w->dp, w->dq, w->dtmp, w->dring};
+                  w->ru_count, w->partials, w->tickets, w->dr, w->dp, w->dq, w->dtmp, w->dring, w->cpartials};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  for (int u = 0; u < kMaxRhs - 1; ++u) {
+    if (w->cdft_h[u]) cudaFree(w->cdft_h[u]);
+    if (w->cdft_l[u]) cudaFree(w->cdft_l[u]);
+  }
   for (int k = 0; k < kMaxShifts; ++k) {
     if (w->pk[k]) cudaFree(w->pk[k]);
     if (w->xk[k]) cudaFree(w->xk[k]);
@@ -670,6 +679,14 @@ static int alloc_workspace(lqcd_ctx* ctx, int prec, int n, Workspace** slot, cud
   int nparts = std::max(dslash_grid_blocks(make_geom(ctx), LQCD_FP32, 8, 64), (int)((vh + 127) / 128)) + 64;
   LQ_CUDA(cudaMalloc(&w->partials, 2 * sizeof(double) * nparts));
   w->partials_b = w->partials + nparts;
+  w->nparts = nparts;
+  if (w->df) {
+    for (int u = 0; u < kMaxRhs - 1; ++u) {
+      LQ_CUDA(cudaMalloc(&w->cdft_h[u], 24 * (size_t)vh));
+      LQ_CUDA(cudaMalloc(&w->cdft_l[u], 24 * (size_t)vh));
+    }
+    LQ_CUDA(cudaMalloc(&w->cpartials, sizeof(double) * nparts * (kMaxRhs - 1)));
+  }
   LQ_CUDA(cudaMalloc(&w->tickets, sizeof(unsigned) * 16));
   LQ_CUDA(cudaMemsetAsync(w->tickets, 0, sizeof(unsigned) * 16, w->st));
   LQ_CUDA(cudaMallocHost(&w->host_status, sizeof(StatusWords) * 2));
@@ -1062,6 +1079,55 @@ static cudaError_t enqueue_resid_df(Launcher& L, const ResidTarget* t, double si
   return e;
 }
 
+// Double-FP32 residuals b - (A + sigma[u]) x_u of nt <= kMaxRhs solutions of one system (L.w, solutions
+// as (hi, lo) pairs) as the nt slots of one D_oe and one D_eo launch (blockIdx.y = slot): every block works
+// on one slot with the arithmetic of a launch of its own, so each residual is the same bits; nt times the
+// blocks per launch fill the GPU's last wave and cut the launches by nt.  Slot u: D_oe x_u in dft (u = 0)
+// or cdft[u - 1], partials in partials or cpartials, ticket 3 or 4 + u.
+static cudaError_t enqueue_resid_df_slots(Launcher& L, const ResidTarget* t, const double* sigma, int nt) {
+  Workspace* w = L.w;
+  lqcd_ctx* ctx = L.ctx;
+  const size_t n3 = 3 * (size_t)L.g.vh;
+  PerSys<DfArgs> d, r;
+  for (int u = 0; u < nt; ++u) {
+    const float2* xh = reinterpret_cast<const float2*>(t[u].x);
+    DfArgs& x = d.s[u];
+    x.links_hi = ctx->gauge.u32;
+    x.links_lo = ctx->gauge.u32lo;
+    x.in_hi = xh;
+    x.in_lo = xh + n3;
+    x.out_hi = u ? w->cdft_h[u - 1] : w->dft_h;
+    x.out_lo = u ? w->cdft_l[u - 1] : w->dft_l;
+    x.out_parity = 1;
+    DfArgs& z = r.s[u];
+    z = x;
+    z.in_hi = x.out_hi;
+    z.in_lo = x.out_lo;
+    z.out_hi = z.out_lo = nullptr;
+    z.out_parity = 0;
+    z.x_hi = xh;
+    z.x_lo = xh + n3;
+    z.b_hi = w->dfb_h;
+    z.b_lo = w->dfb_l;
+    const double a = 4.0 * ctx->mass * ctx->mass + sigma[u];
+    const float ah = (float)a;
+    z.a = a;
+    z.a_hi = ah;
+    z.a_lo = (float)(a - (double)ah);
+    z.a_split = 1;
+    z.r_out = t[u].r_out;
+    z.dot_out = t[u].dot;
+    z.partials = u ? w->cpartials + (size_t)(u - 1) * w->nparts : w->partials;
+    z.ticket = u ? w->tickets + 4 + u : w->tickets + 3;
+  }
+  cudaError_t e = launch_df_dslash_multi(L.g, d, nt, 0, w->st, L.next_pdl());
+  L.nlaunch += 1;
+  if (e != cudaSuccess) return e;
+  e = launch_df_dslash_multi(L.g, r, nt, 2, w->st, L.next_pdl());
+  L.nlaunch += 1;
+  return e;
+}
+
 // one window of the double-FP32 phase of the precision schedule, its phase test and the (guarded,
 // one-time) change to the FP32 phase
 static cudaError_t enqueue_df_window(Launcher& L, int n, cudaGraphConditionalHandle handle, int set_cond) {
@@ -1407,14 +1473,24 @@ static int true_residuals(lqcd_ctx* ctx, Workspace* w, const double* shifts, con
   Launcher L{ctx, w, make_geom(ctx), 0};
   double2* const* xs = run_solutions(w);
   const int n3 = 3 * L.g.vh;
-  for (size_t j = 0; j < ks.size(); ++j) {
-    int k = ks[j];
-    if (w->df) {
-      // straight into the refinement right-hand side (FP32); with no keep the residual is not stored
-      ResidTarget t{xs[k], keep ? static_cast<float2*>(keep[k]) : nullptr, &w->sd->scal[4 + j % kMaxShifts], nullptr};
-      LQ_CUDA(enqueue_resid_df(L, &t, shifts[k], false));
-      continue;
+  if (w->df) {
+    // double-FP32, kMaxRhs shifts per launch pair (slots); each residual straight into the refinement
+    // right-hand side (FP32), or not stored with no keep
+    for (size_t j0 = 0; j0 < ks.size(); j0 += kMaxRhs) {
+      const int nt = (int)std::min<size_t>(kMaxRhs, ks.size() - j0);
+      ResidTarget t[kMaxRhs];
+      double sig[kMaxRhs];
+      for (int u = 0; u < nt; ++u) {
+        const int k = ks[j0 + u];
+        t[u] = ResidTarget{xs[k], keep ? static_cast<float2*>(keep[k]) : nullptr,
+                           &w->sd->scal[4 + (j0 + u) % kMaxShifts], nullptr};
+        sig[u] = shifts[k];
+      }
+      LQ_CUDA(enqueue_resid_df_slots(L, t, sig, nt));
     }
+  }
+  for (size_t j = 0; j < ks.size() && !w->df; ++j) {
+    int k = ks[j];
     LQ_CUDA(enqueue_resid64(L, xs[k], w->b64, shifts[k], &w->sd->scal[4 + j % kMaxShifts], nullptr));
     if (keep) {
       keep_residual_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, w->r64, keep[k], keep_f32);
