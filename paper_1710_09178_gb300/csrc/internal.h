@@ -264,6 +264,7 @@ cudaError_t launch_df_p_update(const Geom& g, const PerSys<DfUpdArgs>& a, int S,
 int df_dslash_grid_blocks(const Geom& g);  // blocks (= partials) of one double-FP32 Dslash launch
 cudaError_t launch_df_flush(const Geom& g, const PerSys<DfFlushArgs>& a, int S, cudaStream_t st, bool pdl);
 cudaError_t launch_df_to_fp64(const Geom& g, const void* v, double2* x, cudaStream_t st);
+cudaError_t launch_df_to_fp64_many(const Geom& g, void* const* v, double2* const* x, int n, cudaStream_t st);
 
 // solver.cu
 int run_mshift(lqcd_ctx* ctx, const double* shifts, const double* residues, int n, double c0, const double* b_dev,

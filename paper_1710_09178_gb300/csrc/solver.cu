@@ -547,6 +547,7 @@ struct Workspace {
   SolverDev* sd = nullptr;
   int* ru_count = nullptr;
   StatusWords* host_status = nullptr;  // pinned, 2 slots
+  int* host_ints = nullptr;            // pinned: windows run / max / double-FP32, shift iterations, reliable updates
   int shift_iters_host = 0;
   double* host_scal = nullptr;         // pinned
   double* partials = nullptr;
@@ -592,6 +593,7 @@ static void destroy_workspace(Workspace* w) {
     if (w->dpk[k]) cudaFree(w->dpk[k]);
   }
   if (w->host_status) cudaFreeHost(w->host_status);
+  if (w->host_ints) cudaFreeHost(w->host_ints);
   if (w->host_scal) cudaFreeHost(w->host_scal);
   cudaEvent_t evs[] = {w->ev_in, w->ev_out, w->ev_t0, w->ev_t1, w->ev_batch[0], w->ev_batch[1]};
   for (cudaEvent_t e : evs)
@@ -690,6 +692,7 @@ static int alloc_workspace(lqcd_ctx* ctx, int prec, int n, Workspace** slot, cud
   LQ_CUDA(cudaMalloc(&w->tickets, sizeof(unsigned) * 16));
   LQ_CUDA(cudaMemsetAsync(w->tickets, 0, sizeof(unsigned) * 16, w->st));
   LQ_CUDA(cudaMallocHost(&w->host_status, sizeof(StatusWords) * 2));
+  LQ_CUDA(cudaMallocHost(&w->host_ints, sizeof(int) * 8));
   LQ_CUDA(cudaMallocHost(&w->host_scal, sizeof(double) * (kMaxShifts + 4)));
   return LQCD_OK;
 }
@@ -1259,6 +1262,7 @@ static int solve_core(Launcher& L, const double* shifts, int n, double tol, int 
     LQ_CUDA(cudaGetLastError());
   }
 
+  int nodes_fp32 = -1, nodes_df = 0;  // kernel nodes per window of the captured loops (graph path)
   if (ctx->use_graph) {
     // One graph per (source, solution set, shift count, base shift, systems): a while-node repeats
     // [kWindow iterations, window update, reliable update if due, loop control] until done; with the
@@ -1340,21 +1344,8 @@ static int solve_core(Launcher& L, const double* shifts, int n, double tol, int 
       it = w->graphs.find(key);
     }
     LQ_CUDA(cudaGraphLaunch(it->second, w->st));
-    // windows_run, max_windows, windows_df (system 0 counts every window of both loops)
-    int* wins = reinterpret_cast<int*>(&w->host_status[1]);
-    LQ_CUDA(cudaMemcpyAsync(wins, &w->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
-    LQ_CUDA(cudaStreamSynchronize(w->st));
-    // kernel nodes per window x windows run, in each phase (a system that left the double-FP32 phase
-    // early idles through the phase's remaining windows)
-    int wdf = 0;
-    if (sched) {
-      for (int s = 0; s < S; ++s) {
-        int v = 0;
-        LQ_CUDA(cudaMemcpy(&v, &L.sys(s)->sd->windows_df, sizeof(int), cudaMemcpyDeviceToHost));
-        wdf = std::max(wdf, v);
-      }
-    }
-    L.nlaunch += w->graph_nodes[key] * (wins[0] - wdf) + w->graph_nodes_df[key] * wdf;
+    nodes_fp32 = w->graph_nodes[key];
+    nodes_df = w->graph_nodes_df[key];
   } else {
     // host-polled batches of windows (at most two in flight) until every system is done (or, in the
     // double-FP32 phase, has left it)
@@ -1399,18 +1390,29 @@ static int solve_core(Launcher& L, const double* shifts, int n, double tol, int 
     int rc = run_batches(false);
     if (rc != LQCD_OK) return rc;
   }
-  // drain a batch still in flight and read the final state of every system
+  // drain a batch still in flight and read the final state of every system: status words, windows run
+  // (of both loops) / max / of the double-FP32 phase, shift iterations and reliable updates, all in one wait
   for (int s = 0; s < S; ++s) {
     Workspace* y = L.sys(s);
     LQ_CUDA(cudaMemcpyAsync(&y->host_status[0], &y->sd->iter, sizeof(StatusWords), cudaMemcpyDeviceToHost, w->st));
+    LQ_CUDA(cudaMemcpyAsync(y->host_ints, &y->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost, w->st));
+    LQ_CUDA(cudaMemcpyAsync(y->host_ints + 3, &y->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost, w->st));
+    LQ_CUDA(cudaMemcpyAsync(y->host_ints + 4, y->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
   }
   LQ_CUDA(cudaStreamSynchronize(w->st));
+  if (nodes_fp32 >= 0) {
+    // kernel nodes per window x windows run, in each phase (system 0 counts every window of both loops; a
+    // system that left the double-FP32 phase early idles through the phase's remaining windows)
+    int wdf = 0;
+    if (sched)
+      for (int s = 0; s < S; ++s) wdf = std::max(wdf, L.sys(s)->host_ints[2]);
+    L.nlaunch += nodes_fp32 * (w->host_ints[0] - wdf) + nodes_df * wdf;
+  }
   for (int s = 0; s < S; ++s) {
     Workspace* y = L.sys(s);
-    int ru_host = 0, wins_df[3] = {0, 0, 0};
-    LQ_CUDA(cudaMemcpy(&ru_host, y->ru_count, sizeof(int), cudaMemcpyDeviceToHost));
-    LQ_CUDA(cudaMemcpy(&y->shift_iters_host, &y->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost));
-    LQ_CUDA(cudaMemcpy(wins_df, &y->sd->windows_run, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    const int ru_host = y->host_ints[4];
+    const int wins_df[3] = {y->host_ints[0], y->host_ints[1], y->host_ints[2]};
+    y->shift_iters_host = y->host_ints[3];
     const StatusWords last = y->host_status[0];
     CoreOut& o = out[s];
     o.iters = last.iter;
@@ -1730,8 +1732,8 @@ int run_mshift_multi(lqcd_ctx* ctx, int S, const double* shifts, const double* r
           if (!(tres[s][k] <= tol)) status = LQCD_ERR_NOT_CONVERGED;
     }
     if (y->xdfmode && bb != 0.0) {
-      for (int k = 0; k < n; ++k) LQ_CUDA(launch_df_to_fp64(g, y->xdf[k], y->xk[k], w->st));
-      ctx->launches += n;
+      LQ_CUDA(launch_df_to_fp64_many(g, y->xdf, y->xk, n, w->st));
+      ctx->launches += 1;
     }
     if (bb == 0.0) {
       for (int k = 0; k < n; ++k) {
