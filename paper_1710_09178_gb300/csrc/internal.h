@@ -1,6 +1,8 @@
 // internal.h - host-side declarations shared by the translation units of liblqcd.so.
 #pragma once
 
+#include <functional>
+
 #include <cuda_runtime.h>
 
 #include <string>
@@ -287,8 +289,10 @@ constexpr int kMrhsSlots = 64;
 int mrhs_prepare(lqcd_ctx* ctx, int prec, int m, void* const** rhs_out);
 // sys_iters (may be null): per system j, the iterations it ran until it met its target (0: it was not
 // iterated; a system still short of it at maxiter gets *iters)
+// before_wait (may be null): called once the solve is enqueued, to enqueue more work on st (the
+// corrections and the next checks) before the host waits for all of it
 int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter, cudaStream_t st,
-               int* iters, int* status, int* sys_iters = nullptr);
+               int* iters, int* status, int* sys_iters = nullptr, const std::function<int()>* before_wait = nullptr);
 void* const* mrhs_solutions(lqcd_ctx* ctx);
 void mrhs_release(lqcd_ctx* ctx);
 

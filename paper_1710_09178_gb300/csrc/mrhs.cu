@@ -494,7 +494,7 @@ static cudaError_t enqueue_mrhs_iteration(lqcd_ctx* ctx, MrhsWorkspace* mw, cons
 // Solve (A + sigma_j) e_j = r_j (r_j already in the workspace's r buffers) until
 // |r_j| <= rel_j |r_j(0)| for every j, or maxiter.  Returns iterations in *iters.
 int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double* rel, int maxiter,
-               cudaStream_t st, int* iters, int* status, int* sys_iters) {
+               cudaStream_t st, int* iters, int* status, int* sys_iters, const std::function<int()>* before_wait) {
   if (m < 1 || m > kMrhsMax) return fail(ctx, LQCD_ERR_ARG, "mrhs: too many systems");
   int it_sys[kMrhsMax];
   MrhsWorkspace* mw = ctx->mrhs;
@@ -532,11 +532,16 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
     ctx->launches += nl;
     *iters = hs[0];
     *status = hs[3];
-    if (sys_iters) {
+    if (before_wait) {
+      const int rc = (*before_wait)();
+      if (rc != LQCD_OK) return rc;
+    }
+    if (sys_iters || before_wait) {
       if ((e = cudaMemcpyAsync(it_sys, mw->md->it_sys, sizeof(int) * m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_check(ctx, e, "mrhs readback");
-      for (int j = 0; j < m; ++j) sys_iters[j] = it_sys[j];
+      if (sys_iters)
+        for (int j = 0; j < m; ++j) sys_iters[j] = it_sys[j];
     }
     return LQCD_OK;
   }
@@ -603,6 +608,10 @@ int mrhs_solve(lqcd_ctx* ctx, int prec, int m, const double* sigma, const double
   if (sys_iters &&
       (e = cudaMemcpyAsync(it_sys, mw->md->it_sys, sizeof(int) * m, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_check(ctx, e, "mrhs readback");
+  if (before_wait) {
+    const int rc = (*before_wait)();
+    if (rc != LQCD_OK) return rc;
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_check(ctx, e, "mrhs sync");
   ctx->launches += nl + (long long)passes * mw->nodes_per_pass;
   *iters = hs[0];

@@ -1226,7 +1226,10 @@ struct CoreOut {
 
 // Solve (A + shifts[k]) x_k = b for all k, for each of the L.S systems (the sources in each
 // system's b64, the solutions in its run_solutions()).
-static int solve_core(Launcher& L, const double* shifts, int n, double tol, int maxiter, bool use_ru, CoreOut* out) {
+// before_wait (may be null): called once the solve and its read-backs are enqueued, to enqueue more work
+// on the solve's stream (the certification) before the host waits for all of it.
+static int solve_core(Launcher& L, const double* shifts, int n, double tol, int maxiter, bool use_ru, CoreOut* out,
+                      const std::function<int()>* before_wait = nullptr) {
   lqcd_ctx* ctx = L.ctx;
   Workspace* w = L.w;
   const int S = L.S;
@@ -1399,6 +1402,10 @@ static int solve_core(Launcher& L, const double* shifts, int n, double tol, int 
     LQ_CUDA(cudaMemcpyAsync(y->host_ints + 3, &y->sd->shift_iters, sizeof(int), cudaMemcpyDeviceToHost, w->st));
     LQ_CUDA(cudaMemcpyAsync(y->host_ints + 4, y->ru_count, sizeof(int), cudaMemcpyDeviceToHost, w->st));
   }
+  if (before_wait) {
+    const int rc = (*before_wait)();
+    if (rc != LQCD_OK) return rc;
+  }
   LQ_CUDA(cudaStreamSynchronize(w->st));
   if (nodes_fp32 >= 0) {
     // kernel nodes per window x windows run, in each phase (system 0 counts every window of both loops; a
@@ -1507,53 +1514,75 @@ static int true_residuals(lqcd_ctx* ctx, Workspace* w, const double* shifts, con
   return LQCD_OK;
 }
 
-// The true residuals of several systems' solutions (held as (hi, lo) pairs) at once: for every shift k,
-// one double-FP32 residual launch pair over the systems that list k (kernels over gridDim.y, each
-// system with its own arithmetic and buffers, so each residual is the bits of its own check), then
-// one wait for all.  ks[s]: the shifts of system s; keep (may be null): the residual of (s, k) goes
-// to keep[s * n + k], the refinement's right-hand side.
-static int true_residuals_joint(lqcd_ctx* ctx, const Launcher& L, const double* shifts, int n,
-                                const std::vector<int>* ks, const double* bb, double (*out)[kMaxShifts],
-                                void* const* keep) {
+// The double-FP32 true residuals of the shifts ks[s] of every system (solutions held as (hi, lo) pairs)
+// enqueued, with their |r|^2 copied to the systems' host_scal[k]; no wait.  One system: four shifts per
+// launch pair (slots of enqueue_resid_df_slots); several: for every shift one launch pair over the
+// systems that list it (blockIdx.y = system).  Either way each residual is computed by the arithmetic
+// of a check of its own, so it is the same bits.  keep (may be null): the residual of (s, k) goes to
+// keep[s * n + k], the refinement's right-hand side.
+static int enqueue_checks(lqcd_ctx* ctx, const Launcher& L, const double* shifts, int n, const std::vector<int>* ks,
+                          void* const* keep) {
   Workspace* w = L.w;
-  for (int k = 0; k < n; ++k) {
-    Launcher Lk{ctx, nullptr, L.g, 0};
-    ResidTarget t[kMaxRhs];
-    int cnt = 0;
-    for (int s = 0; s < L.S; ++s) {
-      if (std::find(ks[s].begin(), ks[s].end(), k) == ks[s].end()) continue;
-      Workspace* y = L.sys(s);
-      if (cnt == 0) Lk.w = y;  // every system runs on system 0's stream
-      else Lk.more[cnt] = y;
-      t[cnt] = ResidTarget{run_solutions(y)[k], keep ? static_cast<float2*>(keep[s * n + k]) : nullptr,
-                           &y->sd->scal[4 + k], nullptr};
-      ++cnt;
+  if (L.S == 1) {
+    const std::vector<int>& kk = ks[0];
+    double2* const* xs = run_solutions(w);
+    for (size_t j0 = 0; j0 < kk.size(); j0 += kMaxRhs) {
+      const int nt = (int)std::min<size_t>(kMaxRhs, kk.size() - j0);
+      ResidTarget t[kMaxRhs];
+      double sig[kMaxRhs];
+      for (int u = 0; u < nt; ++u) {
+        const int k = kk[j0 + u];
+        t[u] = ResidTarget{xs[k], keep ? static_cast<float2*>(keep[k]) : nullptr, &w->sd->scal[4 + k], nullptr};
+        sig[u] = shifts[k];
+      }
+      Launcher Lc{ctx, w, L.g, 0};
+      LQ_CUDA(enqueue_resid_df_slots(Lc, t, sig, nt));
+      ctx->launches += Lc.nlaunch;
     }
-    if (cnt == 0) continue;
-    Lk.S = cnt;
-    LQ_CUDA(enqueue_resid_df(Lk, t, shifts[k], false));
-    ctx->launches += Lk.nlaunch;
+  } else {
+    for (int k = 0; k < n; ++k) {
+      Launcher Lk{ctx, nullptr, L.g, 0};
+      ResidTarget t[kMaxRhs];
+      int cnt = 0;
+      for (int s = 0; s < L.S; ++s) {
+        if (std::find(ks[s].begin(), ks[s].end(), k) == ks[s].end()) continue;
+        Workspace* y = L.sys(s);
+        if (cnt == 0) Lk.w = y;  // every system runs on system 0's stream
+        else Lk.more[cnt] = y;
+        t[cnt] = ResidTarget{run_solutions(y)[k], keep ? static_cast<float2*>(keep[s * n + k]) : nullptr,
+                             &y->sd->scal[4 + k], nullptr};
+        ++cnt;
+      }
+      if (cnt == 0) continue;
+      Lk.S = cnt;
+      LQ_CUDA(enqueue_resid_df(Lk, t, shifts[k], false));
+      ctx->launches += Lk.nlaunch;
+    }
   }
   for (int s = 0; s < L.S; ++s) {
+    if (ks[s].empty()) continue;
     Workspace* y = L.sys(s);
     LQ_CUDA(cudaMemcpyAsync(y->host_scal, &y->sd->scal[4], sizeof(double) * n, cudaMemcpyDeviceToHost, w->st));
   }
-  LQ_CUDA(cudaStreamSynchronize(w->st));
-  for (int s = 0; s < L.S; ++s)
-    for (int k : ks[s]) out[s][k] = sqrt(L.sys(s)->host_scal[k] / bb[s]);
   return LQCD_OK;
 }
 
-// Certification and refinement of S > 1 systems together (solutions as (hi, lo) pairs, S n <=
-// kMrhsSlots): the checks as above, and per round one multi-RHS correction solve for every failing
-// (system, shift) pair, slot s n + k.  Each pair's correction is computed as in a solve of its own
-// system alone (its CG, its scalars and its sums do not depend on the other slots), so the results
-// are the same bits as system by system, with one wait per step instead of one per system; the
-// refinement iterations reported for a system are those its own slots ran.  One difference: a
-// non-finite correction in any slot ends the refinement of every system.
-static int post_solve_joint(lqcd_ctx* ctx, const Launcher& L, int prec, const double* shifts, int n, double tol,
-                            int maxiter, const int* st_main, const double* bb, double (*tres)[kMaxShifts],
-                            int* refine_iters, int* refined, int* rounds_done) {
+// after the wait: the relative true residuals of the checked shifts
+static void read_checks(const Launcher& L, const std::vector<int>* ks, const double* bb, double (*out)[kMaxShifts]) {
+  for (int s = 0; s < L.S; ++s)
+    for (int k : ks[s]) out[s][k] = sqrt(L.sys(s)->host_scal[k] / bb[s]);
+}
+
+// Refinement of the S systems after their certification (tres, read; solutions as (hi, lo) pairs, S n <=
+// kMrhsSlots; rhs: the refinement's right-hand sides, filled by the checks): per round one multi-RHS
+// correction solve for every failing (system, shift) pair, slot s n + k, its corrections and the new
+// checks enqueued behind it, and one wait for all.  Each pair's correction is computed as in a solve of
+// its own system alone (its CG, its scalars and its sums do not depend on the other slots), so the results
+// are the same bits as system by system; the refinement iterations reported for a system are those its
+// own slots ran.  One difference: a non-finite correction in any slot ends the refinement of every system.
+static int refine_all(lqcd_ctx* ctx, const Launcher& L, int prec, const double* shifts, int n, double tol, int maxiter,
+                      const int* st_main, const double* bb, void* const* rhs, double (*tres)[kMaxShifts],
+                      int* refine_iters, int* refined, int* rounds_done) {
   const int S = L.S;
   Workspace* w = L.w;
   bool refine[kMaxRhs], refine_any = false;
@@ -1561,19 +1590,14 @@ static int post_solve_joint(lqcd_ctx* ctx, const Launcher& L, int prec, const do
     refine[s] = ctx->refine && st_main[s] == LQCD_OK;
     refine_any = refine_any || refine[s];
   }
-  void* const* rhs = nullptr;
-  int rc;
-  if (refine_any && (rc = mrhs_prepare(ctx, prec, S * n, &rhs)) != LQCD_OK) return rc;
+  if (!refine_any) return LQCD_OK;
   std::vector<int> ks[kMaxRhs];
-  for (int s = 0; s < S; ++s)
-    for (int k = 0; k < n; ++k) ks[s].push_back(k);
-  if ((rc = true_residuals_joint(ctx, L, shifts, n, ks, bb, tres, rhs)) != LQCD_OK) return rc;
   double sig[kMrhsSlots], rel[kMrhsSlots];
   int its[kMrhsSlots];
   for (int s = 0; s < S; ++s)
     for (int k = 0; k < n; ++k) sig[s * n + k] = shifts[k];
   const int n3 = 3 * L.g.vh;
-  for (int round = 0; refine_any && round < 4; ++round) {
+  for (int round = 0; round < 4; ++round) {
     bool any = false;
     for (int s = 0; s < S; ++s) {
       ks[s].clear();
@@ -1588,26 +1612,32 @@ static int post_solve_joint(lqcd_ctx* ctx, const Launcher& L, int prec, const do
       }
     }
     if (!any) break;
+    // behind the correction solve: x_k += e_k for the failing pairs and their new checks
+    const std::function<int()> next = [&]() -> int {
+      void* const* es = mrhs_solutions(ctx);
+      for (int s = 0; s < S; ++s) {
+        Workspace* y = L.sys(s);
+        for (int k : ks[s]) {
+          add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(y->xdf[k]),
+                                                                         static_cast<const float2*>(es[s * n + k]));
+          ctx->launches += 1;
+        }
+      }
+      LQ_CUDA(cudaGetLastError());
+      return enqueue_checks(ctx, L, shifts, n, ks, rhs);
+    };
     int it2 = 0, st2 = LQCD_OK;
-    if ((rc = mrhs_solve(ctx, prec, S * n, sig, rel, maxiter, w->st, &it2, &st2, its)) != LQCD_OK) return rc;
-    void* const* es = mrhs_solutions(ctx);
+    int rc = mrhs_solve(ctx, prec, S * n, sig, rel, maxiter, w->st, &it2, &st2, its, &next);
+    if (rc != LQCD_OK) return rc;
     for (int s = 0; s < S; ++s) {
       if (ks[s].empty()) continue;
-      Workspace* y = L.sys(s);
       int mx = 0;
-      for (int k : ks[s]) {
-        const int j = s * n + k;
-        mx = std::max(mx, its[j] > 0 ? its[j] : it2);
-        add_correction_df_kernel<<<(n3 + 255) / 256, 256, 0, w->st>>>(n3, static_cast<float2*>(y->xdf[k]),
-                                                                       static_cast<const float2*>(es[j]));
-        ctx->launches += 1;
-      }
+      for (int k : ks[s]) mx = std::max(mx, its[s * n + k] > 0 ? its[s * n + k] : it2);
       refine_iters[s] += mx;
       if (round == 0) refined[s] = (int)ks[s].size();
       rounds_done[s] = round + 1;
     }
-    LQ_CUDA(cudaGetLastError());
-    if ((rc = true_residuals_joint(ctx, L, shifts, n, ks, bb, tres, rhs)) != LQCD_OK) return rc;
+    read_checks(L, ks, bb, tres);
     if (st2 == LQCD_ERR_NONFINITE) break;
   }
   return LQCD_OK;
@@ -1643,31 +1673,45 @@ int run_mshift_multi(lqcd_ctx* ctx, int S, const double* shifts, const double* r
   // The solutions live as (hi, lo) FP32 pairs through the solve, the checks and the refinement
   // (every mode but LQCD_FP64) and become FP64 at the end; LQCD_DF64 needs no reliable updates.
   const bool dfsolve = prec == LQCD_DF64;
+  // Solutions kept as (hi, lo) pairs with every (system, shift) pair within the refinement's slots: the
+  // certification is enqueued right behind the solve and read in the same wait as its status (it is
+  // of no use where the solve turns out non-finite or a source zero: then the systems are checked one by
+  // one below); every system's |b|^2 comes back in that wait too.
+  bool fast = S * n <= kMrhsSlots;
+  for (int s = 0; s < S; ++s) fast = fast && L.sys(s)->xdfmode;
+  void* const* rhs = nullptr;
+  if (fast && ctx->refine && (rc = mrhs_prepare(ctx, prec, S * n, &rhs)) != LQCD_OK) return rc;
+  std::vector<int> all_ks[kMaxRhs];
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < n; ++k) all_ks[s].push_back(k);
+  const std::function<int()> behind_solve = [&]() -> int {
+    for (int s = 0; s < S; ++s) {
+      Workspace* y = L.sys(s);
+      LQ_CUDA(cudaMemcpyAsync(&y->host_scal[kMaxShifts + 3], &y->sd->bb, sizeof(double), cudaMemcpyDeviceToHost,
+                              w->st));
+    }
+    return fast ? enqueue_checks(ctx, L, shifts, n, all_ks, rhs) : LQCD_OK;
+  };
   CoreOut core[kMaxRhs];
-  rc = solve_core(L, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, core);
+  rc = solve_core(L, shifts, n, tol, maxiter, prec != LQCD_FP64 && !dfsolve, core, &behind_solve);
   if (rc != LQCD_OK) return rc;
 
   int status_all = LQCD_OK;
   int refine_iters[kMaxRhs] = {}, refined[kMaxRhs] = {}, rounds_done[kMaxRhs] = {};
   double tres[kMaxRhs][kMaxShifts];
-  // |b|^2 of every system, one wait
   double bbs[kMaxRhs];
   int st_mains[kMaxRhs];
-  for (int s = 0; s < S; ++s) {
-    Workspace* y = L.sys(s);
-    LQ_CUDA(cudaMemcpyAsync(&y->host_scal[kMaxShifts + 3], &y->sd->bb, sizeof(double), cudaMemcpyDeviceToHost, w->st));
-    st_mains[s] = core[s].status;
-    for (int k = 0; k < n; ++k) tres[s][k] = 0.0;
-  }
-  LQ_CUDA(cudaStreamSynchronize(w->st));
-  bool joint = S > 1 && S * n <= kMrhsSlots;  // every system with a nonzero, finite source in double-FP32
+  bool joint = fast;  // every system with a nonzero, finite source
   for (int s = 0; s < S; ++s) {
     bbs[s] = L.sys(s)->host_scal[kMaxShifts + 3];
-    joint = joint && L.sys(s)->xdfmode && bbs[s] > 0.0 && st_mains[s] != LQCD_ERR_NONFINITE;
+    st_mains[s] = core[s].status;
+    for (int k = 0; k < n; ++k) tres[s][k] = 0.0;
+    joint = joint && bbs[s] > 0.0 && st_mains[s] != LQCD_ERR_NONFINITE;
   }
   if (joint) {
-    rc = post_solve_joint(ctx, L, prec, shifts, n, tol, maxiter, st_mains, bbs, tres, refine_iters, refined,
-                          rounds_done);
+    read_checks(L, all_ks, bbs, tres);
+    rc = refine_all(ctx, L, prec, shifts, n, tol, maxiter, st_mains, bbs, rhs, tres, refine_iters, refined,
+                    rounds_done);
     if (rc != LQCD_OK) return rc;
   }
   for (int s = 0; s < S; ++s) {
