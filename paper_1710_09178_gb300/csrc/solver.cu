@@ -1445,6 +1445,33 @@ __global__ void keep_residual_kernel(int n3, const double2* __restrict__ r64, vo
 }
 
 // x ((hi, lo) FP32 pairs) += e (FP32)
+// The n solutions of a solve from (hi, lo) FP32 pairs to FP64 (x = hi + lo, exact) in one launch
+// (blockIdx.y = solution)
+struct DfToFp64Args {
+  const float2* v[kMaxShifts];
+  double2* x[kMaxShifts];
+};
+__global__ void __launch_bounds__(256) df_to_fp64_many_kernel(int n3, const __grid_constant__ DfToFp64Args a) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n3) return;
+  const float2* v = a.v[blockIdx.y];
+  const float2 h = v[o], l = v[o + n3];
+  a.x[blockIdx.y][o] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+}
+
+cudaError_t launch_df_to_fp64_many(const Geom& g, void* const* v, double2* const* x, int n, cudaStream_t st) {
+  if (n < 1 || n > kMaxShifts) return cudaErrorInvalidValue;
+  DfToFp64Args a;
+  memset(&a, 0, sizeof(a));
+  for (int k = 0; k < n; ++k) {
+    a.v[k] = static_cast<const float2*>(v[k]);
+    a.x[k] = x[k];
+  }
+  const int n3 = 3 * g.vh;
+  df_to_fp64_many_kernel<<<dim3((n3 + 255) / 256, n), 256, 0, st>>>(n3, a);
+  return cudaGetLastError();
+}
+
 __global__ void add_correction_df_kernel(int n3, float2* __restrict__ x, const float2* __restrict__ e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
