@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "bounds.h"
+#include "dfdiv.h"
 #include "lqcd.h"
 
 namespace lqcd {
@@ -770,9 +771,9 @@ __device__ __forceinline__ double warp_sum_df(const float2* p, int n) {
 // The partials are loaded whatever the flag says (they are always in bounds), so that no load
 // waits for the flag.
 struct PartialsRatio {
-  double sum, ratio;
+  double sum, ratio;  // FP64 (the double-FP32 form fills them only when asked: want64)
   float ratio_f;
-  float2 ratio_df;
+  float2 ratio_df, sum_df;
   int stop;
 };
 
@@ -796,70 +797,121 @@ __device__ __forceinline__ double warp_tree64(double v) {
 
 constexpr int kSumLanes = 128;  // virtual lanes of partials_ratio's fixed summation order
 
-template <bool SUM_OVER_X, bool DF>
-__device__ __forceinline__ PartialsRatio partials_ratio(const double* partials, int n, double x, bool skip = false) {
+// The FP64 form (the FP64 solve): FP64 partials, x and quotient.
+template <bool SUM_OVER_X>
+__device__ __forceinline__ PartialsRatio partials_ratio64(const double* partials, int n, double x, bool skip = false) {
   __shared__ PartialsRatio res;
   __shared__ double gsum[kSumLanes / 32];
   const int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
   constexpr int kLoads = 8;  // entries per virtual lane loaded before the adds of a round
-  if constexpr (DF) {
-    const float2* p = reinterpret_cast<const float2*>(partials);
-    for (int v = t; v < kSumLanes; v += nt) {  // the same trip count in every lane of a warp
-      float s = 0.f, c = 0.f;
-      for (int b = v; b < n; b += kLoads * kSumLanes) {
-        float2 e[kLoads];
+  for (int v = t; v < kSumLanes; v += nt) {  // the same trip count in every lane of a warp
+    double s = 0.0;
+    for (int b = v; b < n; b += kLoads * kSumLanes) {
+      double e[kLoads];
 #pragma unroll
-        for (int j = 0; j < kLoads; ++j)
-          e[j] = (b + j * kSumLanes < n) ? __ldcg(p + b + j * kSumLanes) : make_float2(0.f, 0.f);
+      for (int j = 0; j < kLoads; ++j) e[j] = (b + j * kSumLanes < n) ? __ldcg(partials + b + j * kSumLanes) : 0.0;
 #pragma unroll
-        for (int j = 0; j < kLoads; ++j) df_add(s, c, e[j].x, e[j].y);
-      }
-      const float2 w = warp_tree_df(df_norm(s, c));
-      if (lane == 0) reinterpret_cast<float2*>(gsum)[v >> 5] = w;
+      for (int j = 0; j < kLoads; ++j) s += e[j];
     }
-    if (__syncthreads_or(skip)) {
-      PartialsRatio r{};
-      r.stop = 1;
-      return r;
-    }
-    if (t < 32) {
-      const float2 u = warp_tree_df(t < kSumLanes / 32 ? reinterpret_cast<const float2*>(gsum)[t] : make_float2(0.f, 0.f));
-      if (t == 0) gsum[0] = (double)u.x + (double)u.y;
-    }
-  } else {
-    for (int v = t; v < kSumLanes; v += nt) {
-      double s = 0.0;
-      for (int b = v; b < n; b += kLoads * kSumLanes) {
-        double e[kLoads];
-#pragma unroll
-        for (int j = 0; j < kLoads; ++j) e[j] = (b + j * kSumLanes < n) ? __ldcg(partials + b + j * kSumLanes) : 0.0;
-#pragma unroll
-        for (int j = 0; j < kLoads; ++j) s += e[j];
-      }
-      const double w = warp_tree64(s);
-      if (lane == 0) gsum[v >> 5] = w;
-    }
-    if (__syncthreads_or(skip)) {
-      PartialsRatio r{};
-      r.stop = 1;
-      return r;
-    }
-    if (t < 32) {
-      const double u = warp_tree64(t < kSumLanes / 32 ? gsum[t] : 0.0);
-      if (t == 0) gsum[0] = u;
-    }
+    const double w = warp_tree64(s);
+    if (lane == 0) gsum[v >> 5] = w;
   }
-  if (t == 0) {
-    const double v = gsum[0];
-    const double q = SUM_OVER_X ? v / x : x / v;
-    res.sum = v;
-    res.ratio = q;
-    res.ratio_df = split_hi_lo(q);
-    res.ratio_f = res.ratio_df.x;
-    res.stop = 0;
+  if (__syncthreads_or(skip)) {
+    PartialsRatio r{};
+    r.stop = 1;
+    return r;
+  }
+  if (t < 32) {
+    const double u = warp_tree64(t < kSumLanes / 32 ? gsum[t] : 0.0);
+    if (t == 0) {
+      const double q = SUM_OVER_X ? u / x : x / u;
+      res.sum = u;
+      res.ratio = q;
+      res.ratio_df = split_hi_lo(q);
+      res.ratio_f = res.ratio_df.x;
+      res.sum_df = split_hi_lo(u);
+      res.stop = 0;
+    }
   }
   __syncthreads();
   return res;
+}
+
+// The double-FP32 form (the FP32 and double-FP32 solves): the partials and x are (hi, lo) pairs, and the
+// quotient is Dekker's double-FP32 division (dfdiv.h), so that no block but one runs an FP64 instruction
+// (GB300's FP64 pipe is 1/64 of the FP32 rate, and this chain sits between the block's loads and its
+// update).  want64: thread 0 also forms the FP64 values of the sum and the quotient, exactly hi + lo (the
+// block that stores the solve's scalars).
+template <bool SUM_OVER_X>
+__device__ __forceinline__ PartialsRatio partials_ratio_df(const double* partials, int n, float2 x, bool skip,
+                                                           bool want64) {
+  __shared__ PartialsRatio res;
+  __shared__ float2 gsum[kSumLanes / 32];
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
+  constexpr int kLoads = 8;  // entries per virtual lane loaded before the adds of a round
+  const float2* p = reinterpret_cast<const float2*>(partials);
+  for (int v = t; v < kSumLanes; v += nt) {  // the same trip count in every lane of a warp
+    float s = 0.f, c = 0.f;
+    for (int b = v; b < n; b += kLoads * kSumLanes) {
+      float2 e[kLoads];
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j)
+        e[j] = (b + j * kSumLanes < n) ? __ldcg(p + b + j * kSumLanes) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) df_add(s, c, e[j].x, e[j].y);
+    }
+    const float2 w = warp_tree_df(df_norm(s, c));
+    if (lane == 0) gsum[v >> 5] = w;
+  }
+  if (__syncthreads_or(skip)) {
+    PartialsRatio r{};
+    r.stop = 1;
+    return r;
+  }
+  if (t < 32) {
+    const float2 u = warp_tree_df(t < kSumLanes / 32 ? gsum[t] : make_float2(0.f, 0.f));
+    if (t == 0) {
+      const DfPair q = SUM_OVER_X ? df_div_pair(u.x, u.y, x.x, x.y) : df_div_pair(x.x, x.y, u.x, u.y);
+      res.sum_df = u;
+      res.ratio_df = make_float2(q.hi, q.lo);
+      res.ratio_f = q.hi;
+      if (want64) {
+        res.sum = (double)u.x + (double)u.y;
+        res.ratio = (double)q.hi + (double)q.lo;
+      }
+      res.stop = 0;
+    }
+  }
+  __syncthreads();
+  return res;
+}
+
+// Sum over the block of per-thread FP32 values as a double-FP32 pair: in FP32 within each warp (a fixed
+// xor tree, as block_sum_mixed), across the warps with TwoSum in a fixed tree; valid in thread 0.
+__device__ __forceinline__ float2 block_sum_f_df(float v) {
+  __shared__ float2 red_fd[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();  // red_fd may still be read by an earlier call
+  if (l == 0) red_fd[w] = make_float2(v, 0.f);
+  __syncthreads();
+  float2 u = make_float2(0.f, 0.f);
+  if (w == 0) u = warp_tree_df(l < nw ? red_fd[l] : make_float2(0.f, 0.f));
+  return u;
+}
+
+// The same for per-thread double-FP32 values (s, c): TwoSum shuffle trees within and across the warps.
+__device__ __forceinline__ float2 block_sum_df_df(float s, float c) {
+  __shared__ float2 red_dd[32];
+  float2 v = warp_tree_df(df_norm(s, c));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red_dd[w] = v;
+  __syncthreads();
+  v = make_float2(0.f, 0.f);
+  if (w == 0) v = warp_tree_df(l < nw ? red_dd[l] : make_float2(0.f, 0.f));
+  return v;
 }
 
 // A block's FP64 sum v as partial idx: a double-FP32 pair in the entry's 8 bytes (DF) or FP64

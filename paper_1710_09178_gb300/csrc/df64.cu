@@ -194,11 +194,12 @@ __global__ void __launch_bounds__(128, 4) df_dslash_kernel(Geom g, const __grid_
         df_mac(ds, dc, xh.y, xl.y, im.x, im.y);
       }
     }
-    const double bs = block_sum_df(ds, dc);
     if (!k.ticket) {  // inside the solve: the r update sums the (hi, lo) partials itself
-      if (threadIdx.x == 0) store_partial<true>(k.partials, blockIdx.x, bs);
+      const float2 bs = block_sum_df_df(ds, dc);
+      if (threadIdx.x == 0) reinterpret_cast<float2*>(k.partials)[blockIdx.x] = bs;
       return;
     }
+    const double bs = block_sum_df(ds, dc);
     if (publish_partial(k.partials, k.ticket, bs)) {
       const double tot = gather_partials(k.partials, k.ticket);
       if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __gri
   const int dn = *reinterpret_cast<const volatile int*>(&sd->done), ht = a.halt ? *a.halt : 0;  // both in flight
   const bool skip = (dn | ht) != 0;
   const int m = sd->m;
-  const double rr = sd->rr;
+  const float2 rr_df = sd->rr_df;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __gri
       rv[3][c] = a.q[ol];
     }
   }
-  const PartialsRatio pa = partials_ratio<false, true>(a.pq_partials, a.n_pq, rr, skip);
+  const PartialsRatio pa = partials_ratio_df<false>(a.pq_partials, a.n_pq, rr_df, skip, scalar_block);
   if (pa.stop) return;  // the same in every thread of the block
   const bool mine = site && m < kWindow;
   if (scalar_block) {
@@ -318,8 +319,8 @@ __global__ void __launch_bounds__(256, 4) df_r_update_kernel(Geom g, const __gri
       df_mac(ls, lc, h.y, l.y, h.y, l.y);
     }
   }
-  const double bs = block_sum_df(ls, lc);
-  if (threadIdx.x == 0) store_partial<true>(a.rr_partials, blockIdx.x, bs);
+  const float2 bs = block_sum_df_df(ls, lc);
+  if (threadIdx.x == 0) reinterpret_cast<float2*>(a.rr_partials)[blockIdx.x] = bs;
 }
 
 // p = r + beta p, one site per thread; beta from the r update's partials; one extra block runs
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, const __gri
   SolverDev* sd = a.sd;
   const int dn = *reinterpret_cast<const volatile int*>(&sd->done), ht = a.halt ? *a.halt : 0;  // both in flight
   const bool skip = (dn | ht) != 0;
-  const double rr_b = sd->rr_b;
+  const float2 rr_b_df = sd->rr_b_df;
   const int vh = g.vh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(256, 4) df_p_update_kernel(Geom g, const __gri
       rv[3][c] = a.p[ol];
     }
   }
-  const PartialsRatio pb = partials_ratio<true, true>(a.rr_partials, (int)gridDim.x - 1, rr_b, skip);
+  const PartialsRatio pb = partials_ratio_df<true>(a.rr_partials, (int)gridDim.x - 1, rr_b_df, skip, scalar_block);
   if (pb.stop) return;  // the same in every thread of the block
   if (scalar_block) {
     solver_beta_step(sd, pb);

@@ -152,14 +152,17 @@ __device__ __forceinline__ void dslash_epilogue(const KArgs& k, const Vec3<T>& d
     }
   }
   if constexpr (EPI != (int)Epi::Plain) {
-    double bs = block_sum_mixed(dsite);
     if (!k.ticket) {  // the next kernel sums the per-block partials itself (FP32: as (hi, lo) pairs)
-      if (threadIdx.x == 0) {
-        if constexpr (sizeof(T) == 4) reinterpret_cast<float2*>(k.partials)[blockIdx.x] = split_hi_lo(bs);
-        else k.partials[blockIdx.x] = bs;
+      if constexpr (sizeof(T) == 4) {
+        const float2 bs = block_sum_f_df(dsite);
+        if (threadIdx.x == 0) reinterpret_cast<float2*>(k.partials)[blockIdx.x] = bs;
+      } else {
+        const double bs = block_sum_mixed(dsite);
+        if (threadIdx.x == 0) k.partials[blockIdx.x] = bs;
       }
       return;
     }
+    double bs = block_sum_mixed(dsite);
     if (publish_partial(k.partials, k.ticket, bs)) {
       double tot = gather_partials(k.partials, k.ticket);
       if (threadIdx.x == 0 && k.dot_out) *k.dot_out = tot;
@@ -478,12 +481,15 @@ static cudaError_t launch_tps(const Geom& g, const KArgs& k, Epi epi, cudaStream
 
 template <int LF>
 static cudaError_t launch_lf(const Geom& g, const KArgs& k, Epi epi, int tps, int bs, cudaStream_t st, bool pdl) {
-  if constexpr (LF == kL64) return launch_tps<LF, 1>(g, k, epi, st, 128, pdl);  // FP64 is arithmetic-bound
-  switch (tps) {
-    case 1: return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);
-    case 2: return launch_tps<LF, 2>(g, k, epi, st, bs, pdl);
-    case 4: return launch_tps<LF, 4>(g, k, epi, st, bs, pdl);
-    default: return launch_tps<LF, 8>(g, k, epi, st, bs, pdl);
+  if constexpr (LF == kL64) {
+    return launch_tps<LF, 1>(g, k, epi, st, 128, pdl);  // FP64 is arithmetic-bound: one thread per site
+  } else {
+    switch (tps) {
+      case 1: return launch_tps<LF, 1>(g, k, epi, st, bs, pdl);
+      case 2: return launch_tps<LF, 2>(g, k, epi, st, bs, pdl);
+      case 4: return launch_tps<LF, 4>(g, k, epi, st, bs, pdl);
+      default: return launch_tps<LF, 8>(g, k, epi, st, bs, pdl);
+    }
   }
 }
 

@@ -46,6 +46,7 @@ struct SolverDev {
   // the vector kernels convert nothing from FP64 per thread
   float alpha_f, beta_f, a_diag_f;
   float2 alpha_df, beta_df, a_diag_df;
+  float2 rr_df, rr_b_df;  // rr and rr_b as (hi, lo) pairs: what the FP32 and double-FP32 update kernels read
   int iter;
   int done;        // 1: every shift stopped (or error); iteration kernels return at entry
   int status;      // LQCD_OK or LQCD_ERR_NONFINITE

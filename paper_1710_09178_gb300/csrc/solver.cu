@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, const __grid_c
   const bool skip = done_now(sd);
   const int m = sd->m;
   const double rr = sd->rr;
+  const float2 rr_df = sd->rr_df;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
   const bool site = !scalar_block && i < g.vh;
@@ -147,7 +148,9 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, const __grid_c
     q = load_vec(static_cast<const V2*>(a.q), i, g.vh);
   }
   // Re<p, q> and alpha = |r|^2 / Re<p, q>
-  const PartialsRatio pa = partials_ratio<false, sizeof(T) == 4>(a.pq_partials, a.n_pq, rr, skip);
+  PartialsRatio pa;
+  if constexpr (sizeof(T) == 4) pa = partials_ratio_df<false>(a.pq_partials, a.n_pq, rr_df, skip, scalar_block);
+  else pa = partials_ratio64<false>(a.pq_partials, a.n_pq, rr, skip);
   if (pa.stop) return;  // the same in every thread of the block
   const bool mine = site && m < kWindow;
   if (scalar_block) {
@@ -166,8 +169,13 @@ __global__ void __launch_bounds__(256, 4) r_update_kernel(Geom g, const __grid_c
     store_s<SF, T>(static_cast<char*>(a.ring) + m * a.slot_bytes, i, g.vh, r);
     loc = site_norm2(r);
   }
-  const double bs = block_sum_mixed(loc);
-  if (threadIdx.x == 0) store_partial<sizeof(T) == 4>(a.rr_partials, blockIdx.x, bs);
+  if constexpr (sizeof(T) == 4) {
+    const float2 bs = block_sum_f_df(loc);
+    if (threadIdx.x == 0) reinterpret_cast<float2*>(a.rr_partials)[blockIdx.x] = bs;
+  } else {
+    const double bs = block_sum_mixed(loc);
+    if (threadIdx.x == 0) a.rr_partials[blockIdx.x] = bs;
+  }
 }
 
 struct PUpdArgs {
@@ -189,6 +197,7 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, const __grid_c
   pdl_trigger();
   const bool skip = done_now(sd);
   const double rr_b = sd->rr_b;
+  const float2 rr_b_df = sd->rr_b_df;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool scalar_block = blockIdx.x == gridDim.x - 1;
   const bool mine = !scalar_block && i < g.vh;
@@ -198,7 +207,9 @@ __global__ void __launch_bounds__(256, 4) p_update_kernel(Geom g, const __grid_c
     p = load_vec(static_cast<const V2*>(a.p), i, g.vh);
   }
   // |r_new|^2 and beta = |r_new|^2 / |r|^2
-  const PartialsRatio pb = partials_ratio<true, sizeof(T) == 4>(a.rr_partials, a.n_rr, rr_b, skip);
+  PartialsRatio pb;
+  if constexpr (sizeof(T) == 4) pb = partials_ratio_df<true>(a.rr_partials, a.n_rr, rr_b_df, skip, scalar_block);
+  else pb = partials_ratio64<true>(a.rr_partials, a.n_rr, rr_b, skip);
   if (pb.stop) return;  // the same in every thread of the block
   if (scalar_block) {
     solver_beta_step(sd, pb);
@@ -445,6 +456,7 @@ __global__ void ru_close_kernel(const __grid_constant__ PerSys<SolverDev*> sds, 
     sd->done = 1;
   }
   sd->rr = rr;
+  sd->rr_df = split_hi_lo(rr);
   sd->rr_ru_max = rr;
   sd->iter_ru = sd->iter;
   sd->ru_skip = 1;

@@ -55,6 +55,7 @@ __device__ __forceinline__ void init_scalars(SolverDev* sd, const InitParams& ip
     sd->alpha_df = sd->beta_df = make_float2(0.f, 0.f);
     sd->bb = bb;
     sd->rr = bb;
+    sd->rr_df = split_hi_lo(bb);
     sd->stop2 = ip.tol * ip.tol * bb;
     sd->alpha = sd->beta = 0.0;
     sd->alpha_prev = 1.0;
@@ -100,6 +101,7 @@ __device__ __forceinline__ void solver_alpha_step(SolverDev* sd, const PartialsR
   const int m = sd->m;
   sd->pq = pq;
   sd->rr_b = sd->rr;
+  sd->rr_b_df = sd->rr_df;
   sd->alpha = alpha;
   sd->alpha_f = pa.ratio_f;
   sd->alpha_df = pa.ratio_df;
@@ -138,6 +140,7 @@ __device__ __forceinline__ void solver_beta_step(SolverDev* sd, const PartialsRa
   sd->beta_df = pb.ratio_df;
   sd->m = m + 1;
   sd->rr = rr_new;
+  sd->rr_df = split_hi_lo(rr_new);
   sd->iter = it;
   if (done) sd->done = 1;
   const double rmax = fmax(sd->rr_ru_max, rr_new);
