@@ -914,13 +914,6 @@ __device__ __forceinline__ float2 block_sum_df_df(float s, float c) {
   return v;
 }
 
-// A block's FP64 sum v as partial idx: a double-FP32 pair in the entry's 8 bytes (DF) or FP64
-template <bool DF>
-__device__ __forceinline__ void store_partial(double* partials, size_t idx, double v) {
-  if constexpr (DF) reinterpret_cast<float2*>(partials)[idx] = split_hi_lo(v);
-  else partials[idx] = v;
-}
-
 // In the last block: the sum of all partials in index order (identical in every thread).
 __device__ __forceinline__ double gather_partials(const double* partials, unsigned* ticket) {
   __threadfence();
