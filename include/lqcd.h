@@ -289,7 +289,10 @@ int mshift_cg(lqcd_ctx* ctx, const double* shifts, const double* residues, int n
  * solves one source at a time).  Every system runs exactly the shifted CG that mshift_cg runs on
  * it alone (the same iterations, reliable updates, phase change and refinement, with identical
  * results); they share the kernel launches, and in the FP32 iterations the Dslash loads every link
- * once for all of them.
+ * once for all of them.  After the solve their true-residual checks and their refinement run
+ * together when nrhs * n <= 64 and every source is nonzero and finite (one refinement solve per
+ * round for every failing system and shift; the results are still those of each system alone, but a
+ * non-finite correction in one system ends the refinement of all of them); otherwise system by system.
  *   nrhs    : 1 <= nrhs <= LQCD_MAX_RHS
  *   b_devs  : host array of nrhs device sources, complex128 [Vh][3] each, all distinct
  *   x_devs  : NULL, or host array of nrhs entries, each NULL or a host array of n device outputs as
