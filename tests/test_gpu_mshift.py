@@ -167,6 +167,24 @@ def test_no_graph_path_matches_graph_path():
         assert np.array_equal(a, c)  # deterministic reductions: identical bits
 
 
+@pytest.mark.parametrize("tps,bs,order", [(1, 64, 1), (2, 128, 0), (4, 64, 0), (8, 128, 1)])
+def test_converged_solve_every_launch_shape(tps, bs, order):
+    # The FP32 Dslash's launch shape (threads per site, threads per block, block-to-site order) changes
+    # the per-site sums (threads per site) and the block partials the update kernels sum (their count
+    # and grouping); whatever the shape, every shift is certified by the oracle at 1e-10 and the
+    # reported residuals are the oracle's.
+    import paper_1710_09178_gb300 as lq
+
+    dims, mass = (10, 6, 4, 6), 0.02
+    ctx, U, b, c0, res, poles = _problem(dims, mass, 12, 11, 12)
+    ctx.set_option(lq.OPT_DSLASH_TPS, tps)
+    ctx.set_option(lq.OPT_DSLASH_BS, bs)
+    ctx.set_option(lq.OPT_DSLASH_ORDER, order)
+    for prec in (FP32, FP32_R12):
+        st, xs, y = _check_converged(ctx, U, b, dims, mass, c0, res, poles, prec)
+        assert st["iterations"] > 10
+
+
 @pytest.mark.parametrize("dims,mass,npoles", [((10, 6, 4, 6), 0.05, 12), ((16, 16, 16, 8), 0.05, 14)])
 def test_reported_true_residuals_match_oracle(dims, mass, npoles):
     # The mixed modes compute reliable updates and true residuals in double-FP32 (~48-bit) instead
