@@ -50,3 +50,20 @@ def test_single_rank_needs_no_process_group():
     import bench
 
     assert bench.replica_aggregate(12.0, 4, 1, None, "cpu") == (12.0, 3.0, 3.0)
+
+
+def test_committed_ncu_records_match_the_kernel_sources():
+    # bench.py takes roofline.traffic and roofline_df.traffic (DRAM bytes per launch) from the committed
+    # ncu records only while the hashed kernel sources are the ones captured; a source change without a
+    # new capture would silently turn those figures into null.  Recapture the record (the command is in
+    # the Markdown summary beside it) whenever this fails.
+    import bench
+
+    import numpy as np
+
+    vh = int(np.prod(bench.DIMS)) // 2
+    fp32 = bench.profiled_traffic("32c8")
+    df = bench.profiled_traffic("32c8", record="df_dslash_32c8.json", files=("df64.cu", "common.cuh"))
+    # DRAM bytes of one cold launch within 10 % of the algorithmic bytes (no re-reads)
+    assert fp32 is not None and abs(fp32 / (bench.DSLASH_BYTES_PER_SITE["fp32"] * vh) - 1) < 0.1
+    assert df is not None and abs(df / (bench.DF_BYTES_PER_SITE * vh) - 1) < 0.1
