@@ -82,7 +82,8 @@ typedef struct {
 
 /*
  * lqcd_create - allocate a context for one lattice.
- *   dims   : Nx, Ny, Nz, Nt (each positive and even; LQCD_ERR_DIMS otherwise)
+ *   dims   : Nx, Ny, Nz, Nt (each positive and even, and Nx Ny Nz Nt / 2 <= 2^27 so that site
+ *            indices and every thread index stay 32-bit; LQCD_ERR_DIMS otherwise)
  *   mass   : quark mass m of M = 2m + D (A = 4 m^2 - D_eo D_oe)
  *   stream : cudaStream_t to enqueue work on (NULL = legacy default stream)
  * On success *out holds the context; on failure *out is NULL.

@@ -87,3 +87,31 @@ def rel_max(a, b):
 
 def rel_norm(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def tiled_half_index(small, tile, parity, device="cuda"):
+    """Tiling a lattice `small` (all extents even) k_mu times along each axis: for every site of the
+    large lattice's half vector of `parity`, the index of the small lattice's site it copies (torch
+    int64 on `device`).  Checkerboard index cb = l >> 1 with l = x + Nx (y + Ny (z + Nz t)); the sites
+    l and l + 1 (l even) differ only in x, so exactly one of them has the parity."""
+    torch = torch_mod()
+    large = [s * k for s, k in zip(small, tile)]
+    X, Y, Z, _ = large
+    xs, ys, zs, _ = small
+    l0 = 2 * torch.arange(int(np.prod(large)) // 2, device=device, dtype=torch.int64)
+    x0 = l0 % X
+    rest = l0 // X
+    y = rest % Y
+    rest = rest // Y
+    z = rest % Z
+    t = rest // Z
+    x = x0 + ((parity + y + z + t) & 1)
+    ls = (x % xs) + xs * ((y % ys) + ys * ((z % zs) + zs * (t % small[3])))
+    return ls >> 1
+
+
+def tiled_gauge(U_small, small, tile):
+    """The canonical (V, 4, 3, 3) gauge tensor U_small (any device) repeated k_mu times per axis."""
+    X, Y, Z, T = small
+    u = U_small.reshape(T, Z, Y, X, 4, 3, 3)
+    return u.repeat(tile[3], tile[2], tile[1], tile[0], 1, 1, 1).reshape(-1, 4, 3, 3).contiguous()

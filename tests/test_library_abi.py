@@ -40,7 +40,9 @@ def test_header_symbols_exported(lib):
 
 def test_create_rejects_bad_dims(lib):
     h = ctypes.c_void_p()
-    for dims, code in [((4, 4, 4, 3), 2), ((0, 4, 4, 4), 2), ((4, 4, -2, 4), 2)]:
+    # odd, zero and negative extents; half volumes one step above the 2^27 limit of 32-bit site indices
+    for dims, code in [((4, 4, 4, 3), 2), ((0, 4, 4, 4), 2), ((4, 4, -2, 4), 2), ((512, 512, 512, 4), 2),
+                       ((256, 256, 256, 18), 2)]:
         arr = (ctypes.c_int * 4)(*dims)
         assert lib.lqcd_create(ctypes.byref(h), arr, 0.1, None) == code
         assert not h.value
