@@ -13,6 +13,8 @@ operator acts on the tile (Section 3.2's hops only read the neighbours).
 - Mixed-precision shifted CG (Section 4) on the tiled source: every shift certified by the
   library's true residual, and every x_k within 2 kappa_k tol of the oracle's FP64 solve of the
   small lattice, tiled (the tiled solution solves the large system exactly).
+- The fermion force and action (Section 3.1) in the mixed mode against the oracle's force of the
+  small lattice, tiled.
 """
 import numpy as np
 import pytest
@@ -112,3 +114,35 @@ def test_mixed_solve_certified_against_the_tiled_oracle_solution(contexts):
     for x, c in zip(xs, res):
         yo += c * x
     assert float(torch.linalg.vector_norm(y - yo) / torch.linalg.vector_norm(yo)) < 1e-13
+
+
+def test_force_and_action_against_the_tiled_oracle(contexts):
+    # the MD force of S_f = phi^+ r(A) phi (Section 3.1) in the mixed mode: every link's force within the
+    # FP32-mode bar of the oracle's force on the small lattice, tiled; the action is the oracle's times
+    # the number of tiles (to the solves' kappa tol)
+    import torch
+
+    import paper_1710_09178_gb300 as lq
+    from oracle import force
+
+    small, large, U = contexts
+    phi = inputs.gaussian_vector(SMALL, 84)
+    c0, res, poles, _ = rational.zolotarev_inv_sqrt(12, 4 * MASS ** 2, 16 + 4 * MASS ** 2)
+    V = int(np.prod(LARGE))
+    F = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    rc, S, _ = lq.fermion_force(large, poles, res, c0, to_dev(phi)[tiled_index(0)], F=F, tol=1e-10, prec=lq.FP32,
+                                raise_on_error=False)
+    torch.cuda.synchronize()
+    assert rc == 0
+    oF = force.fermion_force(U, phi, MASS, SMALL, c0, res, poles, tol=1e-12)
+    ref = tiled_gauge(to_dev(oF), SMALL, TILE)
+    scale = float(ref.abs().max())
+    err = 0.0
+    for a in range(0, V, 1 << 22):
+        err = max(err, float((F[a:a + (1 << 22)] - ref[a:a + (1 << 22)]).abs().max()))
+    assert err <= 2e-5 * scale, err / scale
+    del F, ref
+    torch.cuda.empty_cache()
+    tiles = int(np.prod(TILE))
+    oS = force.action(U, phi, MASS, SMALL, c0, res, poles, tol=1e-12)
+    assert abs(S - tiles * oS) <= 1e-6 * abs(tiles * oS)
