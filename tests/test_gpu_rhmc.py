@@ -1,6 +1,7 @@
 """GPU parity of rhmc_trajectory (Section 3.1) against the oracle trajectory, and reversibility.
 
-Bars (FP64 solves to 1e-12): Hamiltonian pieces within 1e-9 relative; dH within 1e-7 absolute;
+Bars (FP64 solves to 1e-12): Hamiltonian pieces within 1e-9 relative; dH within 1e-7 absolute, and
+|dH| about 4 times smaller at half the step size (the integrator is second order);
 proposed links and final momenta within 1e-8; integrating back with -p returns the links to 1e-10.
 """
 import numpy as np
@@ -201,3 +202,22 @@ def test_trajectory_is_reversible_at_24c6():
     assert np.max(np.abs(back_links.cpu().numpy() - U0)) < 1e-10
     assert np.max(np.abs(back_mom.cpu().numpy() + p0)) < 1e-8
     assert abs(r1["dH"] + r2["dH"]) < 1e-6 * max(1.0, abs(r1["dH"]))
+
+
+def test_energy_error_is_second_order():
+    # Omelyan's 2MN integrator (Section 3.1 molecular dynamics) is second order: from the same links,
+    # momenta and heatbath source, halving the step size cuts |dH| by about 4
+    import paper_1710_09178_gb300 as lq
+
+    act, heat = _coeffs()
+    ctx, U0 = make_context(DIMS, MASS, gauge_seed=31)
+    p0 = _momenta(32)
+    xi = inputs.gaussian_vector(DIMS, 33)
+    dH = []
+    for n in (4, 8):
+        rc, res = lq.rhmc_trajectory(ctx, to_dev(U0), to_dev(p0), to_dev(xi), 0.5, BETA, 0.5, n, act, heat,
+                                     tol=1e-12, prec=FP64)
+        assert rc == 0
+        dH.append(res["dH"])
+    ratio = abs(dH[0]) / abs(dH[1])
+    assert 2.5 < ratio < 6.5, dH
