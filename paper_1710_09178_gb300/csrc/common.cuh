@@ -560,12 +560,6 @@ __device__ __forceinline__ Mat3<float> decode_link8(float4 A, float4 B, float sc
   return M;
 }
 
-__device__ __forceinline__ Mat3<float> load_link8(const float4* __restrict__ U, int p, int mu, int i, int vh,
-                                                  float scale, uint64_t pol) {
-  const float4* blk = U + (size_t)(p * 4 + mu) * 2 * vh;
-  return decode_link8(ld_stream(blk + i, pol), ld_stream(blk + vh + i, pol), scale);
-}
-
 // 16-bit form: int16 codes q of (re, im) of rows 0 and 1, entry = q / 32767; row 2 rebuilt
 __device__ __forceinline__ float code_lo(int w) { return (float)(short)(w & 0xffff); }
 __device__ __forceinline__ float code_hi(int w) { return (float)(w >> 16); }
@@ -582,13 +576,6 @@ __device__ __forceinline__ Mat3<float> decode_link16(int4 a, int2 b, float scale
   complete_third_row(M);
   scale_link(M, scale);
   return M;
-}
-
-__device__ __forceinline__ Mat3<float> load_link16(const char* __restrict__ U, int p, int mu, int i, int vh,
-                                                   float scale, uint64_t pol) {
-  const char* blk = U + (size_t)(p * 4 + mu) * 24 * vh;
-  return decode_link16(ld_stream(reinterpret_cast<const int4*>(blk) + i, pol),
-                       ld_stream(reinterpret_cast<const int2*>(blk + 16 * (size_t)vh) + i, pol), scale);
 }
 
 // ---------------------------------------------------------------------------

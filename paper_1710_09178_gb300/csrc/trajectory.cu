@@ -88,10 +88,6 @@ __device__ __forceinline__ void add_to(M3& a, const M3& b) {
   for (int i = 0; i < 9; ++i) a.e[i] = cadd(a.e[i], b.e[i]);
 }
 
-__device__ __forceinline__ int addr_shift(const Geom& g, const Site& s, int mu, int step) {
-  return neighbour_addr(g, step > 0 ? neighbour_fwd(g, s, mu) : neighbour_bwd(g, s, mu));
-}
-
 __device__ __forceinline__ Site site_at(const Geom& g, int l) {
   Site s;
   unsigned ul = (unsigned)l;
