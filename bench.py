@@ -4,8 +4,9 @@
 One step = one complete call of mshift_cg: the 16-pole rational approximation of
 x^{-1/2} on [4m^2, 16 + 4m^2] (m = 0.02) applied to a Gaussian source, solved to a
 true FP64 residual of 1e-10 for every shift (Section 4, Eq. ratapprx), in the
-mixed mode (FP32 links and Krylov vectors, FP64 dot products, solution
-accumulation, reliable updates and final residuals) -- every row of the hot path:
+mixed mode (double-FP32 until |r| <= 1e-3 |b|, then FP32 links and Krylov vectors;
+dot products, solution accumulation, reliable updates and final residuals with
+FP64-class accuracy as double-FP32 pairs) -- every row of the hot path:
 Dslash, A-apply, reductions, shifted updates, reliable updates, refinement and
 the rational application.
 
@@ -1095,7 +1096,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "poles": NPOLES,
                    "approximation": "x^-1/2 on [4m^2, 16+4m^2], Zolotarev (n,n)", "tol": TOL,
-                   "precision": "FP32 links+Krylov vectors, FP64 dots and x_k, double-FP32 (FP32 hi/lo) reliable updates and true residuals, 12-real FP32 links in the refinement",
+                   "precision": "double-FP32 (FP32 hi/lo) first phase until |r| <= 1e-3 |b|, then FP32 links+Krylov vectors; double-FP32 dots, x_k, reliable updates and true residuals; FP64 per-shift recurrences; 12-real FP32 links in the refinement",
                    "gauge": "exp(i 0.5 H) SU(3), seed 5", "source": "complex Gaussian, seed 6",
                    "l2": "flushed (256 MB written, then another 256 MB read) between timed steps and before every "
                          "isolated Dslash launch; the graph-launched Dslash of the roofline rotates over "

@@ -270,8 +270,9 @@ int lqcd_set_option(lqcd_ctx* ctx, int key, double value);
  *   maxiter    : cap on base iterations (and on each refinement solve)
  *   prec       : LQCD_FP64 (all FP64), LQCD_FP32, LQCD_FP32_R12, LQCD_FP16FIX, LQCD_FP32_R8
  *                or LQCD_FP32_L16 (FP32 arithmetic with that link copy in the shifted CG,
- *                dot products summed in FP32 per warp, FP64 per block and double-FP32 across
- *                blocks, FP64 scalar recurrences, solutions accumulated as double-FP32 pairs, reliable
+ *                dot products summed in FP32 per warp and in double-FP32 across warps and
+ *                blocks, alpha and beta as double-FP32 quotients, the per-shift recurrences in
+ *                FP64, solutions accumulated as double-FP32 pairs, reliable
  *                updates and final residuals in double-FP32 (LQCD_OPT_DF_RESID) or FP64, the
  *                solutions then in FP64 throughout; the refinement solves
  *                of all these modes use the FP32 12-real links), or LQCD_DF64 (every vector,
