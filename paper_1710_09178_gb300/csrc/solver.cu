@@ -8,13 +8,14 @@
 //      an extra block stores alpha (solver_dev.cuh)                      (r_update_kernel)
 //   4. beta from those partials, p = r + beta p; an extra block stores beta and
 //      decides the base stopping test and the reliable update           (p_update_kernel)
-// Every kWindow iterations one warp replays the per-shift recurrences of the window
-// from the stored alpha and beta (window_scalars_kernel), and the window kernel applies
-// the pending x_k / p_k updates of all shifts at once (flush_kernel): each shift vector is read and
-// written once per window instead of once per iteration, which is what makes
-// the multi-shift update (the heaviest loop of the shifted CG in Section 7)
-// cheap.  Iteration batches are captured in CUDA graphs; kernels return at entry
-// once the device-side `done` flag is set, so the host only polls a flag per batch.
+// Every kWindow iterations the per-shift recurrences of the window are replayed from the
+// stored alpha and beta, one block per shift (window_scalars_kernel), and the window kernel
+// applies the pending x_k / p_k updates of all shifts at once (flush_kernel): each shift vector
+// is read and written once per window instead of once per iteration, which is what makes the
+// multi-shift update (the heaviest loop of the shifted CG in Section 7) cheap.  A whole solve is
+// one CUDA graph: conditional while-nodes repeat the double-FP32 windows and then the FP32
+// windows until the device-side `done` flag is set (kernels return at entry once it is), so the
+// host waits once for the solve.  Without graphs the host polls the flag every few windows.
 #include <math.h>
 #include <string.h>
 
