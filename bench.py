@@ -780,6 +780,7 @@ def run_formats(lq, torch, dims_list=((32, 32, 32, 8), (48, 48, 48, 12)), reps=2
 
 def run_profile_target(kind, prec_name):
     """Small fixed workloads for ncu (no timing): `dslash` = 8 half-Dslash launches at 32^3x8,
+    `dslash48` = the same at 48^3x12 (the seeded 24^3x6 field tiled 2x2x2x2, FP32 links 382 MB),
     `dslash_graph` = the roofline's graph of 96 launches over 8 gauge fields (16 warm-up launches,
     then 6 replays of the graph: 592 launches), `df_dslash` = 8 double-FP32 half-Dslash launches,
     `solve` = one shifted-CG solve with CUDA graphs off, so that every kernel is a separate launch,
@@ -794,6 +795,20 @@ def run_profile_target(kind, prec_name):
     from paper_1710_09178_gb300 import inputs
 
     prec = lq.PRECISIONS[prec_name]
+    if kind == "dslash48":
+        # the link-format sweep's large lattice: links far beyond L2
+        dims48, U48 = tiled_field(torch, (24, 24, 24, 6), (2, 2, 2, 2), 9)
+        ctx = lq.Context(dims48, MASS)
+        ctx.set_gauge(U48)
+        vin = ctx.new_vector(prec)
+        vout = ctx.new_vector(prec)
+        vin.view(torch.float32 if prec != lq.FP64 else torch.float64).normal_()
+        for r in range(8):
+            lq.dslash_eo(ctx, vout, vin, r & 1, prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "dslash48", "dims": list(dims48), "prec": prec_name}))
+        ctx.close()
+        return
     ctx = lq.Context(DIMS, MASS)
     ctx.set_gauge(torch.from_numpy(inputs.gauge_field(DIMS, seed=GAUGE_SEED)).cuda())
     if kind == "dslash_graph":
@@ -852,7 +867,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="mixed mode only")
-    ap.add_argument("--profile", choices=["dslash", "dslash_graph", "df_dslash", "solve", "solve_graph", "multi"],
+    ap.add_argument("--profile", choices=["dslash", "dslash48", "dslash_graph", "df_dslash", "solve", "solve_graph", "multi"],
                     help="run a small fixed workload for ncu and exit")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_r12", "fp16fix", "fp32_r8", "fp32_l16", "df64"])
     ap.add_argument("--rhmc", type=int, default=0, help="run N RHMC trajectories on 24^3x6, print one JSON line")
